@@ -1,0 +1,334 @@
+"""Plain FP64 CPU oracle for the TBSCI sigma / Davidson path.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package. The
+CUDA library and its Python binding never import, link or call it, and share
+no code with it; the only shared module is ``tbsci_inputs`` (seeded random
+inputs, no method arithmetic).
+
+What it computes (each function cites the passage it follows):
+
+* ``fci_strings`` / ``sort_validate`` -- the alpha/beta string sets of the TPB
+  space (Sec. II.A, Eq. 3), ascending integer order, 0-based index.
+* ``links_single`` / ``links_double`` -- per-string single / double excitation
+  links restricted to the selected set (BETA_SINGLE_LINK / BETA_DOUBLE_LINK,
+  Sec. II.C; entry layout Sec. III.C), by explicit operator application.
+* ``sigma`` / ``diagonal`` / ``hamiltonian_dense`` -- H restricted to the TPB
+  space by the spin-orbital Slater-Condon rules (Sec. II.C, Eq. 8), sigma = H.c.
+* ``davidson`` -- standard Davidson (Sec. III.A) with restart to the Ritz
+  vectors when the subspace is full (Sec. III.C), in numpy FP64.
+
+Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
+(brute-force second quantisation, closed forms, library special cases,
+invariants, paper-printed counts).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tbsci_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc + OpenMP into ``oracle/_build``."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            i32 = ctypes.c_int
+            lib.orc_fci_strings.argtypes = [i32, i32, P, i64]
+            lib.orc_fci_strings.restype = i64
+            lib.orc_sort_validate.argtypes = [i32, i32, P, i64, P]
+            lib.orc_sort_validate.restype = i32
+            lib.orc_links_single.argtypes = [i32, P, i64, P, P, P, P, P]
+            lib.orc_links_single.restype = i64
+            lib.orc_links_double.argtypes = [i32, P, i64, P, P, P, P, P, P, P]
+            lib.orc_links_double.restype = i64
+            lib.orc_row_capacity.argtypes = [i32, i32, i32]
+            lib.orc_row_capacity.restype = i64
+            lib.orc_row.argtypes = [i32, P, i64, P, i64, P, P, ctypes.c_double, i64, P, P]
+            lib.orc_row.restype = i64
+            lib.orc_sigma_rows.argtypes = [i32, i32, i32, P, i64, P, i64, P, P, ctypes.c_double,
+                                           P, i32, P, i64, P, P, i32]
+            lib.orc_sigma_rows.restype = None
+            lib.orc_diagonal.argtypes = [i32, P, i64, P, i64, P, P, ctypes.c_double, P, i64, P]
+            lib.orc_diagonal.restype = None
+            lib.orc_max_threads.argtypes = []
+            lib.orc_max_threads.restype = i32
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+# ----------------------------------------------------------------- strings
+
+def fci_strings(norb: int, nelec: int) -> np.ndarray:
+    """All ``C(norb, nelec)`` strings, ascending (Sec. II.A, Eq. 3 with every
+    string selected)."""
+    lib = _load()
+    m = lib.orc_fci_strings(norb, nelec, None, 0)
+    out = np.zeros(m, dtype=np.uint64)
+    lib.orc_fci_strings(norb, nelec, _ptr(out), m)
+    return out
+
+
+def sort_validate(norb: int, nelec: int, strings) -> tuple[int, np.ndarray]:
+    """Sorted copy of a selected list and a status: 0 ok, 1 wrong electron count,
+    2 bit at or above ``norb``, 3 duplicate."""
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(strings, dtype=np.uint64))
+    out = np.zeros_like(a)
+    st = lib.orc_sort_validate(norb, nelec, _ptr(a), len(a), _ptr(out))
+    return int(st), out
+
+
+# ------------------------------------------------------------ link tables
+
+def links_single(norb: int, strings: np.ndarray):
+    """Single links per source string (Sec. II.C BETA_SINGLE_LINK; entry fields of
+    Sec. III.C): ``(off[l+1], tgt, sign, p, q)``; target ``a+_p a_q |J>``,
+    rows ordered by ``(q, p)``."""
+    lib = _load()
+    s = np.ascontiguousarray(strings, dtype=np.uint64)
+    l = len(s)
+    off = np.zeros(l + 1, dtype=np.int64)
+    m = lib.orc_links_single(norb, _ptr(s), l, _ptr(off), None, None, None, None)
+    tgt = np.zeros(m, dtype=np.int32)
+    sign = np.zeros(m, dtype=np.int8)
+    p = np.zeros(m, dtype=np.uint8)
+    q = np.zeros(m, dtype=np.uint8)
+    lib.orc_links_single(norb, _ptr(s), l, _ptr(off), _ptr(tgt), _ptr(sign), _ptr(p), _ptr(q))
+    return off, tgt, sign, p, q
+
+
+def links_double(norb: int, strings: np.ndarray):
+    """Double links per source string (Sec. II.C BETA_DOUBLE_LINK):
+    ``(off, tgt, sign, p, r, q, s)``; target ``a+_p a+_r a_s a_q |J>``, q < s,
+    p < r, rows ordered by ``(q, s, p, r)``."""
+    lib = _load()
+    st = np.ascontiguousarray(strings, dtype=np.uint64)
+    l = len(st)
+    off = np.zeros(l + 1, dtype=np.int64)
+    m = lib.orc_links_double(norb, _ptr(st), l, _ptr(off), None, None, None, None, None, None)
+    arrs = [np.zeros(m, dtype=np.int32), np.zeros(m, dtype=np.int8)] + [np.zeros(m, dtype=np.uint8) for _ in range(4)]
+    lib.orc_links_double(norb, _ptr(st), l, _ptr(off), *[_ptr(a) for a in arrs])
+    return (off, *arrs)
+
+
+# ------------------------------------------------------------- Hamiltonian
+
+class Space:
+    """A TPB determinant space (Sec. II.A, Eq. 3): sorted alpha and beta sets."""
+
+    def __init__(self, norb, nalpha, nbeta, alpha, beta):
+        self.norb, self.na, self.nb = int(norb), int(nalpha), int(nbeta)
+        self.sa = np.ascontiguousarray(alpha, dtype=np.uint64)
+        self.sb = np.ascontiguousarray(beta, dtype=np.uint64)
+        if len(self.sa) > 1 and not np.all(self.sa[1:] > self.sa[:-1]):
+            raise ValueError("alpha strings must be strictly ascending")
+        if len(self.sb) > 1 and not np.all(self.sb[1:] > self.sb[:-1]):
+            raise ValueError("beta strings must be strictly ascending")
+        self.la, self.lb = len(self.sa), len(self.sb)
+        self.ndet = self.la * self.lb
+
+
+def make_space(norb, nalpha, nbeta, alpha_sel=None, beta_sel=None) -> Space:
+    """Space from optional selections (``None`` = full string space)."""
+    if alpha_sel is None:
+        sa = fci_strings(norb, nalpha)
+    else:
+        st, sa = sort_validate(norb, nalpha, alpha_sel)
+        if st:
+            raise ValueError("bad alpha selection (status %d)" % st)
+    if beta_sel is None:
+        sb = fci_strings(norb, nbeta)
+    else:
+        st, sb = sort_validate(norb, nbeta, beta_sel)
+        if st:
+            raise ValueError("bad beta selection (status %d)" % st)
+    return Space(norb, nalpha, nbeta, sa, sb)
+
+
+def _ham_arrays(h, eri):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    n = h.shape[0]
+    assert eri.shape == (n, n, n, n)
+    return h, eri
+
+
+def sigma(space: Space, h, eri, ecore, C, rows=None, nthreads: int = 0, with_bound: bool = False):
+    """sigma = H.c (Sec. II.B, Eq. 7 with one process) over the listed determinant rows.
+
+    ``C``: ``[nvec, la, lb]`` or ``[nvec, ndet]`` float64. Returns ``[nvec, nrows]``
+    (and ``sum_J |H_KJ||c_J|`` when ``with_bound``)."""
+    lib = _load()
+    h, eri = _ham_arrays(h, eri)
+    C = np.ascontiguousarray(np.asarray(C, dtype=np.float64).reshape(-1, space.ndet))
+    nvec = C.shape[0]
+    if rows is None:
+        nrows = space.ndet
+        rows_arr = None
+    else:
+        rows_arr = np.ascontiguousarray(rows, dtype=np.int64)
+        nrows = len(rows_arr)
+    out = np.zeros((nvec, nrows))
+    bound = np.zeros((nvec, nrows)) if with_bound else None
+    lib.orc_sigma_rows(space.norb, space.na, space.nb, _ptr(space.sa), space.la, _ptr(space.sb), space.lb,
+                       _ptr(h), _ptr(eri), float(ecore), _ptr(C), nvec, _ptr(rows_arr), nrows,
+                       _ptr(out), _ptr(bound), int(nthreads))
+    return (out, bound) if with_bound else out
+
+
+def diagonal(space: Space, h, eri, ecore, rows=None) -> np.ndarray:
+    """H_KK (Sec. II.C, the stored [0,0] class) for the listed rows (all by default)."""
+    lib = _load()
+    h, eri = _ham_arrays(h, eri)
+    if rows is None:
+        rows_arr, nrows = None, space.ndet
+    else:
+        rows_arr = np.ascontiguousarray(rows, dtype=np.int64)
+        nrows = len(rows_arr)
+    out = np.zeros(nrows)
+    lib.orc_diagonal(space.norb, _ptr(space.sa), space.la, _ptr(space.sb), space.lb, _ptr(h), _ptr(eri),
+                     float(ecore), _ptr(rows_arr), nrows, _ptr(out))
+    return out
+
+
+def row(space: Space, h, eri, ecore, K: int):
+    """Non-zero elements ``(cols, vals)`` of row K of H, diagonal first."""
+    lib = _load()
+    h, eri = _ham_arrays(h, eri)
+    cap = lib.orc_row_capacity(space.norb, space.na, space.nb)
+    cols = np.zeros(cap, dtype=np.int64)
+    vals = np.zeros(cap)
+    m = lib.orc_row(space.norb, _ptr(space.sa), space.la, _ptr(space.sb), space.lb, _ptr(h), _ptr(eri),
+                    float(ecore), int(K), _ptr(cols), _ptr(vals))
+    return cols[:m].copy(), vals[:m].copy()
+
+
+def hamiltonian_dense(space: Space, h, eri, ecore) -> np.ndarray:
+    """Dense H over the space (small spaces only)."""
+    H = np.zeros((space.ndet, space.ndet))
+    for K in range(space.ndet):
+        cols, vals = row(space, h, eri, ecore, K)
+        H[K, cols] = vals
+    return H
+
+
+# --------------------------------------------------------------- Davidson
+
+def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, max_iter=300):
+    """Standard Davidson (Sec. III.A) for the lowest ``nroots`` eigenpairs.
+
+    Steps, in order, each iteration: Rayleigh matrix G = V^T W; eigenpairs of G;
+    Ritz vectors X = V Y and residuals R = W Y - X diag(theta); stop when every
+    root has |theta - theta_prev| < tol_e and ||r|| < tol_r; otherwise precondition
+    each unconverged residual by (theta - H_KK)^-1 (denominators of magnitude
+    below 1e-8 clamped to +-1e-8, zero -> +1e-8); when the subspace would exceed
+    ``max_subspace`` restart from the Ritz vectors (the paper's restart scheme,
+    Sec. III.C); orthogonalise the new directions twice against the basis and
+    each other, normalise, and drop those whose norm fell below 1e-10 of their
+    pre-projection norm.
+
+    ``apply_h(V)`` maps ``[k, N]`` to ``[k, N]``. The guess is the ``nroots``
+    unit vectors at the lowest diagonal entries, ties broken by index.
+    Returns ``(energies, vectors[nroots, N], info)``.
+    """
+    diag = np.asarray(diag, dtype=np.float64)
+    N = len(diag)
+    if max_subspace is None:
+        max_subspace = max(8 * nroots, nroots + 2)
+    order = np.lexsort((np.arange(N), diag))
+    V = np.zeros((nroots, N))
+    for k in range(nroots):
+        V[k, order[k]] = 1.0
+    W = apply_h(V)
+    nsigma = nroots
+    theta_prev = None
+    info = dict(iterations=0, converged=False, nsigma=0)
+    for it in range(1, max_iter + 1):
+        G = V @ W.T
+        G = 0.5 * (G + G.T)
+        evals, Y = np.linalg.eigh(G)
+        theta = evals[:nroots]
+        Y = Y[:, :nroots]
+        X = Y.T @ V
+        WY = Y.T @ W
+        R = WY - theta[:, None] * X
+        rnorm = np.linalg.norm(R, axis=1)
+        dE = np.full(nroots, np.inf) if theta_prev is None else np.abs(theta - theta_prev)
+        theta_prev = theta.copy()
+        info.update(iterations=it, rnorm=rnorm.copy(), nsigma=nsigma)
+        if np.all(dE < tol_e) and np.all(rnorm < tol_r):
+            info["converged"] = True
+            return theta, X, info
+        T = []
+        for k in range(nroots):
+            if rnorm[k] < tol_r:
+                continue
+            d = theta[k] - diag
+            small = np.abs(d) < 1e-8
+            d[small] = np.where(d[small] < 0, -1e-8, 1e-8)
+            T.append(R[k] / d)
+        if V.shape[0] + len(T) > max_subspace:
+            V, W = X, WY
+        newV = []
+        for t in T:
+            t0 = np.linalg.norm(t)
+            for _ in range(2):
+                t = t - V.T @ (V @ t)
+                for u in newV:
+                    t = t - (u @ t) * u
+            nt = np.linalg.norm(t)
+            if nt <= 1e-10 * t0:
+                continue
+            newV.append(t / nt)
+        if newV:
+            Vn = np.array(newV)
+            Wn = apply_h(Vn)
+            nsigma += len(newV)
+            V = np.vstack([V, Vn])
+            W = np.vstack([W, Wn])
+    info["converged"] = False
+    return theta_prev, X, info
+
+
+def solve(space: Space, h, eri, ecore, nroots, nthreads=0, **kw):
+    """Lowest eigenpairs of H on the space: oracle sigma + oracle Davidson."""
+    d = diagonal(space, h, eri, ecore)
+
+    def apply_h(V):
+        return sigma(space, h, eri, ecore, V, nthreads=nthreads)
+
+    return davidson(apply_h, d, nroots, **kw)

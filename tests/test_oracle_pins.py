@@ -1,0 +1,350 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Each check is chosen so that a plausible slip in the oracle (a dropped exchange
+term, a wrong sign convention, a transposed integral index, a missed
+excitation class, a wrong table order) fails at least one of them:
+
+* brute-force second quantisation of H = sum h a+a + 1/2 sum (pq|rs) a+a+aa
+  on tiny spaces (independent of the Slater-Condon rules the oracle uses);
+* closed forms: one-electron systems, N_alpha = N_beta = 1 FCI Hamiltonian
+  h x 1 + 1 x h + (ij|kl), one-electron eigenvalue sums;
+* invariants: symmetry, particle-number shift, spin flip, variational order;
+* paper-printed numbers: Table VI single-link entry counts (Sec. III.C).
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tbsci_inputs import synth_hamiltonian, selected_strings
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ brute force
+
+def _annihilate(occ, P):
+    if P not in occ:
+        return 0, None
+    i = occ.index(P)
+    return (-1) ** i, occ[:i] + occ[i + 1:]
+
+
+def _create(occ, P):
+    if P in occ:
+        return 0, None
+    i = sum(1 for x in occ if x < P)
+    return (-1) ** i, tuple(sorted(occ + (P,)))
+
+
+def _apply(ops, occ):
+    """Apply an operator product (leftmost acts last) to a determinant."""
+    sign = 1
+    for kind, P in reversed(ops):
+        s, occ = (_create if kind == "c" else _annihilate)(occ, P)
+        if s == 0:
+            return 0, None
+        sign *= s
+    return sign, occ
+
+
+def brute_force_h(n, sa, sb, h, eri, ecore):
+    """Dense H over the TPB space from the second-quantised operator sum."""
+    dets = []
+    for a in sa:
+        for b in sb:
+            occ = tuple([p for p in range(n) if (int(a) >> p) & 1] + [n + p for p in range(n) if (int(b) >> p) & 1])
+            dets.append(occ)
+    index = {d: k for k, d in enumerate(dets)}
+    N = len(dets)
+    H = np.zeros((N, N))
+    spins = (0, n)
+    for J, occ in enumerate(dets):
+        H[J, J] += ecore
+        for sg in spins:
+            for p in range(n):
+                for q in range(n):
+                    s, new = _apply([("c", sg + p), ("a", sg + q)], occ)
+                    if s and new in index:
+                        H[index[new], J] += s * h[p, q]
+        for s1 in spins:
+            for s2 in spins:
+                for p, q, r, s_ in itertools.product(range(n), repeat=4):
+                    v = eri[p, q, r, s_]
+                    if v == 0.0:
+                        continue
+                    sgn, new = _apply([("c", s1 + p), ("c", s2 + r), ("a", s2 + s_), ("a", s1 + q)], occ)
+                    if sgn and new in index:
+                        H[index[new], J] += 0.5 * sgn * v
+    return H
+
+
+@pytest.mark.parametrize("n,na,nb,sel", [(3, 1, 1, None), (4, 2, 1, None), (4, 2, 2, None),
+                                         (5, 2, 2, 6), (5, 3, 2, None)])
+def test_dense_h_matches_second_quantisation(n, na, nb, sel):
+    h, eri, _ = synth_hamiltonian(n, seed=11 + n + na)
+    ecore = 0.37
+    asel = None if sel is None else selected_strings(n, na, sel, seed=5)
+    bsel = None if sel is None else selected_strings(n, nb, sel, seed=6)
+    sp = oracle.make_space(n, na, nb, asel, bsel)
+    H = oracle.hamiltonian_dense(sp, h, eri, ecore)
+    Hb = brute_force_h(n, sp.sa, sp.sb, h, eri, ecore)
+    assert np.max(np.abs(H - Hb)) < 1e-12
+
+
+# ------------------------------------------------------------ closed forms
+
+def test_one_electron_alpha_only_is_h():
+    n = 7
+    h, eri, _ = synth_hamiltonian(n, seed=3)
+    sp = oracle.make_space(n, 1, 0)
+    assert sp.la == n and sp.lb == 1
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.5)
+    # one alpha electron, no beta: H = h + ecore exactly (two-electron terms vanish)
+    assert np.max(np.abs(H - (h + 0.5 * np.eye(n)))) < 1e-14
+
+
+def test_one_plus_one_fci_closed_form():
+    n = 6
+    h, eri, _ = synth_hamiltonian(n, seed=4)
+    sp = oracle.make_space(n, 1, 1)
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.0)
+    I = np.eye(n)
+    ref = np.kron(h, I) + np.kron(I, h) + eri.transpose(0, 2, 1, 3).reshape(n * n, n * n)
+    assert np.max(np.abs(H - ref)) < 1e-13
+
+
+def test_one_electron_operator_eigenvalue_sum():
+    n, na, nb = 7, 3, 2
+    h, eri, _ = synth_hamiltonian(n, seed=9)
+    sp = oracle.make_space(n, na, nb)
+    H = oracle.hamiltonian_dense(sp, h, np.zeros_like(eri), 0.0)
+    e = np.linalg.eigvalsh(h)
+    assert abs(np.linalg.eigvalsh(H)[0] - (e[:na].sum() + e[:nb].sum())) < 1e-12
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_symmetry_and_slater_condon_sparsity():
+    n, na, nb = 6, 3, 3
+    h, eri, _ = synth_hamiltonian(n, seed=21)
+    sp = oracle.make_space(n, na, nb)
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.0)
+    assert np.max(np.abs(H - H.T)) <= 1e-14 * np.max(np.abs(H))
+    # Eq. 8: no coupling beyond two differing spin orbitals in total
+    pc = np.vectorize(lambda x: bin(int(x)).count("1"))
+    da = pc(np.bitwise_xor.outer(sp.sa, sp.sa)) // 2
+    db = pc(np.bitwise_xor.outer(sp.sb, sp.sb)) // 2
+    diff = (da[:, None, :, None] + db[None, :, None, :]).reshape(sp.ndet, sp.ndet)
+    assert np.all(H[diff > 2] == 0.0)
+    # all six classes [a,b] with a+b <= 2 occur
+    classes = {(int(a), int(b)) for a in range(3) for b in range(3) if a + b <= 2}
+    found = set()
+    for a, b in classes:
+        m = (da[:, None, :, None] == a) & (db[None, :, None, :] == b)
+        if np.any(H[m.reshape(sp.ndet, sp.ndet)] != 0.0):
+            found.add((a, b))
+    assert found == classes
+
+
+def test_sigma_matches_dense_and_bound():
+    n, na, nb = 6, 3, 2
+    h, eri, _ = synth_hamiltonian(n, seed=22)
+    sp = oracle.make_space(n, na, nb, None, selected_strings(n, nb, 9, seed=1))
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.1)
+    C = np.random.default_rng(0).standard_normal((2, sp.ndet))
+    S, B = oracle.sigma(sp, h, eri, 0.1, C, with_bound=True)
+    assert np.max(np.abs(S - C @ H.T)) < 1e-12
+    assert np.max(np.abs(B - np.abs(C) @ np.abs(H).T)) < 1e-12
+    rows = np.array([3, 0, sp.ndet - 1])
+    assert np.max(np.abs(oracle.sigma(sp, h, eri, 0.1, C, rows=rows) - S[:, rows])) == 0.0
+    assert np.max(np.abs(oracle.diagonal(sp, h, eri, 0.1) - np.diag(H))) < 1e-13
+
+
+def test_particle_number_shift():
+    n, na, nb = 8, 4, 3
+    h, eri, _ = synth_hamiltonian(n, seed=23)
+    sp = oracle.make_space(n, na, nb, selected_strings(n, na, 40, seed=2), None)
+    C = np.random.default_rng(1).standard_normal((1, sp.ndet))
+    eps = 0.25
+    s0 = oracle.sigma(sp, h, eri, 0.0, C)
+    s1 = oracle.sigma(sp, h + eps * np.eye(n), eri, 0.0, C)
+    assert np.max(np.abs(s1 - s0 - eps * (na + nb) * C)) < 1e-12
+
+
+def test_spin_flip_transpose():
+    n = 8
+    h, eri, _ = synth_hamiltonian(n, seed=24)
+    sel = selected_strings(n, 4, 50, seed=3)
+    sp = oracle.make_space(n, 4, 4, sel, sel)
+    C = np.random.default_rng(2).standard_normal((sp.la, sp.lb))
+    s = oracle.sigma(sp, h, eri, 0.0, C[None]).reshape(sp.la, sp.lb)
+    st = oracle.sigma(sp, h, eri, 0.0, C.T.copy()[None]).reshape(sp.la, sp.lb)
+    assert np.max(np.abs(st - s.T)) < 1e-12
+
+
+def test_variational_nested_selections():
+    n, na, nb = 8, 4, 4
+    h, eri, _ = synth_hamiltonian(n, seed=25)
+    full = oracle.make_space(n, na, nb)
+    e_fci = np.linalg.eigvalsh(oracle.hamiltonian_dense(full, h, eri, 0.0))[0]
+    last = np.inf
+    order = selected_strings(n, na, 70, seed=4, shuffle=False)
+    for cnt in (10, 25, 45, 70):
+        sub = order[:cnt]
+        sp = oracle.make_space(n, na, nb, sub, sub)
+        e0 = np.linalg.eigvalsh(oracle.hamiltonian_dense(sp, h, eri, 0.0))[0]
+        assert e0 <= last + 1e-12
+        assert e0 >= e_fci - 1e-12
+        last = e0
+    assert abs(last - e_fci) < 1e-10
+
+
+# ------------------------------------------------------------ strings / links
+
+def test_fci_strings_against_combinations():
+    for n, N in [(1, 0), (1, 1), (6, 3), (10, 4), (12, 6)]:
+        s = oracle.fci_strings(n, N)
+        ref = sorted(sum(1 << i for i in c) for c in itertools.combinations(range(n), N))
+        assert list(map(int, s)) == ref
+
+
+def test_sort_validate_errors():
+    ok, out = oracle.sort_validate(6, 2, [0b110000, 0b11, 0b101])
+    assert ok == 0 and list(map(int, out)) == [0b11, 0b101, 0b110000]
+    assert oracle.sort_validate(6, 2, [0b111])[0] == 1
+    assert oracle.sort_validate(6, 2, [0b1000001])[0] == 2
+    assert oracle.sort_validate(6, 2, [0b11, 0b11])[0] == 3
+
+
+def _bf_single_links(n, strs):
+    index = {int(s): i for i, s in enumerate(strs)}
+    rows = []
+    for s in strs:
+        occ = tuple(p for p in range(n) if (int(s) >> p) & 1)
+        row = []
+        for q in range(n):
+            for p in range(n):
+                if p == q:
+                    continue
+                sg, new = _apply([("c", p), ("a", q)], occ)
+                if sg == 0:
+                    continue
+                t = sum(1 << x for x in new)
+                if t in index:
+                    row.append((index[t], sg, p, q))
+        rows.append(row)
+    return rows
+
+
+def _bf_double_links(n, strs):
+    index = {int(s): i for i, s in enumerate(strs)}
+    rows = []
+    for s in strs:
+        occ = tuple(p for p in range(n) if (int(s) >> p) & 1)
+        vir = [p for p in range(n) if p not in occ]
+        row = []
+        for q, s_ in itertools.combinations(occ, 2):
+            for p, r in itertools.combinations(vir, 2):
+                sg, new = _apply([("c", p), ("c", r), ("a", s_), ("a", q)], occ)
+                t = sum(1 << x for x in new)
+                if t in index:
+                    row.append((index[t], sg, p, r, q, s_))
+        rows.append(row)
+    return rows
+
+
+@pytest.mark.parametrize("n,N,sel", [(6, 3, None), (8, 4, None), (9, 3, 30), (10, 5, 60)])
+def test_links_against_brute_force(n, N, sel):
+    strs = oracle.fci_strings(n, N) if sel is None else oracle.sort_validate(n, N, selected_strings(n, N, sel, 7))[1]
+    off, tgt, sign, p, q = oracle.links_single(n, strs)
+    bf = _bf_single_links(n, strs)
+    for i, row in enumerate(bf):
+        got = list(zip(tgt[off[i]:off[i + 1]].tolist(), sign[off[i]:off[i + 1]].tolist(),
+                       p[off[i]:off[i + 1]].tolist(), q[off[i]:off[i + 1]].tolist()))
+        assert got == row
+    off2, tgt2, sg2, p2, r2, q2, s2 = oracle.links_double(n, strs)
+    bf2 = _bf_double_links(n, strs)
+    for i, row in enumerate(bf2):
+        sl = slice(off2[i], off2[i + 1])
+        got = list(zip(tgt2[sl].tolist(), sg2[sl].tolist(), p2[sl].tolist(), r2[sl].tolist(),
+                       q2[sl].tolist(), s2[sl].tolist()))
+        assert got == row
+    if sel is None:
+        assert off[-1] == math.comb(n, N) * N * (n - N)
+        assert off2[-1] == math.comb(n, N) * math.comb(N, 2) * math.comb(n - N, 2)
+
+
+def test_single_link_reciprocity():
+    n, N = 10, 5
+    strs = oracle.sort_validate(n, N, selected_strings(n, N, 80, 8))[1]
+    off, tgt, sign, p, q = oracle.links_single(n, strs)
+    fwd = set()
+    for j in range(len(strs)):
+        for k in range(off[j], off[j + 1]):
+            fwd.add((j, int(tgt[k]), int(sign[k]), int(p[k]), int(q[k])))
+    for (j, i, sg, pp, qq) in fwd:
+        assert (i, j, sg, qq, pp) in fwd
+
+
+def _read_table6():
+    rows = []
+    with open(os.path.join(GOLDEN, "table6_single_links.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                name, n, nb, entries, gb = line.split()
+                rows.append((name, int(n), int(nb), int(entries), float(gb)))
+    return rows
+
+
+def test_table6_single_link_counts_closed_form():
+    """Paper Table VI (Sec. III.C): FCI single-link entry counts and their 7-byte
+    footprint. The oracle's link count equals C(n,N) N (n-N) on full spaces
+    (checked above by brute force), so this pins the count and byte model to the
+    printed values."""
+    rows = _read_table6()
+    assert len(rows) == 4
+    for name, n, nb, entries, gb in rows:
+        assert math.comb(n, nb) * nb * (n - nb) == entries, name
+        assert abs(entries * 7 / 2 ** 30 - gb) < 0.006, name
+
+
+def test_oracle_link_count_matches_closed_form_medium():
+    for n, N in [(12, 6), (14, 3)]:
+        strs = oracle.fci_strings(n, N)
+        off, *_ = oracle.links_single(n, strs)
+        assert off[-1] == math.comb(n, N) * N * (n - N)
+
+
+# ------------------------------------------------------------------ Davidson
+
+def test_davidson_matches_dense_small():
+    n, na, nb = 6, 3, 3
+    h, eri, _ = synth_hamiltonian(n, seed=31)
+    sp = oracle.make_space(n, na, nb)
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.0)
+    ref = np.linalg.eigvalsh(H)[:4]
+    e, X, info = oracle.solve(sp, h, eri, 0.0, nroots=4, max_subspace=16)
+    assert info["converged"]
+    assert np.max(np.abs(e - ref)) < 1e-8
+    for k in range(4):
+        r = H @ X[k] - e[k] * X[k]
+        assert np.linalg.norm(r) < 1e-5
+
+
+def test_fci8_golden_energies():
+    """Config norb=8, 4+4, all 70 x 70 strings: dense eigenvalues stored by
+    tests/golden/make_golden.py (oracle + numpy eigh) and the oracle Davidson."""
+    path = os.path.join(GOLDEN, "fci8_energies.txt")
+    ref = np.loadtxt(path)
+    from tbsci_inputs import WORKLOADS
+    wl = WORKLOADS["fci8"]
+    h, eri, ecore = wl.hamiltonian()
+    sp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta)
+    e, X, info = oracle.solve(sp, h, eri, ecore, nroots=3)
+    assert info["converged"]
+    assert np.max(np.abs(e - ref[:3])) < 1e-8
