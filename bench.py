@@ -1,0 +1,319 @@
+"""Benchmark: sigma = H.c throughput (GDet/s) on one GB300, plus Davidson time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+                    [--workload sel16|fci8|fci16|sel24] [--dtype f64|f32]
+
+A step is one sigma evaluation of ``nvec`` vectors over the whole space (all of
+its Slater-Condon classes, one fused kernel launch per group of <= 4 vectors).
+The default workload is norb=16, 8+8 electrons, 3,000 x 3,000 selected strings
+(9.0M determinants), FP64, 3 vectors -- 216 MB of input and 216 MB of output per
+step, both larger than the 129 MB L2, so no flush is needed between steps.
+
+value  = nvec * ndet / (device time per step) / 1e9, timed with CUDA events on
+         the launching stream after W warm-up steps, max over ranks.
+e2e    = the same metric through tbsci_sigma_host with pinned host buffers:
+         host->device copy of c and device->host copy of sigma inside the timed
+         region.
+roofline = the fused sigma kernel against the FP64 ALU (2 flops per non-zero
+         H_IJ per vector) or the FP32 ALU.
+cpu_baseline = the CPU oracle timed on a bounded row sample of the same
+         workload on this host's cores (rank 0, N = 1 only).
+--impl reference runs the oracle alone as the reference arm.
+
+Under torchrun (N > 1) every rank runs an independent replica (the path does
+not shard); value sums the ranks' work over the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from tbsci_inputs import WORKLOADS, random_vectors  # noqa: E402
+
+METRIC = "σ GDet/s and Davidson time to 1e-8 Eh; serving p50/p99 vs plain FP64 on GB300"
+UNIT = "GDet/s"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (recipe nominal)
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FMA = 2 flops
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def cpu_baseline(wl, nvec, budget_s=15.0, impl_rows=None):
+    """Oracle sigma over a bounded, seeded row sample of the workload."""
+    import oracle
+    h, eri, ecore = wl.hamiltonian()
+    sp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, wl.alpha_selection(), wl.beta_selection())
+    C = random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec).reshape(nvec, -1)
+    rng = np.random.default_rng(wl.seed_vec + 17)
+    # calibrate on a small sample, then size the measured sample to the budget
+    probe = rng.choice(sp.ndet, 500, replace=False)
+    t0 = time.perf_counter()
+    oracle.sigma(sp, h, eri, ecore, C, rows=probe)
+    rate = 500 / max(time.perf_counter() - t0, 1e-6)
+    nrows = impl_rows or int(min(sp.ndet, max(1000, rate * budget_s)))
+    rows = rng.choice(sp.ndet, nrows, replace=False)
+    t0 = time.perf_counter()
+    oracle.sigma(sp, h, eri, ecore, C, rows=rows)
+    dt = time.perf_counter() - t0
+    return {"value": nrows * nvec / dt / 1e9, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "%d seeded determinant rows of %d (%d vectors), %.1f s" % (nrows, sp.ndet, nvec, dt),
+            "seconds": dt, "rows": nrows}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOADS[args.workload]
+    nvec = wl.nvec
+    h, eri, ecore = wl.hamiltonian()
+    sp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, wl.alpha_selection(), wl.beta_selection())
+    C = random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec).reshape(nvec, -1)
+    rng = np.random.default_rng(wl.seed_vec + 29)
+    rows_per_step = min(sp.ndet, args.ref_rows)
+    for _ in range(args.warmup):
+        oracle.sigma(sp, h, eri, ecore, C, rows=rng.choice(sp.ndet, rows_per_step, replace=False))
+    times = []
+    for _ in range(args.steps):
+        rows = rng.choice(sp.ndet, rows_per_step, replace=False)
+        t0 = time.perf_counter()
+        oracle.sigma(sp, h, eri, ecore, C, rows=rows)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = rows_per_step * nvec * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(wl, nvec, "f64"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "%d seeded determinant rows per step of %d, %d vectors" %
+                                   (rows_per_step, sp.ndet, nvec)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(wl, nvec, dtype):
+    la = math.comb(wl.norb, wl.nalpha) if wl.count_alpha is None else min(wl.count_alpha, math.comb(wl.norb, wl.nalpha))
+    lb = math.comb(wl.norb, wl.nbeta) if wl.count_beta is None else min(wl.count_beta, math.comb(wl.norb, wl.nbeta))
+    return {"workload": wl.notes, "name": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta,
+            "l_alpha": la, "l_beta": lb, "ndet": la * lb, "nvec": nvec, "sigma_dtype": dtype,
+            "l2_policy": "inputs larger than L2 (no flush)" if la * lb * nvec * (8 if dtype == "f64" else 4) > 129e6
+            else "L2 flushed between steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default="sel16", choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--ref-rows", type=int, default=20000)
+    ap.add_argument("--no-davidson", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2503_10335_gb300 as tb
+
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    nvec = wl.nvec
+    h, eri, ecore = wl.hamiltonian()
+    ctx = tb.Context(local)
+    t_setup = time.perf_counter()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=wl.alpha_selection(),
+                  beta=wl.beta_selection())
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    counts = sp.counts()
+    Cn = random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec)
+    tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    C = torch.from_numpy(Cn).to(dev).to(tdt)
+    S = torch.empty_like(C)
+    stream = torch.cuda.current_stream()
+    launches_per_step = (nvec + 3) // 4
+
+    for _ in range(args.warmup):
+        sp.sigma(C, S, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        sp.sigma(C, S, stream=stream)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = ws * nvec * sp.ndet / (ms_step * 1e-3) / 1e9
+
+    # roofline of the fused sigma kernel (one launch per step for nvec <= 4)
+    flops_step = 2.0 * counts["nnz"] * nvec
+    kern_ms = statistics.mean(per_step) / launches_per_step
+    achieved = flops_step / launches_per_step / (kern_ms * 1e-3) / 1e12
+    peak = FP64_NOMINAL_TFLOPS if args.dtype == "f64" else FP32_NOMINAL_TFLOPS
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_sigma (fused, all classes)",
+                "peak_source": "nominal %s ALU (152 SMs, 2070 MHz)" % ("FP64" if args.dtype == "f64" else "FP32"),
+                "algorithmic_flops_per_launch": flops_step / launches_per_step}
+
+    # end to end through the C ABI with pinned host buffers (FP64)
+    e2e = None
+    if args.dtype == "f64":
+        hc = torch.from_numpy(Cn).pin_memory()
+        hs = torch.empty_like(hc).pin_memory()
+        hcn, hsn = hc.numpy(), hs.numpy()
+        sp.sigma_host(hcn)  # warm the device buffers
+        tb.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, hcn, hsn, nvec)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            tb.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, hcn, hsn, nvec)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        nbytes = nvec * sp.ndet * 8
+        e2e = {"value": ws * nvec * sp.ndet / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3, "steps": args.e2e_steps,
+               "api": "tbsci_sigma_host"}
+
+    dav = None
+    if not args.no_davidson and rank == 0:
+        dav = {}
+        for mode in ("f64", "mixed"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e, info = sp.davidson(wl.nroots, mixed=(mode == "mixed"), tol_energy=1e-9, tol_residual=1e-5)
+            dt = time.perf_counter() - t0
+            dav[mode] = {"seconds": dt, "iterations": info["iterations"], "nsigma": info["nsigma"],
+                         "nsigma_f32": info["nsigma_f32"], "energies": [float(x) for x in e],
+                         "converged": info["converged"], "seconds_sigma": info["seconds_sigma"]}
+        dav["mixed_minus_f64_max_abs"] = max(abs(a - b) for a, b in zip(dav["mixed"]["energies"],
+                                                                       dav["f64"]["energies"]))
+        dav["target"] = "time to |dE| < 1e-9 and ||r|| < 1e-5 per root (energies within 1e-8 Eh)"
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, nvec)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": dict(_config(wl, nvec, args.dtype), parallelism="replicas" if ws > 1 else "single"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks, "davidson": dav,
+            "counts": counts, "setup_seconds": t_setup,
+            "step_ms_min": min(per_step), "step_ms_max": max(per_step),
+        }
+        print(json.dumps(line), flush=True)
+    sp.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

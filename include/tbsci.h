@@ -1,0 +1,227 @@
+/*
+ * tbsci.h -- C ABI of the GB300 TBSCI library: the Hamiltonian-times-vector
+ * product sigma = H.c over a tensor-product bitstring (TPB) determinant space
+ * and the Davidson eigensolver that drives it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns a tbsci_status; nothing aborts or exits. On an error
+ *    tbsci_last_error() of the context gives a one-line reason.
+ *  - Strings are uint64 occupation bitstrings: bit i (LSB = 0) is spatial
+ *    orbital i, norb <= 64. A string set is kept in ascending integer order and
+ *    a string's index is its 0-based rank in that order.
+ *  - A determinant is an alpha string times a beta string (Sec. II.A, Eq. 2-3);
+ *    as a spin-orbital determinant it is a+_{alpha occ} a+_{beta occ} |0> with
+ *    ascending indices inside each block, so a beta excitation carries only its
+ *    own string sign. Determinant index K = w * l_beta + u (beta fastest,
+ *    Sec. II.A, Eq. 4-5), so a CI vector is a row-major l_alpha x l_beta matrix.
+ *  - Vectors passed to sigma/davidson are DEVICE pointers owned by the caller,
+ *    layout [nvec][l_alpha][l_beta], contiguous. Host arrays passed in are copied
+ *    before the call returns. Objects the library creates are opaque handles
+ *    that own their device memory and are freed by the matching *_destroy.
+ *  - Objects belong to the context that made them; one context is used by one
+ *    host thread at a time. Calls take a stream where they launch work on a
+ *    caller's stream; otherwise they run on the context's own stream and return
+ *    when the work is complete.
+ */
+#ifndef TBSCI_H
+#define TBSCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tbsci_status {
+    TBSCI_OK = 0,
+    TBSCI_EINVAL = 1,   /* invalid argument or input data */
+    TBSCI_ENOMEM = 2,   /* device or host allocation failed / over budget */
+    TBSCI_ECUDA = 3,    /* a CUDA call failed (message in tbsci_last_error) */
+    TBSCI_ENOCONV = 4,  /* Davidson reached max_iter; best estimates returned */
+    TBSCI_EAGAIN = 5,   /* serving: queue full / result not ready */
+    TBSCI_ETIMEOUT = 6, /* serving: poll timed out */
+    TBSCI_EBUSY = 7     /* object in use */
+} tbsci_status;
+
+/* Arithmetic of a sigma evaluation. F64 and F32 name the type of c and sigma
+ * and of all arithmetic. */
+typedef enum tbsci_dtype { TBSCI_F64 = 0, TBSCI_F32 = 1 } tbsci_dtype;
+
+/* Same object as cudaStream_t; NULL = the legacy default stream. */
+typedef struct CUstream_st *tbsci_stream;
+
+typedef struct tbsci_ctx tbsci_ctx;
+typedef struct tbsci_strings tbsci_strings;
+typedef struct tbsci_tables tbsci_tables;
+typedef struct tbsci_ham tbsci_ham;
+
+/* One single-excitation link of a source string J (8 bytes): the target string
+ * I = a+_p a_q |J> of the same set, and sign = <I|a+_p a_q|J>. This is the
+ * BETA_SINGLE_LINK entry of Sec. II.C (the paper packs the same fields into
+ * 7 bytes, Sec. III.C). */
+typedef struct tbsci_single_link {
+    int32_t target;
+    int8_t sign;
+    uint8_t p; /* created orbital */
+    uint8_t q; /* annihilated orbital */
+    uint8_t pad;
+} tbsci_single_link;
+
+/* One double-excitation link (12 bytes, BETA_DOUBLE_LINK of Sec. II.C):
+ * I = a+_p a+_r a_s a_q |J>, q < s annihilated, p < r created, sign =
+ * <I|a+_p a+_r a_s a_q|J>. */
+typedef struct tbsci_double_link {
+    int32_t target;
+    int8_t sign;
+    uint8_t p, r, q, s;
+    uint8_t pad[3];
+} tbsci_double_link;
+
+/* ------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device` (made current for the calls of this
+ * context). Errors: EINVAL (bad device), ECUDA. */
+tbsci_status tbsci_create(int device, tbsci_ctx **out);
+void tbsci_destroy(tbsci_ctx *ctx);
+/* Last error message of this context ("" when none). Valid until the next call. */
+const char *tbsci_last_error(const tbsci_ctx *ctx);
+const char *tbsci_status_string(tbsci_status st);
+
+/* --------------------------------------------------------------- strings */
+
+/* Builds a string set (Sec. II.A, Eq. 3: the sets {S^alpha}, {S^beta}).
+ * selected == NULL: all C(norb, nelec) strings (full string space; nsel is
+ * ignored). Otherwise `selected` is a HOST array of nsel strings in any order;
+ * the set is sorted ascending on the device.
+ * Errors: EINVAL when norb is outside 1..64, nelec outside 0..norb, a selected
+ * string has the wrong electron count, a bit at or above norb, or appears
+ * twice, or the set would exceed 2^31 - 1 strings; ENOMEM; ECUDA. */
+tbsci_status tbsci_build_strings(tbsci_ctx *ctx, int norb, int nelec, const uint64_t *selected,
+                                 int64_t nsel, tbsci_strings **out);
+tbsci_status tbsci_strings_count(const tbsci_strings *s, int64_t *count);
+/* Copies the sorted set into host memory `out` (count entries). */
+tbsci_status tbsci_strings_export(tbsci_ctx *ctx, const tbsci_strings *s, uint64_t *out);
+void tbsci_strings_destroy(tbsci_strings *s);
+
+/* ---------------------------------------------------------- link tables */
+
+#define TBSCI_TABLES_SINGLES_ONLY 1 /* build no double links */
+#define TBSCI_TABLES_COUNT_ONLY 2   /* count links, store no entries */
+
+/* Builds the single and double excitation links of every string of the set
+ * within the set (BETA_SINGLE_LINK / BETA_DOUBLE_LINK, Sec. II.C; the paper
+ * builds them for beta, this library for both spins). Rows are CSR by source
+ * string; inside a row singles are ordered by (q, p) and doubles by
+ * (q, s, p, r), ascending. The target index comes from the combinatorial rank
+ * (full string space) or a binary search (selected set). Sign from masked
+ * popcounts. The tables keep their own copy of the strings.
+ * Errors: EINVAL (flags), ENOMEM, ECUDA. */
+tbsci_status tbsci_build_excitation_tables(tbsci_ctx *ctx, const tbsci_strings *s, int flags,
+                                           tbsci_tables **out);
+tbsci_status tbsci_tables_counts(const tbsci_tables *t, int64_t *nsingle, int64_t *ndouble);
+/* Copies the tables into host arrays: off1[l+1], ent1[nsingle], off2[l+1],
+ * ent2[ndouble]; any pointer may be NULL to skip that array. EINVAL when entries
+ * are requested from a COUNT_ONLY or SINGLES_ONLY table that has none. */
+tbsci_status tbsci_tables_export(tbsci_ctx *ctx, const tbsci_tables *t, int64_t *off1,
+                                 tbsci_single_link *ent1, int64_t *off2, tbsci_double_link *ent2);
+void tbsci_tables_destroy(tbsci_tables *t);
+
+/* ----------------------------------------------------------- Hamiltonian */
+
+/* Creates a Hamiltonian from HOST integrals (the FCIDUMP content the paper
+ * reads, Sec. III.A): h[norb*norb] row-major one-electron integrals and
+ * eri[norb^4] two-electron integrals in chemists' notation (ij|kl) at
+ * ((i*n + j)*n + k)*n + l, plus the constant ecore. H = ecore +
+ * sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps).
+ * Errors: EINVAL when norb is outside 1..64, h is not symmetric or eri lacks
+ * the 8-fold symmetry of real orbitals (tolerance 1e-12 absolute); ENOMEM; ECUDA. */
+tbsci_status tbsci_hamiltonian_create(tbsci_ctx *ctx, int norb, const double *h, const double *eri,
+                                      double ecore, tbsci_ham **out);
+void tbsci_hamiltonian_destroy(tbsci_ham *ham);
+
+/* Prepares (and caches inside `ham`) the per-space data sigma needs: string
+ * Hamiltonian values of every link, per-string energies, the beta Coulomb
+ * table and the work schedules. Called implicitly by tbsci_sigma; exposed to
+ * keep set-up out of timed regions. `a` and `b` must have double links and
+ * the same norb as `ham`. Errors: EINVAL, ENOMEM, ECUDA. */
+tbsci_status tbsci_prepare(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b);
+
+/* sigma = H.c over the space a x b (Sec. II.B, Eq. 7, on one device; the six
+ * Slater-Condon classes of Sec. II.C, Eq. 8 and Algorithm 1). c and sigma are
+ * DEVICE arrays [nvec][l_a][l_b] of `dtype`, must not overlap; sigma is
+ * overwritten. Work is enqueued on `stream`; the call returns without waiting.
+ * Errors: EINVAL (null pointers, nvec < 1, norb mismatch, tables without
+ * double links), ENOMEM, ECUDA. */
+tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                         const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream);
+
+/* Same product with HOST vectors: copies c in, evaluates in FP64, copies sigma
+ * out and returns when done (uses a device buffer owned by the context). */
+tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
+                              const tbsci_tables *b, const double *c, double *sigma, int nvec);
+
+/* Diagonal H_KK (the [0,0] class, Sec. II.C) into the DEVICE array diag[l_a*l_b]
+ * (FP64), enqueued on `stream`. */
+tbsci_status tbsci_diagonal(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                            double *diag, tbsci_stream stream);
+
+/* Work counts of one sigma per vector: nnz = number of non-zero H_IJ of the
+ * space (each costs one multiply-add per vector), and the split by class. */
+typedef struct tbsci_sigma_counts {
+    int64_t ndet;
+    int64_t nnz;         /* total non-zeros of H */
+    int64_t nnz_aa;      /* alpha singles + doubles (classes [1,0] and [2,0]) */
+    int64_t nnz_bb;      /* beta singles + doubles ([0,1], [0,2]) */
+    int64_t nnz_ab;      /* alpha-single x beta-single ([1,1]) */
+    int64_t bytes_tables;
+} tbsci_sigma_counts;
+tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
+                                    const tbsci_tables *b, tbsci_sigma_counts *out);
+
+/* -------------------------------------------------------------- Davidson */
+
+typedef struct tbsci_davidson_opts {
+    int max_subspace;    /* basis size before restart; 0 -> max(8*nroots, nroots+2) */
+    int max_iter;        /* 0 -> 300 */
+    double tol_energy;   /* |theta - theta_prev| per root; 0 -> 1e-9 */
+    double tol_residual; /* ||r||_2 per root; 0 -> 1e-5 */
+    int mixed;           /* 0: FP64 sigma throughout. 1: FP32 sigma until converged
+                            to tol_mixed, then FP64 sigma refinement to the FP64
+                            tolerances; everything else in FP64 */
+    double tol_mixed_residual; /* residual target of the FP32 phase; 0 -> 1e-3 */
+    tbsci_stream stream; /* stream for all work; NULL -> the context's stream */
+} tbsci_davidson_opts;
+
+typedef struct tbsci_davidson_info {
+    int iterations;
+    int converged;
+    int nsigma;          /* sigma vector evaluations, FP64 + FP32 */
+    int nsigma_f32;
+    int iterations_f32;
+    double residual[8];  /* final ||r|| per root (first 8) */
+    double energy_f32[8];/* energies at the end of the FP32 phase (mixed mode) */
+    double seconds_total;
+    double seconds_sigma;
+} tbsci_davidson_info;
+
+/* Lowest nroots (1..8) eigenpairs of H on a x b by standard Davidson (Sec. III.A)
+ * with restart to the Ritz vectors when the basis is full (Sec. III.C). Guess:
+ * unit vectors at the nroots lowest H_KK (ties by K). Each iteration: Rayleigh
+ * matrix, its eigenpairs, Ritz vectors and residuals, stop when every root has
+ * |dE| < tol_energy and ||r|| < tol_residual, else precondition residuals by
+ * (theta - H_KK)^-1 (|denominator| clamped at 1e-8), orthonormalise twice
+ * against the basis (FP64 Gram-Schmidt) and add. energies: HOST array
+ * [nroots]. vecs: DEVICE array [nroots][l_a][l_b] FP64 or NULL.
+ * Errors: EINVAL, ENOMEM, ECUDA; ENOCONV when max_iter is reached (energies
+ * and vecs hold the last estimates). Blocks until done. */
+tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                            int nroots, const tbsci_davidson_opts *opts, double *energies, double *vecs,
+                            tbsci_davidson_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TBSCI_H */

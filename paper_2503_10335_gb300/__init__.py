@@ -1,0 +1,117 @@
+"""GB300 TBSCI: sigma = H.c over a tensor-product bitstring space and the
+Davidson solver that drives it (arXiv 2503.10335, Sec. II), on one GPU.
+
+The compute path is libtbsci.so (CUDA for sm_103a, C ABI in include/tbsci.h);
+this package only marshals arguments to it. ``Space`` bundles the handles of
+one problem (strings, link tables, Hamiltonian) for convenience.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+
+# the C entry points (same names) and status / dtype constants
+for _n in dir(B):
+    if _n.startswith(("tbsci_", "TBSCI_")):
+        globals()[_n] = getattr(B, _n)
+del _n
+
+__all__ = ["Context", "Space", "B"] + [n for n in dir(B) if n.startswith(("tbsci_", "TBSCI_"))]
+
+
+class Context:
+    """A libtbsci context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.handle = B.tbsci_create(device)
+        self.device = device
+
+    def close(self):
+        if self.handle is not None:
+            B.tbsci_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Space:
+    """One TPB problem: alpha/beta string sets (selected or full), their link
+    tables, and a Hamiltonian. ``alpha`` / ``beta``: host uint64 arrays or None
+    for the full string space."""
+
+    def __init__(self, ctx: Context, norb, nalpha, nbeta, h, eri, ecore=0.0, alpha=None, beta=None,
+                 prepare=True):
+        self.ctx = ctx
+        c = ctx.handle
+        self.norb, self.nalpha, self.nbeta = int(norb), int(nalpha), int(nbeta)
+        self._handles = []
+        self.sa = B.tbsci_build_strings(c, norb, nalpha, alpha)
+        self._handles.append((B.tbsci_strings_destroy, self.sa))
+        self.sb = B.tbsci_build_strings(c, norb, nbeta, beta)
+        self._handles.append((B.tbsci_strings_destroy, self.sb))
+        self.ta = B.tbsci_build_excitation_tables(c, self.sa, 0)
+        self._handles.append((B.tbsci_tables_destroy, self.ta))
+        self.tb = B.tbsci_build_excitation_tables(c, self.sb, 0)
+        self._handles.append((B.tbsci_tables_destroy, self.tb))
+        self.ham = B.tbsci_hamiltonian_create(c, h, eri, ecore)
+        self._handles.append((B.tbsci_hamiltonian_destroy, self.ham))
+        self.la = B.tbsci_strings_count(self.sa)
+        self.lb = B.tbsci_strings_count(self.sb)
+        self.ndet = self.la * self.lb
+        if prepare:
+            B.tbsci_prepare(c, self.ham, self.ta, self.tb)
+
+    def strings(self):
+        return B.tbsci_strings_export(self.ctx.handle, self.sa), B.tbsci_strings_export(self.ctx.handle, self.sb)
+
+    def sigma(self, c, out=None, stream=None):
+        """sigma = H c for a device tensor ``c`` [nvec, la, lb] (float64 or float32)."""
+        import torch
+        nvec = c.shape[0] if c.dim() == 3 else 1
+        assert c.is_cuda and c.is_contiguous() and c.numel() == nvec * self.ndet
+        if out is None:
+            out = torch.empty_like(c)
+        dt = B.TBSCI_F64 if c.dtype == torch.float64 else B.TBSCI_F32
+        B.tbsci_sigma(self.ctx.handle, self.ham, self.ta, self.tb, c, out, nvec, dt, stream)
+        return out
+
+    def sigma_host(self, c: np.ndarray) -> np.ndarray:
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        nvec = c.shape[0] if c.ndim == 3 else 1
+        out = np.empty_like(c)
+        B.tbsci_sigma_host(self.ctx.handle, self.ham, self.ta, self.tb, c, out, nvec)
+        return out
+
+    def diagonal(self, stream=None):
+        import torch
+        d = torch.empty(self.ndet, dtype=torch.float64, device="cuda:%d" % self.ctx.device)
+        B.tbsci_diagonal(self.ctx.handle, self.ham, self.ta, self.tb, d, stream)
+        return d
+
+    def counts(self) -> dict:
+        return B.tbsci_sigma_counts_get(self.ctx.handle, self.ham, self.ta, self.tb)
+
+    def davidson(self, nroots, want_vectors=False, **kw):
+        import torch
+        vecs = None
+        if want_vectors:
+            vecs = torch.empty((nroots, self.la, self.lb), dtype=torch.float64,
+                               device="cuda:%d" % self.ctx.device)
+        e, info = B.tbsci_davidson(self.ctx.handle, self.ham, self.ta, self.tb, nroots, vecs=vecs, **kw)
+        return (e, info, vecs) if want_vectors else (e, info)
+
+    def close(self):
+        for fn, h in reversed(self._handles):
+            fn(h)
+        self._handles = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

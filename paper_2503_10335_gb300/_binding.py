@@ -1,0 +1,277 @@
+"""ctypes binding of libtbsci (include/tbsci.h): argument marshalling only.
+
+Every function named ``tbsci_*`` here calls the C entry point of the same name;
+all computation runs in the library's CUDA kernels. Device arrays are torch
+tensors (their ``data_ptr()`` is passed), streams are torch CUDA streams. The
+binding raises ``TbsciError`` on any non-OK status and ``RuntimeError`` when the
+library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtbsci.so")
+
+TBSCI_OK, TBSCI_EINVAL, TBSCI_ENOMEM, TBSCI_ECUDA, TBSCI_ENOCONV, TBSCI_EAGAIN, TBSCI_ETIMEOUT, TBSCI_EBUSY = range(8)
+TBSCI_F64, TBSCI_F32 = 0, 1
+TBSCI_TABLES_SINGLES_ONLY, TBSCI_TABLES_COUNT_ONLY = 1, 2
+
+# exported names declared in include/tbsci.h
+EXPORTS = [
+    "tbsci_create", "tbsci_destroy", "tbsci_last_error", "tbsci_status_string",
+    "tbsci_build_strings", "tbsci_strings_count", "tbsci_strings_export", "tbsci_strings_destroy",
+    "tbsci_build_excitation_tables", "tbsci_tables_counts", "tbsci_tables_export", "tbsci_tables_destroy",
+    "tbsci_hamiltonian_create", "tbsci_hamiltonian_destroy", "tbsci_prepare", "tbsci_sigma",
+    "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson",
+]
+
+
+class SingleLink(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_int32), ("sign", ctypes.c_int8), ("p", ctypes.c_uint8),
+                ("q", ctypes.c_uint8), ("pad", ctypes.c_uint8)]
+
+
+class DoubleLink(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_int32), ("sign", ctypes.c_int8), ("p", ctypes.c_uint8),
+                ("r", ctypes.c_uint8), ("q", ctypes.c_uint8), ("s", ctypes.c_uint8),
+                ("pad", ctypes.c_uint8 * 3)]
+
+
+SINGLE_DTYPE = np.dtype([("target", "<i4"), ("sign", "i1"), ("p", "u1"), ("q", "u1"), ("pad", "u1")])
+DOUBLE_DTYPE = np.dtype([("target", "<i4"), ("sign", "i1"), ("p", "u1"), ("r", "u1"), ("q", "u1"),
+                         ("s", "u1"), ("pad", "u1", (3,))])
+assert SINGLE_DTYPE.itemsize == 8 and DOUBLE_DTYPE.itemsize == 12
+
+
+class SigmaCounts(ctypes.Structure):
+    _fields_ = [("ndet", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_aa", ctypes.c_int64),
+                ("nnz_bb", ctypes.c_int64), ("nnz_ab", ctypes.c_int64), ("bytes_tables", ctypes.c_int64)]
+
+
+class DavidsonOpts(ctypes.Structure):
+    _fields_ = [("max_subspace", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol_energy", ctypes.c_double),
+                ("tol_residual", ctypes.c_double), ("mixed", ctypes.c_int),
+                ("tol_mixed_residual", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class DavidsonInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("nsigma", ctypes.c_int),
+                ("nsigma_f32", ctypes.c_int), ("iterations_f32", ctypes.c_int),
+                ("residual", ctypes.c_double * 8), ("energy_f32", ctypes.c_double * 8),
+                ("seconds_total", ctypes.c_double), ("seconds_sigma", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(iterations=self.iterations, converged=bool(self.converged), nsigma=self.nsigma,
+                    nsigma_f32=self.nsigma_f32, iterations_f32=self.iterations_f32,
+                    residual=list(self.residual), energy_f32=list(self.energy_f32),
+                    seconds_total=self.seconds_total, seconds_sigma=self.seconds_sigma)
+
+
+class TbsciError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("tbsci status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads libtbsci.so (raises if it has not been built). An explicit ``path``
+    loads that file without caching it."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libtbsci.so is not built (%s); run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "tbsci_create": ([I, PP], I),
+        "tbsci_destroy": ([P], None),
+        "tbsci_last_error": ([P], ctypes.c_char_p),
+        "tbsci_status_string": ([I], ctypes.c_char_p),
+        "tbsci_build_strings": ([P, I, I, P, I64, PP], I),
+        "tbsci_strings_count": ([P, ctypes.POINTER(I64)], I),
+        "tbsci_strings_export": ([P, P, P], I),
+        "tbsci_strings_destroy": ([P], None),
+        "tbsci_build_excitation_tables": ([P, P, I, PP], I),
+        "tbsci_tables_counts": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64)], I),
+        "tbsci_tables_export": ([P, P, P, P, P, P], I),
+        "tbsci_tables_destroy": ([P], None),
+        "tbsci_hamiltonian_create": ([P, I, P, P, D, PP], I),
+        "tbsci_hamiltonian_destroy": ([P], None),
+        "tbsci_prepare": ([P, P, P, P], I),
+        "tbsci_sigma": ([P, P, P, P, P, P, I, I, P], I),
+        "tbsci_sigma_host": ([P, P, P, P, P, P, I], I),
+        "tbsci_diagonal": ([P, P, P, P, P, P], I),
+        "tbsci_sigma_counts_get": ([P, P, P, P, ctypes.POINTER(SigmaCounts)], I),
+        "tbsci_davidson": ([P, P, P, P, I, ctypes.POINTER(DavidsonOpts), P, P, ctypes.POINTER(DavidsonInfo)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(ctx, st):
+    if st != TBSCI_OK:
+        msg = load().tbsci_last_error(ctx).decode() if ctx else ""
+        raise TbsciError(st, msg)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- handles
+
+def tbsci_create(device: int = 0):
+    h = ctypes.c_void_p()
+    st = load().tbsci_create(device, ctypes.byref(h))
+    if st != TBSCI_OK:
+        raise TbsciError(st, "tbsci_create(%d) failed" % device)
+    return h
+
+
+def tbsci_destroy(ctx):
+    load().tbsci_destroy(ctx)
+
+
+def tbsci_last_error(ctx) -> str:
+    return load().tbsci_last_error(ctx).decode()
+
+
+def tbsci_build_strings(ctx, norb: int, nelec: int, selected=None):
+    out = ctypes.c_void_p()
+    if selected is None:
+        st = load().tbsci_build_strings(ctx, norb, nelec, None, 0, ctypes.byref(out))
+    else:
+        sel = np.ascontiguousarray(np.asarray(selected, dtype=np.uint64))
+        st = load().tbsci_build_strings(ctx, norb, nelec, _ptr(sel), len(sel), ctypes.byref(out))
+    _check(ctx, st)
+    return out
+
+
+def tbsci_strings_count(s) -> int:
+    c = ctypes.c_int64()
+    st = load().tbsci_strings_count(s, ctypes.byref(c))
+    if st:
+        raise TbsciError(st, "strings_count")
+    return c.value
+
+
+def tbsci_strings_export(ctx, s) -> np.ndarray:
+    out = np.zeros(tbsci_strings_count(s), dtype=np.uint64)
+    _check(ctx, load().tbsci_strings_export(ctx, s, _ptr(out)))
+    return out
+
+
+def tbsci_strings_destroy(s):
+    load().tbsci_strings_destroy(s)
+
+
+def tbsci_build_excitation_tables(ctx, strings, flags: int = 0):
+    out = ctypes.c_void_p()
+    _check(ctx, load().tbsci_build_excitation_tables(ctx, strings, flags, ctypes.byref(out)))
+    return out
+
+
+def tbsci_tables_counts(t):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    st = load().tbsci_tables_counts(t, ctypes.byref(a), ctypes.byref(b))
+    if st:
+        raise TbsciError(st, "tables_counts")
+    return a.value, b.value
+
+
+def tbsci_tables_export(ctx, t, nrows: int, singles=True, doubles=True):
+    """Returns ``(off1, ent1, off2, ent2)`` as numpy arrays (structured entries)."""
+    n1, n2 = tbsci_tables_counts(t)
+    off1 = np.zeros(nrows + 1, dtype=np.int64)
+    off2 = np.zeros(nrows + 1, dtype=np.int64) if doubles else None
+    e1 = np.zeros(n1, dtype=SINGLE_DTYPE) if singles else None
+    e2 = np.zeros(n2, dtype=DOUBLE_DTYPE) if doubles else None
+    _check(ctx, load().tbsci_tables_export(ctx, t, _ptr(off1), _ptr(e1), _ptr(off2), _ptr(e2)))
+    return off1, e1, off2, e2
+
+
+def tbsci_tables_destroy(t):
+    load().tbsci_tables_destroy(t)
+
+
+def tbsci_hamiltonian_create(ctx, h, eri, ecore: float = 0.0):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    n = h.shape[0]
+    out = ctypes.c_void_p()
+    _check(ctx, load().tbsci_hamiltonian_create(ctx, n, _ptr(h), _ptr(eri), float(ecore), ctypes.byref(out)))
+    return out
+
+
+def tbsci_hamiltonian_destroy(ham):
+    load().tbsci_hamiltonian_destroy(ham)
+
+
+def tbsci_prepare(ctx, ham, ta, tb):
+    _check(ctx, load().tbsci_prepare(ctx, ham, ta, tb))
+
+
+def tbsci_sigma(ctx, ham, ta, tb, c, sigma, nvec: int, dtype: int = TBSCI_F64, stream=None):
+    """sigma <- H c on device tensors [nvec][la][lb] (F64 or F32)."""
+    _check(ctx, load().tbsci_sigma(ctx, ham, ta, tb, _ptr(c), _ptr(sigma), int(nvec), int(dtype), _stream(stream)))
+
+
+def tbsci_sigma_host(ctx, ham, ta, tb, c: np.ndarray, sigma: np.ndarray, nvec: int):
+    """sigma <- H c with host FP64 arrays (copies inside the call)."""
+    assert c.dtype == np.float64 and sigma.dtype == np.float64
+    assert c.flags.c_contiguous and sigma.flags.c_contiguous
+    _check(ctx, load().tbsci_sigma_host(ctx, ham, ta, tb, _ptr(c), _ptr(sigma), int(nvec)))
+
+
+def tbsci_diagonal(ctx, ham, ta, tb, diag, stream=None):
+    _check(ctx, load().tbsci_diagonal(ctx, ham, ta, tb, _ptr(diag), _stream(stream)))
+
+
+def tbsci_sigma_counts_get(ctx, ham, ta, tb) -> dict:
+    c = SigmaCounts()
+    _check(ctx, load().tbsci_sigma_counts_get(ctx, ham, ta, tb, ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in SigmaCounts._fields_}
+
+
+def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max_iter=0, tol_energy=0.0,
+                   tol_residual=0.0, mixed=False, tol_mixed_residual=0.0, stream=None, check=True):
+    """Lowest ``nroots`` energies (numpy) and the info dict; ``vecs`` (device FP64
+    tensor [nroots][la][lb]) receives the eigenvectors when given."""
+    o = DavidsonOpts(max_subspace, max_iter, tol_energy, tol_residual, 1 if mixed else 0, tol_mixed_residual,
+                     None if stream is None else _stream(stream).value)
+    e = np.zeros(nroots)
+    info = DavidsonInfo()
+    st = load().tbsci_davidson(ctx, ham, ta, tb, nroots, ctypes.byref(o), _ptr(e), _ptr(vecs), ctypes.byref(info))
+    if check or st not in (TBSCI_OK, TBSCI_ENOCONV):
+        _check(ctx, st)
+    d = info.as_dict()
+    d["status"] = st
+    return e, d

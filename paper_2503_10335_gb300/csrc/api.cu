@@ -1,0 +1,300 @@
+// extern "C" entry points of libtbsci (declared in include/tbsci.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace tbsci {
+
+tbsci_status fail(tbsci_ctx *ctx, tbsci_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+}  // namespace tbsci
+
+using namespace tbsci;
+
+#define TB_GUARD_CTX(ctx)                                    \
+    do {                                                     \
+        if (!(ctx)) return TBSCI_EINVAL;                     \
+        cudaError_t e_ = cudaSetDevice((ctx)->device);       \
+        if (e_ != cudaSuccess)                               \
+            return fail((ctx), TBSCI_ECUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" {
+
+const char *tbsci_status_string(tbsci_status st) {
+    switch (st) {
+        case TBSCI_OK: return "ok";
+        case TBSCI_EINVAL: return "invalid argument";
+        case TBSCI_ENOMEM: return "out of memory";
+        case TBSCI_ECUDA: return "CUDA error";
+        case TBSCI_ENOCONV: return "not converged";
+        case TBSCI_EAGAIN: return "try again";
+        case TBSCI_ETIMEOUT: return "timed out";
+        case TBSCI_EBUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+tbsci_status tbsci_create(int device, tbsci_ctx **out) {
+    if (!out) return TBSCI_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return TBSCI_EINVAL;
+    tbsci_ctx *ctx = new (std::nothrow) tbsci_ctx();
+    if (!ctx) return TBSCI_ENOMEM;
+    ctx->device = device;
+    auto bad = [&](cudaError_t e) {
+        if (e == cudaSuccess) return false;
+        delete ctx;
+        return true;
+    };
+    if (bad(cudaSetDevice(device))) return TBSCI_ECUDA;
+    cudaDeviceProp prop;
+    if (bad(cudaGetDeviceProperties(&prop, device))) return TBSCI_ECUDA;
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    if (bad(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking))) return TBSCI_ECUDA;
+    // binomials by Pascal's rule (no intermediate overflow up to C(64, 32))
+    std::vector<int64_t> B(65 * 65, 0);
+    for (int m = 0; m <= 64; ++m) {
+        B[m * 65] = 1;
+        for (int k = 1; k <= m; ++k) B[m * 65 + k] = B[(m - 1) * 65 + k - 1] + (k <= m - 1 ? B[(m - 1) * 65 + k] : 0);
+    }
+    if (bad(ctx->d_binom.alloc(B.size()))) return TBSCI_ENOMEM;
+    if (bad(cudaMemcpy(ctx->d_binom.p, B.data(), B.size() * sizeof(int64_t), cudaMemcpyHostToDevice))) return TBSCI_ECUDA;
+    *out = ctx;
+    return TBSCI_OK;
+}
+
+void tbsci_destroy(tbsci_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->host_c.release();
+    ctx->host_s.release();
+    ctx->d_binom.release();
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *tbsci_last_error(const tbsci_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+tbsci_status tbsci_build_strings(tbsci_ctx *ctx, int norb, int nelec, const uint64_t *selected, int64_t nsel,
+                                 tbsci_strings **out) {
+    TB_GUARD_CTX(ctx);
+    if (!out) return fail(ctx, TBSCI_EINVAL, "out is NULL");
+    *out = nullptr;
+    tbsci_strings *s = new (std::nothrow) tbsci_strings();
+    if (!s) return fail(ctx, TBSCI_ENOMEM, "host allocation failed");
+    tbsci_status st = strings_build(ctx, norb, nelec, selected, nsel, s);
+    if (st != TBSCI_OK) {
+        delete s;
+        return st;
+    }
+    *out = s;
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_strings_count(const tbsci_strings *s, int64_t *count) {
+    if (!s || !count) return TBSCI_EINVAL;
+    *count = s->count;
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_strings_export(tbsci_ctx *ctx, const tbsci_strings *s, uint64_t *out) {
+    TB_GUARD_CTX(ctx);
+    if (!s || !out) return fail(ctx, TBSCI_EINVAL, "null argument");
+    if (s->count > 0) TB_CUDA(ctx, cudaMemcpy(out, s->d_str.p, s->count * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return TBSCI_OK;
+}
+
+void tbsci_strings_destroy(tbsci_strings *s) {
+    if (!s) return;
+    if (s->ctx) cudaSetDevice(s->ctx->device);
+    delete s;
+}
+
+tbsci_status tbsci_build_excitation_tables(tbsci_ctx *ctx, const tbsci_strings *s, int flags, tbsci_tables **out) {
+    TB_GUARD_CTX(ctx);
+    if (!s || !out) return fail(ctx, TBSCI_EINVAL, "null argument");
+    *out = nullptr;
+    tbsci_tables *t = new (std::nothrow) tbsci_tables();
+    if (!t) return fail(ctx, TBSCI_ENOMEM, "host allocation failed");
+    t->id = ctx->next_id++;
+    tbsci_status st = tables_build(ctx, s, flags, t);
+    if (st != TBSCI_OK) {
+        delete t;
+        return st;
+    }
+    *out = t;
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_tables_counts(const tbsci_tables *t, int64_t *nsingle, int64_t *ndouble) {
+    if (!t) return TBSCI_EINVAL;
+    if (nsingle) *nsingle = t->nsingle;
+    if (ndouble) *ndouble = t->ndouble;
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_tables_export(tbsci_ctx *ctx, const tbsci_tables *t, int64_t *off1, tbsci_single_link *ent1,
+                                 int64_t *off2, tbsci_double_link *ent2) {
+    TB_GUARD_CTX(ctx);
+    if (!t) return fail(ctx, TBSCI_EINVAL, "null tables");
+    const bool stored = !(t->flags & TBSCI_TABLES_COUNT_ONLY);
+    const bool doubles = !(t->flags & TBSCI_TABLES_SINGLES_ONLY);
+    if (ent1 && !stored) return fail(ctx, TBSCI_EINVAL, "tables hold no single-link entries");
+    if (off2 && !doubles) return fail(ctx, TBSCI_EINVAL, "tables hold no double links");
+    if (ent2 && !(stored && doubles)) return fail(ctx, TBSCI_EINVAL, "tables hold no double-link entries");
+    if (off1) std::memcpy(off1, t->h_off1.data(), t->h_off1.size() * sizeof(int64_t));
+    if (off2) std::memcpy(off2, t->h_off2.data(), t->h_off2.size() * sizeof(int64_t));
+    if (ent1 && t->nsingle > 0)
+        TB_CUDA(ctx, cudaMemcpy(ent1, t->d_ent1.p, t->nsingle * sizeof(tbsci_single_link), cudaMemcpyDeviceToHost));
+    if (ent2 && t->ndouble > 0)
+        TB_CUDA(ctx, cudaMemcpy(ent2, t->d_ent2.p, t->ndouble * sizeof(tbsci_double_link), cudaMemcpyDeviceToHost));
+    return TBSCI_OK;
+}
+
+void tbsci_tables_destroy(tbsci_tables *t) {
+    if (!t) return;
+    if (t->ctx) cudaSetDevice(t->ctx->device);
+    delete t;
+}
+
+tbsci_status tbsci_hamiltonian_create(tbsci_ctx *ctx, int norb, const double *h, const double *eri, double ecore,
+                                      tbsci_ham **out) {
+    TB_GUARD_CTX(ctx);
+    if (!out || !h || !eri) return fail(ctx, TBSCI_EINVAL, "null argument");
+    *out = nullptr;
+    if (norb < 1 || norb > 64) return fail(ctx, TBSCI_EINVAL, "norb must be in 1..64");
+    const int n = norb;
+    const size_t n2 = (size_t)n * n, n4 = n2 * n2;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            if (!std::isfinite(h[i * n + j])) return fail(ctx, TBSCI_EINVAL, "h has a non-finite entry");
+            if (std::fabs(h[i * n + j] - h[j * n + i]) > 1e-12) return fail(ctx, TBSCI_EINVAL, "h is not symmetric");
+        }
+    auto E = [&](int i, int j, int k, int l) { return eri[(((size_t)i * n + j) * n + k) * n + l]; };
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k)
+                for (int l = 0; l < n; ++l) {
+                    double v = E(i, j, k, l);
+                    if (!std::isfinite(v)) return fail(ctx, TBSCI_EINVAL, "eri has a non-finite entry");
+                    if (std::fabs(v - E(j, i, k, l)) > 1e-12 || std::fabs(v - E(i, j, l, k)) > 1e-12 ||
+                        std::fabs(v - E(k, l, i, j)) > 1e-12)
+                        return fail(ctx, TBSCI_EINVAL, "eri lacks the 8-fold symmetry of real orbitals");
+                }
+    tbsci_ham *H = new (std::nothrow) tbsci_ham();
+    if (!H) return fail(ctx, TBSCI_ENOMEM, "host allocation failed");
+    H->ctx = ctx;
+    H->norb = n;
+    H->npair = n * (n + 1) / 2;
+    H->ecore = ecore;
+    H->h_h.assign(h, h + n2);
+    H->h_eri.assign(eri, eri + n4);
+    const int P = H->npair;
+    std::vector<double> V((size_t)P * P);
+    std::vector<float> Vf((size_t)P * P);
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q <= p; ++q)
+            for (int r = 0; r < n; ++r)
+                for (int s = 0; s <= r; ++s) {
+                    size_t idx = (size_t)pair_index(p, q) * P + pair_index(r, s);
+                    V[idx] = E(p, q, r, s);
+                    Vf[idx] = (float)V[idx];
+                }
+    auto cleanup = [&](tbsci_status st, const char *msg) {
+        delete H;
+        return fail(ctx, st, msg);
+    };
+    if (H->d_h.alloc(n2) != cudaSuccess || H->d_V.alloc(V.size()) != cudaSuccess ||
+        H->d_Vf.alloc(Vf.size()) != cudaSuccess || H->d_eri.alloc(n4) != cudaSuccess)
+        return cleanup(TBSCI_ENOMEM, "device allocation failed");
+    if (cudaMemcpy(H->d_h.p, h, n2 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_V.p, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_Vf.p, Vf.data(), Vf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(H->d_eri.p, eri, n4 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return cleanup(TBSCI_ECUDA, "copy of integrals failed");
+    *out = H;
+    return TBSCI_OK;
+}
+
+void tbsci_hamiltonian_destroy(tbsci_ham *ham) {
+    if (!ham) return;
+    if (ham->ctx) cudaSetDevice(ham->ctx->device);
+    delete ham;
+}
+
+tbsci_status tbsci_prepare(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b) {
+    TB_GUARD_CTX(ctx);
+    Plan *p = nullptr;
+    return plan_get(ctx, ham, a, b, &p);
+}
+
+tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b, const void *c,
+                         void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream) {
+    TB_GUARD_CTX(ctx);
+    if (!c || !sigma) return fail(ctx, TBSCI_EINVAL, "null vector pointer");
+    if (nvec < 1) return fail(ctx, TBSCI_EINVAL, "nvec must be >= 1");
+    if (c == sigma) return fail(ctx, TBSCI_EINVAL, "c and sigma must not overlap");
+    Plan *p = nullptr;
+    TB_TRY(plan_get(ctx, ham, a, b, &p));
+    return sigma_launch(ctx, ham, p, c, sigma, nvec, dtype, (cudaStream_t)stream);
+}
+
+tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                              const double *c, double *sigma, int nvec) {
+    TB_GUARD_CTX(ctx);
+    if (!c || !sigma) return fail(ctx, TBSCI_EINVAL, "null vector pointer");
+    if (nvec < 1) return fail(ctx, TBSCI_EINVAL, "nvec must be >= 1");
+    Plan *p = nullptr;
+    TB_TRY(plan_get(ctx, ham, a, b, &p));
+    const size_t n = (size_t)nvec * p->A.l * p->B.l;
+    if (ctx->host_c.n < n) {
+        TB_CUDA(ctx, ctx->host_c.alloc(n));
+        TB_CUDA(ctx, ctx->host_s.alloc(n));
+    }
+    cudaStream_t st = ctx->stream;
+    if (n > 0) TB_CUDA(ctx, cudaMemcpyAsync(ctx->host_c.p, c, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    TB_TRY(sigma_launch(ctx, ham, p, ctx->host_c.p, ctx->host_s.p, nvec, TBSCI_F64, st));
+    if (n > 0) TB_CUDA(ctx, cudaMemcpyAsync(sigma, ctx->host_s.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(ctx, cudaStreamSynchronize(st));
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_diagonal(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b, double *diag,
+                            tbsci_stream stream) {
+    TB_GUARD_CTX(ctx);
+    if (!diag) return fail(ctx, TBSCI_EINVAL, "null diag pointer");
+    Plan *p = nullptr;
+    TB_TRY(plan_get(ctx, ham, a, b, &p));
+    return diagonal_launch(ctx, ham, p, diag, (cudaStream_t)stream);
+}
+
+tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                                    tbsci_sigma_counts *out) {
+    TB_GUARD_CTX(ctx);
+    if (!out) return fail(ctx, TBSCI_EINVAL, "null out");
+    Plan *p = nullptr;
+    TB_TRY(plan_get(ctx, ham, a, b, &p));
+    *out = p->counts;
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b, int nroots,
+                            const tbsci_davidson_opts *opts, double *energies, double *vecs,
+                            tbsci_davidson_info *info) {
+    TB_GUARD_CTX(ctx);
+    if (!energies) return fail(ctx, TBSCI_EINVAL, "null energies");
+    Plan *p = nullptr;
+    TB_TRY(plan_get(ctx, ham, a, b, &p));
+    return davidson_run(ctx, ham, p, nroots, opts, energies, vecs, info);
+}
+
+}  // extern "C"

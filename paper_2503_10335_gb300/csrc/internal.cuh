@@ -1,0 +1,174 @@
+// Internal declarations shared by the CUDA translation units of libtbsci.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tbsci.h"
+
+namespace tbsci {
+
+// ------------------------------------------------------------ error plumbing
+
+struct Error {
+    tbsci_status st;
+    std::string msg;
+};
+
+// Records `msg` in the context and returns `st`.
+tbsci_status fail(tbsci_ctx *ctx, tbsci_status st, const std::string &msg);
+
+#define TB_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return ::tbsci::fail((ctx), TBSCI_ECUDA,                                         \
+                                 std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+#define TB_CHECK(ctx, cond, st, msg)                                                         \
+    do {                                                                                     \
+        if (!(cond)) return ::tbsci::fail((ctx), (st), (msg));                               \
+    } while (0)
+
+#define TB_TRY(expr)                                                                         \
+    do {                                                                                     \
+        tbsci_status s_ = (expr);                                                            \
+        if (s_ != TBSCI_OK) return s_;                                                       \
+    } while (0)
+
+// Device buffer owned by one object; freed in the destructor.
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t alloc(size_t count) {
+        release();
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc((void **)&p, count * sizeof(T));
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+}  // namespace tbsci
+
+// ------------------------------------------------------------- public objects
+
+struct tbsci_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    uint64_t next_id = 1;
+    // device buffers of tbsci_sigma_host
+    tbsci::DevBuf<double> host_c, host_s;
+    // binomial table C(m, k) for m, k in 0..64, row-major [65][65]
+    tbsci::DevBuf<int64_t> d_binom;
+};
+
+struct tbsci_strings {
+    tbsci_ctx *ctx = nullptr;
+    int norb = 0, nelec = 0;
+    int64_t count = 0;
+    bool full = false;  // the full C(norb, nelec) space (combinatorial rank applies)
+    tbsci::DevBuf<uint64_t> d_str;
+};
+
+struct tbsci_tables {
+    tbsci_ctx *ctx = nullptr;
+    uint64_t id = 0;
+    int norb = 0, nelec = 0, flags = 0;
+    int64_t count = 0;
+    bool full = false;
+    int64_t nsingle = 0, ndouble = 0;
+    tbsci::DevBuf<uint64_t> d_str;
+    tbsci::DevBuf<int64_t> d_off1, d_off2;
+    tbsci::DevBuf<tbsci_single_link> d_ent1;
+    tbsci::DevBuf<tbsci_double_link> d_ent2;
+    std::vector<int64_t> h_off1, h_off2;  // host copies of the row offsets
+};
+
+namespace tbsci {
+
+// Per-spin data of one prepared space (values depend on the Hamiltonian).
+struct SpinPlan {
+    int64_t l = 0;
+    int nelec = 0;
+    const uint64_t *d_str = nullptr;  // owned by the tables
+    const int64_t *d_soff = nullptr, *d_doff = nullptr;
+    DevBuf<int2> d_sci;      // singles: {target, 2*pair(p,q) + (sign < 0)}
+    DevBuf<double> d_sval;   // singles: signed string-Hamiltonian value
+    DevBuf<float> d_svalf;
+    DevBuf<int32_t> d_dcol;  // doubles: target
+    DevBuf<double> d_dval;   // doubles: signed value (pq|rs) - (ps|rq)
+    DevBuf<float> d_dvalf;
+    DevBuf<double> d_E;      // string energies
+    DevBuf<float> d_Ef;
+    std::vector<int64_t> h_soff, h_doff;
+};
+
+struct Plan {
+    uint64_t ida = 0, idb = 0;
+    int norb = 0, npair = 0;
+    SpinPlan A, B;
+    DevBuf<double> d_U;      // [npair][l_b]: sum_{r in occ(Ib)} (pair|rr)
+    DevBuf<float> d_Uf;
+    DevBuf<int32_t> d_permb; // beta columns ordered by single-link count (descending)
+    DevBuf<int32_t> d_rowsa; // alpha rows ordered by work (descending)
+    tbsci_sigma_counts counts{};
+};
+
+}  // namespace tbsci
+
+struct tbsci_ham {
+    tbsci_ctx *ctx = nullptr;
+    int norb = 0, npair = 0;
+    double ecore = 0.0;
+    tbsci::DevBuf<double> d_h, d_V, d_eri;  // h[n][n], V[npair][npair] = (pq|rs) pair-packed, eri[n^4]
+    tbsci::DevBuf<float> d_Vf;
+    std::vector<double> h_h, h_eri;
+    std::vector<std::unique_ptr<tbsci::Plan>> plans;
+};
+
+namespace tbsci {
+
+inline int pair_index(int p, int q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
+
+// strings.cu
+tbsci_status strings_build(tbsci_ctx *ctx, int norb, int nelec, const uint64_t *sel, int64_t nsel,
+                           tbsci_strings *out);
+// tables.cu
+tbsci_status tables_build(tbsci_ctx *ctx, const tbsci_strings *s, int flags, tbsci_tables *out);
+// plan.cu
+tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                      Plan **out);
+// sigma.cu
+tbsci_status sigma_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const void *c, void *s,
+                          int nvec, tbsci_dtype dt, cudaStream_t st);
+tbsci_status diagonal_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, double *diag,
+                             cudaStream_t st);
+
+// davidson.cu
+tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
+                          double *energies, double *vecs, tbsci_davidson_info *info);
+
+// Exclusive scan of n int64 counts into out[0..n] (out[n] = total), on stream st.
+tbsci_status scan_exclusive(tbsci_ctx *ctx, const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
+
+}  // namespace tbsci

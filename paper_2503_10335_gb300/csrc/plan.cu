@@ -1,0 +1,204 @@
+// Per-space preparation for sigma (the values of the [a,b] classes of Sec. II.C):
+//  - string energies  E(S) = sum_{i in S} h_ii + 1/2 sum_{i,j in S} [(ii|jj) - (ij|ji)]
+//    (the same-spin part of the stored [0,0] diagonal);
+//  - single-link values  sign * [h_pq + sum_{k in J} ((pq|kk) - (pk|kq))]
+//    (same-spin part of the [1,0] / [0,1] classes);
+//  - double-link values  sign * [(pq|rs) - (ps|rq)]  ([2,0] / [0,2]);
+//  - the beta Coulomb table U[pair(p,q)][Ib] = sum_{r in Ib} (pq|rr), which
+//    carries the opposite-spin part of [1,0] and of the diagonal;
+//  - schedules: beta columns ordered by their single-link count and alpha rows
+//    by their work, both descending, so warps and CTAs get even work.
+#include <algorithm>
+#include <numeric>
+
+#include "internal.cuh"
+
+namespace tbsci {
+
+namespace {
+
+__device__ __forceinline__ double eri_at(const double *__restrict__ eri, int n, int i, int j, int k, int l) {
+    return __ldg(eri + (((size_t)i * n + j) * n + k) * n + l);
+}
+
+__global__ void k_string_energy(const uint64_t *__restrict__ str, int64_t l, int n, const double *__restrict__ h,
+                                const double *__restrict__ eri, double *E, float *Ef) {
+    int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= l) return;
+    uint64_t s = str[w];
+    double e = 0.0;
+    for (uint64_t a = s; a; a &= a - 1) {
+        int i = __ffsll((long long)a) - 1;
+        e += h[i * n + i];
+        for (uint64_t b = s; b; b &= b - 1) {
+            int j = __ffsll((long long)b) - 1;
+            e += 0.5 * (eri_at(eri, n, i, i, j, j) - eri_at(eri, n, i, j, j, i));
+        }
+    }
+    E[w] = e;
+    Ef[w] = (float)e;
+}
+
+// one warp per source row; lanes over the row's single links
+__global__ void k_single_values(const uint64_t *__restrict__ str, int64_t l, int n, const int64_t *__restrict__ off,
+                                const tbsci_single_link *__restrict__ ent, const double *__restrict__ h,
+                                const double *__restrict__ eri, int2 *sci, double *val, float *valf) {
+    int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= l) return;
+    uint64_t J = str[row];
+    for (int64_t k = off[row] + lane; k < off[row + 1]; k += 32) {
+        tbsci_single_link e = ent[k];
+        int p = e.p, q = e.q;
+        double v = h[p * n + q];
+        for (uint64_t a = J; a; a &= a - 1) {
+            int kk = __ffsll((long long)a) - 1;
+            v += eri_at(eri, n, p, q, kk, kk) - eri_at(eri, n, p, kk, kk, q);
+        }
+        v *= (double)e.sign;
+        int pr = p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+        sci[k] = make_int2(e.target, 2 * pr + (e.sign < 0 ? 1 : 0));
+        val[k] = v;
+        valf[k] = (float)v;
+    }
+}
+
+__global__ void k_double_values(int64_t nd, int n, const tbsci_double_link *__restrict__ ent,
+                                const double *__restrict__ eri, int32_t *col, double *val, float *valf) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nd) return;
+    tbsci_double_link e = ent[k];
+    double v = (double)e.sign * (eri_at(eri, n, e.p, e.q, e.r, e.s) - eri_at(eri, n, e.p, e.s, e.r, e.q));
+    col[k] = e.target;
+    val[k] = v;
+    valf[k] = (float)v;
+}
+
+// U[pair][Ib] = sum_{r in occ(Ib)} V[pair][rr]
+__global__ void k_coulomb_table(const uint64_t *__restrict__ strb, int64_t lb, int npair, const double *__restrict__ V,
+                                double *U, float *Uf) {
+    int64_t ib = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int pr = blockIdx.y;
+    if (ib >= lb) return;
+    uint64_t s = strb[ib];
+    double u = 0.0;
+    for (; s; s &= s - 1) {
+        int r = __ffsll((long long)s) - 1;
+        u += V[(size_t)pr * npair + r * (r + 1) / 2 + r];
+    }
+    U[(size_t)pr * lb + ib] = u;
+    Uf[(size_t)pr * lb + ib] = (float)u;
+}
+
+tbsci_status build_spin(tbsci_ctx *ctx, const tbsci_ham *ham, const tbsci_tables *t, SpinPlan &sp, cudaStream_t st) {
+    const int n = ham->norb;
+    sp.l = t->count;
+    sp.nelec = t->nelec;
+    sp.d_str = t->d_str.p;
+    sp.d_soff = t->d_off1.p;
+    sp.d_doff = t->d_off2.p;
+    sp.h_soff = t->h_off1;
+    sp.h_doff = t->h_off2;
+    TB_CUDA(ctx, sp.d_E.alloc(sp.l));
+    TB_CUDA(ctx, sp.d_Ef.alloc(sp.l));
+    TB_CUDA(ctx, sp.d_sci.alloc(t->nsingle));
+    TB_CUDA(ctx, sp.d_sval.alloc(t->nsingle));
+    TB_CUDA(ctx, sp.d_svalf.alloc(t->nsingle));
+    TB_CUDA(ctx, sp.d_dcol.alloc(t->ndouble));
+    TB_CUDA(ctx, sp.d_dval.alloc(t->ndouble));
+    TB_CUDA(ctx, sp.d_dvalf.alloc(t->ndouble));
+    const double *eri = ham->d_eri.p;
+    if (sp.l > 0) {
+        k_string_energy<<<(unsigned)((sp.l + 127) / 128), 128, 0, st>>>(sp.d_str, sp.l, n, ham->d_h.p, eri, sp.d_E.p,
+                                                                       sp.d_Ef.p);
+        TB_CUDA(ctx, cudaGetLastError());
+        if (t->nsingle > 0) {
+            k_single_values<<<(unsigned)((sp.l * 32 + 255) / 256), 256, 0, st>>>(
+                sp.d_str, sp.l, n, t->d_off1.p, t->d_ent1.p, ham->d_h.p, eri, sp.d_sci.p, sp.d_sval.p, sp.d_svalf.p);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+        if (t->ndouble > 0) {
+            k_double_values<<<(unsigned)((t->ndouble + 255) / 256), 256, 0, st>>>(t->ndouble, n, t->d_ent2.p, eri,
+                                                                                 sp.d_dcol.p, sp.d_dval.p,
+                                                                                 sp.d_dvalf.p);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+    }
+    TB_CUDA(ctx, cudaStreamSynchronize(st));
+    return TBSCI_OK;
+}
+
+}  // namespace
+
+tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b, Plan **out) {
+    TB_CHECK(ctx, ham && a && b, TBSCI_EINVAL, "null handle");
+    for (auto &p : ham->plans)
+        if (p->ida == a->id && p->idb == b->id) {
+            *out = p.get();
+            return TBSCI_OK;
+        }
+    TB_CHECK(ctx, a->norb == ham->norb && b->norb == ham->norb, TBSCI_EINVAL,
+             "tables and Hamiltonian have different norb");
+    TB_CHECK(ctx, a->flags == 0 && b->flags == 0, TBSCI_EINVAL,
+             "sigma needs tables built with single and double links (flags = 0)");
+    cudaStream_t st = ctx->stream;
+    auto plan = std::make_unique<Plan>();
+    plan->ida = a->id;
+    plan->idb = b->id;
+    plan->norb = ham->norb;
+    plan->npair = ham->npair;
+    TB_TRY(build_spin(ctx, ham, a, plan->A, st));
+    TB_TRY(build_spin(ctx, ham, b, plan->B, st));
+    const int64_t la = a->count, lb = b->count;
+    TB_CUDA(ctx, plan->d_U.alloc((size_t)ham->npair * lb));
+    TB_CUDA(ctx, plan->d_Uf.alloc((size_t)ham->npair * lb));
+    if (lb > 0) {
+        dim3 grid((unsigned)((lb + 127) / 128), (unsigned)ham->npair);
+        k_coulomb_table<<<grid, 128, 0, st>>>(b->d_str.p, lb, ham->npair, ham->d_V.p, plan->d_U.p, plan->d_Uf.p);
+        TB_CUDA(ctx, cudaGetLastError());
+    }
+    // schedules
+    std::vector<int64_t> s1b(lb), idx_b(lb);
+    int64_t S1b = 0, D2b = 0;
+    for (int64_t i = 0; i < lb; ++i) {
+        s1b[i] = b->h_off1[i + 1] - b->h_off1[i];
+        S1b += s1b[i];
+        D2b += b->h_off2[i + 1] - b->h_off2[i];
+    }
+    std::iota(idx_b.begin(), idx_b.end(), 0);
+    std::stable_sort(idx_b.begin(), idx_b.end(), [&](int64_t x, int64_t y) { return s1b[x] > s1b[y]; });
+    std::vector<int32_t> permb(idx_b.begin(), idx_b.end());
+    std::vector<double> work(la);
+    std::vector<int64_t> idx_a(la);
+    int64_t S1a = 0, D2a = 0;
+    for (int64_t i = 0; i < la; ++i) {
+        int64_t s1 = a->h_off1[i + 1] - a->h_off1[i];
+        int64_t d2 = a->h_off2[i + 1] - a->h_off2[i];
+        S1a += s1;
+        D2a += d2;
+        work[i] = (double)(1 + s1) * (double)(lb + S1b) + (double)d2 * (double)lb + (double)D2b;
+    }
+    std::iota(idx_a.begin(), idx_a.end(), 0);
+    std::stable_sort(idx_a.begin(), idx_a.end(), [&](int64_t x, int64_t y) { return work[x] > work[y]; });
+    std::vector<int32_t> rowsa(idx_a.begin(), idx_a.end());
+    TB_CUDA(ctx, plan->d_permb.alloc(lb));
+    TB_CUDA(ctx, plan->d_rowsa.alloc(la));
+    if (lb > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_permb.p, permb.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (la > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_rowsa.p, rowsa.data(), la * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // work counts: non-zeros of H by class (Sec. II.C, Table I)
+    tbsci_sigma_counts &c = plan->counts;
+    c.ndet = la * lb;
+    c.nnz_aa = (S1a + D2a) * lb;
+    c.nnz_bb = (S1b + D2b) * la;
+    c.nnz_ab = S1a * S1b;
+    c.nnz = c.ndet + c.nnz_aa + c.nnz_bb + c.nnz_ab;
+    c.bytes_tables = (int64_t)(plan->A.d_sci.bytes() + plan->A.d_sval.bytes() + plan->A.d_dcol.bytes() +
+                               plan->A.d_dval.bytes() + plan->B.d_sci.bytes() + plan->B.d_sval.bytes() +
+                               plan->B.d_dcol.bytes() + plan->B.d_dval.bytes() + plan->d_U.bytes());
+    TB_CUDA(ctx, cudaStreamSynchronize(st));
+    *out = plan.get();
+    ham->plans.push_back(std::move(plan));
+    return TBSCI_OK;
+}
+
+}  // namespace tbsci

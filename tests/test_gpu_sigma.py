@@ -1,0 +1,173 @@
+"""GPU sigma = H.c vs the oracle (rows a3-a6), through the C ABI.
+
+Full element-by-element comparison on spaces the oracle finishes in seconds
+(several CTAs, ragged column counts, nvec that splits across launches), and at
+the full norb=16, 3,000 x 3,000 size on sampled rows in the launch
+configuration the bench times (FP64, 3 vectors)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_sigma_close
+from tbsci_inputs import WORKLOADS, random_vectors, selected_strings, synth_hamiltonian
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tb():
+    import paper_2503_10335_gb300 as tb
+    return tb
+
+
+@pytest.fixture(scope="module")
+def ctx(tb):
+    c = tb.Context(0)
+    yield c
+    c.close()
+
+
+def _case(tb, ctx, n, na, nb, acnt, bcnt, seed, ecore=0.0):
+    h, eri, _ = synth_hamiltonian(n, seed=seed)
+    asel = None if acnt is None else selected_strings(n, na, acnt, seed + 1)
+    bsel = None if bcnt is None else selected_strings(n, nb, bcnt, seed + 2)
+    sp = tb.Space(ctx, n, na, nb, h, eri, ecore, alpha=asel, beta=bsel)
+    osp = oracle.make_space(n, na, nb, asel, bsel)
+    assert (sp.la, sp.lb) == (osp.la, osp.lb)
+    return sp, osp, h, eri
+
+
+CASES = [
+    # n, na, nb, alpha count, beta count, nvec
+    (6, 3, 3, None, None, 1),
+    (8, 4, 4, None, None, 3),
+    (8, 4, 3, 40, None, 2),
+    (10, 5, 5, 120, 257, 5),     # 257 columns: a ragged tail past one 256-thread sweep
+    (10, 3, 5, None, 90, 4),
+    (12, 6, 6, 300, 300, 1),
+    (9, 1, 0, None, None, 2),    # one alpha electron, no beta: H = h
+    (7, 7, 2, None, None, 1),    # fully occupied alpha string
+    (14, 7, 7, 700, 650, 3),
+]
+
+
+@pytest.mark.parametrize("n,na,nb,acnt,bcnt,nvec", CASES)
+def test_sigma_f64_full_parity(tb, ctx, n, na, nb, acnt, bcnt, nvec):
+    import torch
+    sp, osp, h, eri = _case(tb, ctx, n, na, nb, acnt, bcnt, seed=100 + n, ecore=0.25)
+    C = random_vectors(nvec, sp.la, sp.lb, seed=n)
+    s = sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy()
+    ref, bound = oracle.sigma(osp, h, eri, 0.25, C, with_bound=True)
+    assert_sigma_close(s.reshape(nvec, -1), ref, bound)
+    sp.close()
+
+
+def test_sigma_f32_parity(tb, ctx):
+    import torch
+    sp, osp, h, eri = _case(tb, ctx, 12, 6, 6, 300, 280, seed=7)
+    C = random_vectors(2, sp.la, sp.lb, seed=8)
+    s = sp.sigma(torch.from_numpy(C).float().cuda()).double().cpu().numpy().reshape(2, -1)
+    # FP32 inputs: compare against the oracle applied to the same rounded vector
+    C32 = C.astype(np.float32).astype(np.float64)
+    ref, bound = oracle.sigma(osp, h, eri, 0.0, C32, with_bound=True)
+    # FP32 products and sums: |d| <= 64 * 2^-24 * (|H||c|) per element
+    assert_sigma_close(s, ref, bound, rel=64 * 2.0 ** -24, norm_rel=1e-5)
+    sp.close()
+
+
+def test_diagonal_parity(tb, ctx):
+    sp, osp, h, eri = _case(tb, ctx, 10, 5, 4, 100, None, seed=9)
+    d = sp.diagonal().cpu().numpy()
+    ref = oracle.diagonal(osp, h, eri, 0.0)
+    assert np.max(np.abs(d - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    sp.close()
+
+
+def test_sigma_host_equals_device_and_deterministic(tb, ctx):
+    import torch
+    sp, osp, h, eri = _case(tb, ctx, 10, 5, 5, 150, 150, seed=10)
+    C = random_vectors(2, sp.la, sp.lb, seed=11)
+    s1 = sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy()
+    s2 = sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy()
+    s3 = sp.sigma_host(C)
+    assert np.array_equal(s1, s2) and np.array_equal(s1, s3)
+    sp.close()
+
+
+def test_fci8_sigma(tb, ctx):
+    import torch
+    wl = WORKLOADS["fci8"]
+    h, eri, ecore = wl.hamiltonian()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore)
+    osp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta)
+    C = random_vectors(1, sp.la, sp.lb, seed=wl.seed_vec)
+    s = sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy()
+    ref, bound = oracle.sigma(osp, h, eri, ecore, C, with_bound=True)
+    assert_sigma_close(s.reshape(1, -1), ref, bound)
+    sp.close()
+
+
+def test_sel16_sigma_sampled_rows_full_size(tb, ctx):
+    """norb=16, 3,000 x 3,000 selected strings (9.0M determinants), FP64, 3
+    vectors in one call: the bench's workload and launch configuration. 4,000
+    seeded rows (whole rows of the first and last alpha strings included) are
+    recomputed by the oracle."""
+    import torch
+    wl = WORKLOADS["sel16"]
+    h, eri, ecore = wl.hamiltonian()
+    asel, bsel = wl.alpha_selection(), wl.beta_selection()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=asel, beta=bsel)
+    osp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, asel, bsel)
+    assert sp.ndet == 9_000_000
+    C = random_vectors(3, sp.la, sp.lb, seed=wl.seed_vec)
+    s = sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy().reshape(3, -1)
+    rng = np.random.default_rng(wl.seed_vec)
+    rows = np.unique(np.concatenate([rng.choice(sp.ndet, 3000, replace=False), np.arange(500),
+                                     np.arange(sp.ndet - 500, sp.ndet)]))
+    ref, bound = oracle.sigma(osp, h, eri, ecore, C.reshape(3, -1), rows=rows, with_bound=True)
+    assert_sigma_close(s[:, rows], ref, bound)
+    sp.close()
+
+
+def test_sigma_edge_cases(tb, ctx):
+    import torch
+    h, eri, _ = synth_hamiltonian(6, seed=12)
+    # empty selection: nothing to do, no error
+    sp = tb.Space(ctx, 6, 3, 3, h, eri, alpha=np.zeros(0, dtype=np.uint64))
+    assert sp.ndet == 0
+    c = torch.zeros((1, 0, sp.lb), dtype=torch.float64, device="cuda")
+    tb.tbsci_sigma(ctx.handle, sp.ham, sp.ta, sp.tb, c, torch.zeros_like(c), 1)
+    sp.close()
+    # a single determinant: sigma = H_00 c
+    sp, osp, h, eri = _case(tb, ctx, 6, 3, 3, 1, 1, seed=13)
+    C = np.array([[[1.5]]])
+    s = sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy()
+    assert abs(s[0, 0, 0] - 1.5 * oracle.diagonal(osp, h, eri, 0.0)[0]) < 1e-12
+    sp.close()
+
+
+def test_invalid_arguments(tb, ctx):
+    import torch
+    h, eri, _ = synth_hamiltonian(5, seed=14)
+    bad = h.copy()
+    bad[0, 1] += 1e-6
+    with pytest.raises(tb.B.TbsciError):
+        tb.tbsci_hamiltonian_create(ctx.handle, bad, eri)
+    e2 = eri.copy()
+    e2[0, 1, 2, 3] += 1e-6
+    with pytest.raises(tb.B.TbsciError):
+        tb.tbsci_hamiltonian_create(ctx.handle, h, e2)
+    sp = tb.Space(ctx, 5, 2, 2, h, eri)
+    c = torch.zeros((1, sp.la, sp.lb), dtype=torch.float64, device="cuda")
+    with pytest.raises(tb.B.TbsciError):
+        tb.tbsci_sigma(ctx.handle, sp.ham, sp.ta, sp.tb, c, c, 1)  # aliasing
+    with pytest.raises(tb.B.TbsciError):
+        tb.tbsci_sigma(ctx.handle, sp.ham, sp.ta, sp.tb, c, torch.zeros_like(c), 0)
+    # tables without doubles cannot drive sigma
+    s = tb.tbsci_build_strings(ctx.handle, 5, 2, None)
+    t = tb.tbsci_build_excitation_tables(ctx.handle, s, tb.TBSCI_TABLES_SINGLES_ONLY)
+    with pytest.raises(tb.B.TbsciError):
+        tb.tbsci_prepare(ctx.handle, sp.ham, t, t)
+    tb.tbsci_tables_destroy(t)
+    tb.tbsci_strings_destroy(s)
+    sp.close()
