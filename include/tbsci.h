@@ -184,13 +184,16 @@ tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_
 
 typedef struct tbsci_davidson_opts {
     int max_subspace;    /* basis size before restart; 0 -> max(8*nroots, nroots+2) */
-    int max_iter;        /* 0 -> 300 */
+    int restart_keep;    /* Ritz vectors kept at a restart; 0 -> max(nroots, max_subspace/2) */
+    int max_iter;        /* 0 -> 1000 */
     double tol_energy;   /* |theta - theta_prev| per root; 0 -> 1e-9 */
     double tol_residual; /* ||r||_2 per root; 0 -> 1e-5 */
-    int mixed;           /* 0: FP64 sigma throughout. 1: FP32 sigma until converged
-                            to tol_mixed, then FP64 sigma refinement to the FP64
+    int mixed;           /* 0: FP64 sigma throughout. 1: FP32 sigma until every
+                            residual is below tol_mixed_residual (or stops falling
+                            for 8 iterations), then restart from the roots' Ritz
+                            vectors with FP64 sigma and converge to the FP64
                             tolerances; everything else in FP64 */
-    double tol_mixed_residual; /* residual target of the FP32 phase; 0 -> 1e-3 */
+    double tol_mixed_residual; /* residual target of the FP32 phase; 0 -> 5e-5 */
     tbsci_stream stream; /* stream for all work; NULL -> the context's stream */
 } tbsci_davidson_opts;
 
@@ -207,7 +210,9 @@ typedef struct tbsci_davidson_info {
 } tbsci_davidson_info;
 
 /* Lowest nroots (1..8) eigenpairs of H on a x b by standard Davidson (Sec. III.A)
- * with restart to the Ritz vectors when the basis is full (Sec. III.C). Guess:
+ * with restart to the lowest restart_keep Ritz vectors when the basis is full
+ * (Sec. III.C). Memory: 2 * max_subspace + restart_keep + 3 * nroots FP64
+ * vectors (+ 2 * nroots FP32 in mixed mode). Guess:
  * unit vectors at the nroots lowest H_KK (ties by K). Each iteration: Rayleigh
  * matrix, its eigenpairs, Ritz vectors and residuals, stop when every root has
  * |dE| < tol_energy and ||r|| < tol_residual, else precondition residuals by

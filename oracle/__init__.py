@@ -248,7 +248,8 @@ def hamiltonian_dense(space: Space, h, eri, ecore) -> np.ndarray:
 
 # --------------------------------------------------------------- Davidson
 
-def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, max_iter=300):
+def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, max_iter=1000,
+             restart_keep=None):
     """Standard Davidson (Sec. III.A) for the lowest ``nroots`` eigenpairs.
 
     Steps, in order, each iteration: Rayleigh matrix G = V^T W; eigenpairs of G;
@@ -256,10 +257,11 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     root has |theta - theta_prev| < tol_e and ||r|| < tol_r; otherwise precondition
     each unconverged residual by (theta - H_KK)^-1 (denominators of magnitude
     below 1e-8 clamped to +-1e-8, zero -> +1e-8); when the subspace would exceed
-    ``max_subspace`` restart from the Ritz vectors (the paper's restart scheme,
-    Sec. III.C); orthogonalise the new directions twice against the basis and
-    each other, normalise, and drop those whose norm fell below 1e-10 of their
-    pre-projection norm.
+    ``max_subspace`` restart from the lowest ``restart_keep`` Ritz vectors
+    (default ``max(nroots, max_subspace // 2)``; the paper's restart scheme,
+    Sec. III.C, keeps a bounded number of vectors and says no more); orthogonalise
+    the new directions twice against the basis and each other, normalise, and
+    drop those whose norm fell below 1e-10 of their pre-projection norm.
 
     ``apply_h(V)`` maps ``[k, N]`` to ``[k, N]``. The guess is the ``nroots``
     unit vectors at the lowest diagonal entries, ties broken by index.
@@ -269,6 +271,8 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     N = len(diag)
     if max_subspace is None:
         max_subspace = max(8 * nroots, nroots + 2)
+    if restart_keep is None:
+        restart_keep = max(nroots, max_subspace // 2)
     order = np.lexsort((np.arange(N), diag))
     V = np.zeros((nroots, N))
     for k in range(nroots):
@@ -280,9 +284,9 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     for it in range(1, max_iter + 1):
         G = V @ W.T
         G = 0.5 * (G + G.T)
-        evals, Y = np.linalg.eigh(G)
+        evals, Yall = np.linalg.eigh(G)
         theta = evals[:nroots]
-        Y = Y[:, :nroots]
+        Y = Yall[:, :nroots]
         X = Y.T @ V
         WY = Y.T @ W
         R = WY - theta[:, None] * X
@@ -302,7 +306,8 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
             d[small] = np.where(d[small] < 0, -1e-8, 1e-8)
             T.append(R[k] / d)
         if V.shape[0] + len(T) > max_subspace:
-            V, W = X, WY
+            keep = min(restart_keep, V.shape[0])
+            V, W = Yall[:, :keep].T @ V, Yall[:, :keep].T @ W
         newV = []
         for t in T:
             t0 = np.linalg.norm(t)

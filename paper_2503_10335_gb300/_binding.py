@@ -53,7 +53,8 @@ class SigmaCounts(ctypes.Structure):
 
 
 class DavidsonOpts(ctypes.Structure):
-    _fields_ = [("max_subspace", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol_energy", ctypes.c_double),
+    _fields_ = [("max_subspace", ctypes.c_int), ("restart_keep", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("tol_energy", ctypes.c_double),
                 ("tol_residual", ctypes.c_double), ("mixed", ctypes.c_int),
                 ("tol_mixed_residual", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
@@ -262,10 +263,12 @@ def tbsci_sigma_counts_get(ctx, ham, ta, tb) -> dict:
 
 
 def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max_iter=0, tol_energy=0.0,
-                   tol_residual=0.0, mixed=False, tol_mixed_residual=0.0, stream=None, check=True):
+                   tol_residual=0.0, mixed=False, tol_mixed_residual=0.0, stream=None, check=True,
+                   restart_keep=0):
     """Lowest ``nroots`` energies (numpy) and the info dict; ``vecs`` (device FP64
     tensor [nroots][la][lb]) receives the eigenvectors when given."""
-    o = DavidsonOpts(max_subspace, max_iter, tol_energy, tol_residual, 1 if mixed else 0, tol_mixed_residual,
+    o = DavidsonOpts(max_subspace, restart_keep, max_iter, tol_energy, tol_residual, 1 if mixed else 0,
+                     tol_mixed_residual,
                      None if stream is None else _stream(stream).value)
     e = np.zeros(nroots)
     info = DavidsonInfo()

@@ -240,22 +240,24 @@ tbsci_status tbsci_prepare(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a
 tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b, const void *c,
                          void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream) {
     TB_GUARD_CTX(ctx);
-    if (!c || !sigma) return fail(ctx, TBSCI_EINVAL, "null vector pointer");
     if (nvec < 1) return fail(ctx, TBSCI_EINVAL, "nvec must be >= 1");
-    if (c == sigma) return fail(ctx, TBSCI_EINVAL, "c and sigma must not overlap");
     Plan *p = nullptr;
     TB_TRY(plan_get(ctx, ham, a, b, &p));
+    if (p->A.l * p->B.l == 0) return TBSCI_OK;  // empty space: nothing to read or write
+    if (!c || !sigma) return fail(ctx, TBSCI_EINVAL, "null vector pointer");
+    if (c == sigma) return fail(ctx, TBSCI_EINVAL, "c and sigma must not overlap");
     return sigma_launch(ctx, ham, p, c, sigma, nvec, dtype, (cudaStream_t)stream);
 }
 
 tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
                               const double *c, double *sigma, int nvec) {
     TB_GUARD_CTX(ctx);
-    if (!c || !sigma) return fail(ctx, TBSCI_EINVAL, "null vector pointer");
     if (nvec < 1) return fail(ctx, TBSCI_EINVAL, "nvec must be >= 1");
     Plan *p = nullptr;
     TB_TRY(plan_get(ctx, ham, a, b, &p));
     const size_t n = (size_t)nvec * p->A.l * p->B.l;
+    if (n == 0) return TBSCI_OK;
+    if (!c || !sigma) return fail(ctx, TBSCI_EINVAL, "null vector pointer");
     if (ctx->host_c.n < n) {
         TB_CUDA(ctx, ctx->host_c.alloc(n));
         TB_CUDA(ctx, ctx->host_s.alloc(n));
@@ -271,9 +273,10 @@ tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables
 tbsci_status tbsci_diagonal(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b, double *diag,
                             tbsci_stream stream) {
     TB_GUARD_CTX(ctx);
-    if (!diag) return fail(ctx, TBSCI_EINVAL, "null diag pointer");
     Plan *p = nullptr;
     TB_TRY(plan_get(ctx, ham, a, b, &p));
+    if (p->A.l * p->B.l == 0) return TBSCI_OK;
+    if (!diag) return fail(ctx, TBSCI_EINVAL, "null diag pointer");
     return diagonal_launch(ctx, ham, p, diag, (cudaStream_t)stream);
 }
 

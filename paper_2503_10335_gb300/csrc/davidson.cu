@@ -303,12 +303,14 @@ tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots
     tbsci_davidson_opts opt{};
     if (o) opt = *o;
     const int m_max = opt.max_subspace > 0 ? opt.max_subspace : std::max(8 * nroots, nroots + 2);
-    const int max_iter = opt.max_iter > 0 ? opt.max_iter : 300;
+    const int keep = opt.restart_keep > 0 ? opt.restart_keep : std::max(nroots, m_max / 2);
+    const int max_iter = opt.max_iter > 0 ? opt.max_iter : 1000;
     const double tol_e = opt.tol_energy > 0 ? opt.tol_energy : 1e-9;
     const double tol_r = opt.tol_residual > 0 ? opt.tol_residual : 1e-5;
-    const double tol_rm = opt.tol_mixed_residual > 0 ? opt.tol_mixed_residual : 1e-3;
+    const double tol_rm = opt.tol_mixed_residual > 0 ? opt.tol_mixed_residual : 5e-5;
     TB_CHECK(ctx, nroots >= 1 && nroots <= kMaxOut, TBSCI_EINVAL, "nroots must be in 1..8");
     TB_CHECK(ctx, m_max >= nroots + 1 && m_max <= kMaxBasis, TBSCI_EINVAL, "max_subspace must be in nroots+1..128");
+    TB_CHECK(ctx, keep >= nroots && keep < m_max, TBSCI_EINVAL, "restart_keep must be in nroots..max_subspace-1");
     Dav D;
     D.ctx = ctx;
     D.ham = ham;
@@ -318,11 +320,12 @@ tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots
     const int64_t N = D.N;
     TB_CHECK(ctx, N >= nroots, TBSCI_EINVAL, "space has fewer determinants than roots");
     D.nblocks = 2 * ctx->num_sms;
-    TB_CUDA(ctx, D.partial.alloc((size_t)D.nblocks * kMaxBasis * kMaxOut));
-    TB_CUDA(ctx, D.red.alloc(kMaxBasis * kMaxOut));
+    // dot partials: up to max_subspace x max_subspace products per block
+    TB_CUDA(ctx, D.partial.alloc((size_t)D.nblocks * kMaxBasis * kMaxBasis));
+    TB_CUDA(ctx, D.red.alloc(kMaxBasis * kMaxBasis));
     TB_CUDA(ctx, D.dY.alloc(kMaxBasis * kMaxOut));
     TB_CUDA(ctx, D.dtheta.alloc(kMaxOut));
-    DevBuf<double> V, W, X, WY, T, diag;
+    DevBuf<double> V, W, X, WY, T, diag, R;  // R: Ritz block of a thick restart
     TB_CUDA(ctx, V.alloc((size_t)m_max * N));
     TB_CUDA(ctx, W.alloc((size_t)m_max * N));
     TB_CUDA(ctx, X.alloc((size_t)nroots * N));
@@ -396,6 +399,8 @@ tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots
     std::vector<double> theta(nroots), theta_prev(nroots, INFINITY), rnorm(nroots, INFINITY);
     std::vector<double> e32(nroots, 0.0);
     int it = 0, it32 = 0;
+    double best32 = INFINITY;  // FP32 phase: smallest max-residual so far
+    int stall32 = 0;
     bool converged = false;
     tbsci_status result = TBSCI_OK;
     for (it = 1; it <= max_iter; ++it) {
@@ -418,11 +423,22 @@ tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots
         TB_CUDA(ctx, cudaMemcpyAsync(rnorm.data(), D.red.p, nroots * sizeof(double), cudaMemcpyDeviceToHost, st));
         TB_CUDA(ctx, cudaStreamSynchronize(st));
         bool ok = true;
+        double rmax = 0.0;
         for (int k = 0; k < nroots; ++k) {
             rnorm[k] = std::sqrt(rnorm[k]);
+            rmax = std::max(rmax, rnorm[k]);
             double dE = std::fabs(theta[k] - theta_prev[k]);
             if (f32) ok = ok && rnorm[k] < tol_rm;
             else ok = ok && dE < tol_e && rnorm[k] < tol_r;
+        }
+        if (f32) {
+            // leave the FP32 phase also when its residuals stop falling (FP32 noise floor)
+            if (rmax < 0.9 * best32) {
+                best32 = rmax;
+                stall32 = 0;
+            } else if (++stall32 >= 8) {
+                ok = true;
+            }
         }
         theta_prev = theta;
         if (ok && f32) {
@@ -444,9 +460,22 @@ tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots
         for (int k = 0; k < nroots; ++k)
             if (rnorm[k] >= (f32 ? tol_rm : tol_r)) todo.push_back(k);
         if (m + (int)todo.size() > m_max) {
-            TB_CUDA(ctx, cudaMemcpyAsync(V.p, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            TB_CUDA(ctx, cudaMemcpyAsync(W.p, WY.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            m = nroots;
+            // thick restart: keep the lowest `kk` Ritz vectors and their images
+            const int kk = std::min(keep, m);
+            if (!R.p) TB_CUDA(ctx, R.alloc((size_t)keep * N));
+            std::vector<double> Yk;
+            for (int half = 0; half < 2; ++half) {
+                double *src = half == 0 ? V.p : W.p;
+                for (int k0 = 0; k0 < kk; k0 += kMaxOut) {
+                    const int kc = std::min(kMaxOut, kk - k0);
+                    Yk.assign((size_t)m * kc, 0.0);
+                    for (int i = 0; i < m; ++i)
+                        for (int k = 0; k < kc; ++k) Yk[(size_t)i * kc + k] = Yv[(size_t)i * m + k0 + k];
+                    TB_TRY(D.lincomb(src, m, R.p + (size_t)k0 * N, kc, 0.0, Yk));
+                }
+                TB_CUDA(ctx, cudaMemcpyAsync(src, R.p, (size_t)kk * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            m = kk;
             TB_TRY(refresh_G(0, m));
         }
         const int m_old = m;

@@ -46,7 +46,7 @@ def test_small_selected_vs_dense(tb, ctx):
     osp = oracle.make_space(n, na, nb, asel, None)
     H = oracle.hamiltonian_dense(osp, h, eri, 0.1)
     w, U = np.linalg.eigh(H)
-    e, info, X = sp.davidson(4, want_vectors=True, max_subspace=12)
+    e, info, X = sp.davidson(4, want_vectors=True, max_subspace=16)
     assert info["converged"]
     assert np.max(np.abs(e - w[:4])) < 1e-8
     X = X.cpu().numpy().reshape(4, -1)
