@@ -225,6 +225,16 @@ tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *
                             int nroots, const tbsci_davidson_opts *opts, double *energies, double *vecs,
                             tbsci_davidson_info *info);
 
+/* Overlaps of FP64 DEVICE vectors: S[i*mb + j] = sum_K A[i][K] * B[j][K] for
+ * i < ma, j < mb, each vector n long (CI vectors of a space: n = l_a * l_b; the
+ * Rayleigh-matrix and Gram-Schmidt products of the Davidson of Sec. III.A). S is
+ * a HOST array [ma*mb]. Fixed grid and fixed reduction order: the result is
+ * run-to-run bit-identical. Scratch of (2 * SM count + 1) * ma * mb doubles is
+ * allocated and freed inside the call. Blocks until done.
+ * Errors: EINVAL (null pointers, ma or mb < 0, n < 0), ENOMEM, ECUDA. */
+tbsci_status tbsci_overlap(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n,
+                           double *S, tbsci_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = [
     "tbsci_build_strings", "tbsci_strings_count", "tbsci_strings_export", "tbsci_strings_destroy",
     "tbsci_build_excitation_tables", "tbsci_tables_counts", "tbsci_tables_export", "tbsci_tables_destroy",
     "tbsci_hamiltonian_create", "tbsci_hamiltonian_destroy", "tbsci_prepare", "tbsci_sigma",
-    "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson",
+    "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson", "tbsci_overlap",
 ]
 
 
@@ -114,6 +114,7 @@ def load(path: str | None = None):
         "tbsci_diagonal": ([P, P, P, P, P, P], I),
         "tbsci_sigma_counts_get": ([P, P, P, P, ctypes.POINTER(SigmaCounts)], I),
         "tbsci_davidson": ([P, P, P, P, I, ctypes.POINTER(DavidsonOpts), P, P, ctypes.POINTER(DavidsonInfo)], I),
+        "tbsci_overlap": ([P, P, I, P, I, I64, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -278,3 +279,14 @@ def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max
     d = info.as_dict()
     d["status"] = st
     return e, d
+
+
+def tbsci_overlap(ctx, A, B, stream=None) -> np.ndarray:
+    """S[i, j] = <A_i | B_j> for FP64 device tensors A [ma, ...] and B [mb, ...]
+    with the same number of elements per vector; returns a numpy [ma, mb]."""
+    ma, mb = int(A.shape[0]), int(B.shape[0])
+    n = int(A[0].numel()) if ma else 0
+    assert mb == 0 or int(B[0].numel()) == n
+    S = np.zeros((ma, mb))
+    _check(ctx, load().tbsci_overlap(ctx, _ptr(A), ma, _ptr(B), mb, n, _ptr(S), _stream(stream)))
+    return S

@@ -300,4 +300,10 @@ tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *
     return davidson_run(ctx, ham, p, nroots, opts, energies, vecs, info);
 }
 
+tbsci_status tbsci_overlap(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n, double *S,
+                           tbsci_stream stream) {
+    TB_GUARD_CTX(ctx);
+    return overlap_run(ctx, A, ma, B, mb, n, S, (cudaStream_t)stream);
+}
+
 }  // extern "C"

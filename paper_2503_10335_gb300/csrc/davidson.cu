@@ -526,4 +526,26 @@ tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots
     return result;
 }
 
+tbsci_status overlap_run(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n, double *S,
+                         cudaStream_t st) {
+    TB_CHECK(ctx, ma >= 0 && mb >= 0 && n >= 0, TBSCI_EINVAL, "tbsci_overlap: negative size");
+    if (ma == 0 || mb == 0) return TBSCI_OK;
+    TB_CHECK(ctx, A && B && S, TBSCI_EINVAL, "tbsci_overlap: null pointer");
+    TB_CHECK(ctx, (ma + kMA - 1) / kMA <= 65535 && (mb + kMB - 1) / kMB <= 65535, TBSCI_EINVAL,
+             "tbsci_overlap: too many vectors");
+    const int nblocks = 2 * ctx->num_sms;
+    const int ldp = ma * mb;
+    DevBuf<double> partial, red;
+    TB_CUDA(ctx, partial.alloc((size_t)nblocks * ldp));
+    TB_CUDA(ctx, red.alloc(ldp));
+    dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + kMB - 1) / kMB);
+    k_dots<<<grid, kDotThreads, 0, st>>>(A, ma, B, mb, n, partial.p, ldp);
+    TB_CUDA(ctx, cudaGetLastError());
+    k_reduce_partials<<<(ldp + 127) / 128, 128, 0, st>>>(partial.p, nblocks, ldp, ldp, red.p);
+    TB_CUDA(ctx, cudaGetLastError());
+    TB_CUDA(ctx, cudaMemcpyAsync(S, red.p, (size_t)ldp * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(ctx, cudaStreamSynchronize(st));
+    return TBSCI_OK;
+}
+
 }  // namespace tbsci

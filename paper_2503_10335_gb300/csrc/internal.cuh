@@ -168,6 +168,9 @@ tbsci_status diagonal_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *p
 tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
                           double *energies, double *vecs, tbsci_davidson_info *info);
 
+tbsci_status overlap_run(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n, double *S,
+                         cudaStream_t st);
+
 // Exclusive scan of n int64 counts into out[0..n] (out[n] = total), on stream st.
 tbsci_status scan_exclusive(tbsci_ctx *ctx, const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
 
