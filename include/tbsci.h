@@ -235,6 +235,27 @@ tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *
 tbsci_status tbsci_overlap(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n,
                            double *S, tbsci_stream stream);
 
+/* Allocation-free form of tbsci_overlap, for callers that must not allocate
+ * device memory while they run: for example a framework that has handed all
+ * free HBM to its own caching pool (a cudaMalloc would fail or break its
+ * accounting), or a latency-bound serving loop where cudaMalloc/cudaFree would
+ * synchronise the device and stall other streams. The paper has no counterpart.
+ *
+ * Same product as tbsci_overlap, but S is a DEVICE array [ma*mb] written on
+ * `stream`, and the call returns without waiting. The per-block partial sums
+ * live in a 2 MiB array of static device memory that the library holds on every
+ * GPU that loads it until the process exits; it limits ma * mb to 512
+ * (larger requests return EINVAL and launch nothing). Every partial is
+ * rewritten by each call, so nothing needs clearing between calls, but all calls
+ * share the one array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * The first call on each device resolves the array's device address (and may
+ * load the library's device code); make that first call during set-up, before
+ * any stream capture. No call allocates: no cudaMalloc, cudaFree or allocating
+ * library routine. Errors: EINVAL, ECUDA. */
+tbsci_status tbsci_overlap_noalloc(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n,
+                                   double *S, tbsci_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

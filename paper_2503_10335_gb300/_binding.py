@@ -27,6 +27,7 @@ EXPORTS = [
     "tbsci_build_excitation_tables", "tbsci_tables_counts", "tbsci_tables_export", "tbsci_tables_destroy",
     "tbsci_hamiltonian_create", "tbsci_hamiltonian_destroy", "tbsci_prepare", "tbsci_sigma",
     "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson", "tbsci_overlap",
+    "tbsci_overlap_noalloc",
 ]
 
 
@@ -115,6 +116,7 @@ def load(path: str | None = None):
         "tbsci_sigma_counts_get": ([P, P, P, P, ctypes.POINTER(SigmaCounts)], I),
         "tbsci_davidson": ([P, P, P, P, I, ctypes.POINTER(DavidsonOpts), P, P, ctypes.POINTER(DavidsonInfo)], I),
         "tbsci_overlap": ([P, P, I, P, I, I64, P, P], I),
+        "tbsci_overlap_noalloc": ([P, P, I, P, I, I64, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

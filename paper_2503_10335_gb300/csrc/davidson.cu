@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -549,3 +551,55 @@ tbsci_status overlap_run(tbsci_ctx *ctx, const double *A, int ma, const double *
 }
 
 }  // namespace tbsci
+
+// ---------------------------------------------------------------------------
+// Allocation-free overlap. Its scratch is a file-scope device array: host code
+// must not use the symbol itself as a device address, so each device's address
+// is looked up once with cudaGetSymbolAddress (on that device) and cached.
+
+namespace {
+constexpr int kNoAllocMaxProducts = 512;  // ma * mb
+constexpr int kNoAllocMaxBlocks = 512;    // dot blocks per call
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+// partial[block][product]: 512 x 512 doubles = 2 MiB per device
+static __device__ __align__(256) double g_noalloc_partial[kNoAllocMaxBlocks * kNoAllocMaxProducts];
+
+extern "C" tbsci_status tbsci_overlap_noalloc(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb,
+                                              int64_t n, double *S, tbsci_stream stream) {
+    using namespace tbsci;
+    if (!ctx) return TBSCI_EINVAL;
+    TB_CUDA(ctx, cudaSetDevice(ctx->device));
+    TB_CHECK(ctx, ma >= 0 && mb >= 0 && n >= 0, TBSCI_EINVAL, "tbsci_overlap_noalloc: negative size");
+    if ((int64_t)ma * mb > kNoAllocMaxProducts)
+        return fail(ctx, TBSCI_EINVAL,
+                    "tbsci_overlap_noalloc: ma*mb = " + std::to_string((int64_t)ma * mb) +
+                        " exceeds the static scratch limit of 512 products; use tbsci_overlap");
+    if (ma == 0 || mb == 0) return TBSCI_OK;
+    TB_CHECK(ctx, A && B && S, TBSCI_EINVAL, "tbsci_overlap_noalloc: null pointer");
+    TB_CHECK(ctx, ctx->device < kNoAllocMaxDevices, TBSCI_EINVAL, "tbsci_overlap_noalloc: device index >= 64");
+    double *partial = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[ctx->device]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+            if (e != cudaSuccess)
+                return fail(ctx, TBSCI_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_addr[ctx->device] = static_cast<double *>(p);
+        }
+        partial = g_noalloc_addr[ctx->device];
+    }
+    const int nblocks = std::min(2 * ctx->num_sms, kNoAllocMaxBlocks);
+    const int ldp = ma * mb;
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + kMB - 1) / kMB);
+    k_dots<<<grid, kDotThreads, 0, st>>>(A, ma, B, mb, n, partial, ldp);
+    TB_CUDA(ctx, cudaGetLastError());
+    k_reduce_partials<<<(ldp + 127) / 128, 128, 0, st>>>(partial, nblocks, ldp, ldp, S);
+    TB_CUDA(ctx, cudaGetLastError());
+    return TBSCI_OK;
+}
