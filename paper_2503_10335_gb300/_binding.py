@@ -287,8 +287,10 @@ def tbsci_overlap(ctx, A, B, stream=None) -> np.ndarray:
     """S[i, j] = <A_i | B_j> for FP64 device tensors A [ma, ...] and B [mb, ...]
     with the same number of elements per vector; returns a numpy [ma, mb]."""
     ma, mb = int(A.shape[0]), int(B.shape[0])
-    n = int(A[0].numel()) if ma else 0
-    assert mb == 0 or int(B[0].numel()) == n
+    na = A.numel() // ma if ma else None
+    nb = B.numel() // mb if mb else None
+    assert na is None or nb is None or na == nb, "vectors of different length"
+    n = int(na if na is not None else (nb or 0))
     S = np.zeros((ma, mb))
     _check(ctx, load().tbsci_overlap(ctx, _ptr(A), ma, _ptr(B), mb, n, _ptr(S), _stream(stream)))
     return S
