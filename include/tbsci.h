@@ -225,6 +225,73 @@ tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *
                             int nroots, const tbsci_davidson_opts *opts, double *energies, double *vecs,
                             tbsci_davidson_info *info);
 
+/* --------------------------------------------------------------- serving */
+
+/* A request loop for many solves (no counterpart in the paper, which runs one
+ * solve at a time): requests of any norb, electron counts and string sets are
+ * submitted from any thread; a scheduler thread admits them against an HBM
+ * budget in arrival order, builds their strings, tables and Hamiltonian on the
+ * device, and advances all admitted solves together -- continuous batching:
+ * a request that arrives while others run joins as soon as a slot and memory
+ * are free, its sigma work goes into the same batched launches and its vector
+ * work overlaps on its own stream. Each solve is the Davidson of tbsci_davidson,
+ * so a result does not depend on what else was running (batched sigma launches
+ * compute every job exactly as a launch of its own would). */
+typedef struct tbsci_server tbsci_server;
+
+typedef struct tbsci_server_opts {
+    int device;
+    size_t hbm_budget; /* bytes the admitted solves may hold; 0 -> 60 GiB */
+    int max_active;    /* solves advanced together; 0 -> 64 */
+    int max_queue;     /* submitted but not yet admitted; 0 -> 4096 (then EAGAIN) */
+    int fuse_sigma;    /* 0 or 1: one batched sigma launch per precision per
+                          scheduler round; -1: one launch per solve */
+    int fail_admission_at; /* test hook: the n-th admission (1-based) fails with ENOMEM; 0 = off */
+} tbsci_server_opts;
+
+typedef struct tbsci_request {
+    int norb, nalpha, nbeta;
+    const double *h;   /* HOST [norb*norb], copied at submit */
+    const double *eri; /* HOST [norb^4] chemists' order, copied at submit */
+    double ecore;
+    const uint64_t *alpha; /* HOST selected alpha strings or NULL (full space) */
+    int64_t n_alpha;
+    const uint64_t *beta;  /* HOST selected beta strings or NULL (full space) */
+    int64_t n_beta;
+    int nroots;            /* 1..8 */
+    int mixed;             /* 1: FP32 sigma then FP64 refinement; 0: FP64 throughout */
+    double tol_energy, tol_residual; /* 0 -> the tbsci_davidson defaults */
+    int max_iter;          /* 0 -> 1000 */
+} tbsci_request;
+
+typedef struct tbsci_result {
+    tbsci_status status;   /* OK, ENOCONV, EINVAL, ENOMEM, ECUDA */
+    int nroots;
+    double energies[8];
+    double residual[8];
+    int iterations, nsigma, nsigma_f32;
+    int64_t ndet;
+    /* seconds since the server was created */
+    double t_submit, t_admit, t_first_sigma, t_done;
+} tbsci_result;
+
+/* Starts a server (its own context and scheduler thread) on opts->device.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+tbsci_status tbsci_server_create(const tbsci_server_opts *opts, tbsci_server **out);
+/* Queues a solve; copies every host array before returning. *ticket identifies
+ * it in tbsci_poll. Errors: EINVAL (bad sizes or null arrays), EAGAIN (queue
+ * full), EBUSY (server shutting down). */
+tbsci_status tbsci_submit(tbsci_server *srv, const tbsci_request *req, uint64_t *ticket);
+/* Waits up to timeout_ms (0: do not wait, < 0: forever) for the ticket. OK with
+ * *out filled (the ticket is then released), ETIMEOUT when not finished in time,
+ * EINVAL for an unknown ticket. */
+tbsci_status tbsci_poll(tbsci_server *srv, uint64_t ticket, int timeout_ms, tbsci_result *out);
+/* Number of queued and of admitted (running) requests. */
+tbsci_status tbsci_server_load(tbsci_server *srv, int *queued, int *active);
+/* Stops the scheduler after the running solves finish; queued requests are
+ * dropped with EBUSY results. Frees everything. */
+void tbsci_server_destroy(tbsci_server *srv);
+
 /* Overlaps of FP64 DEVICE vectors: S[i*mb + j] = sum_K A[i][K] * B[j][K] for
  * i < ma, j < mb, each vector n long (CI vectors of a space: n = l_a * l_b; the
  * Rayleigh-matrix and Gram-Schmidt products of the Davidson of Sec. III.A). S is

@@ -17,7 +17,7 @@ for _n in dir(B):
         globals()[_n] = getattr(B, _n)
 del _n
 
-__all__ = ["Context", "Space", "B"] + [n for n in dir(B) if n.startswith(("tbsci_", "TBSCI_"))]
+__all__ = ["Context", "Space", "Server", "B"] + [n for n in dir(B) if n.startswith(("tbsci_", "TBSCI_"))]
 
 
 class Context:
@@ -109,6 +109,37 @@ class Space:
         for fn, h in reversed(self._handles):
             fn(h)
         self._handles = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (tbsci_server_*): submit solves from any thread, poll results."""
+
+    def __init__(self, device=0, hbm_budget=0, max_active=0, max_queue=0, fuse_sigma=0, fail_admission_at=0):
+        self.handle = B.tbsci_server_create(device, hbm_budget, max_active, max_queue, fuse_sigma,
+                                            fail_admission_at)
+
+    def submit(self, norb, nalpha, nbeta, h, eri, ecore=0.0, alpha=None, beta=None, nroots=1, mixed=False, **kw):
+        st, ticket = B.tbsci_submit(self.handle, norb, nalpha, nbeta, h, eri, ecore, alpha, beta, nroots, mixed, **kw)
+        if st != B.TBSCI_OK:
+            raise B.TbsciError(st, "tbsci_submit")
+        return ticket
+
+    def poll(self, ticket, timeout_ms=-1):
+        return B.tbsci_poll(self.handle, ticket, timeout_ms)
+
+    def load(self):
+        return B.tbsci_server_load(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            B.tbsci_server_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -27,7 +27,8 @@ EXPORTS = [
     "tbsci_build_excitation_tables", "tbsci_tables_counts", "tbsci_tables_export", "tbsci_tables_destroy",
     "tbsci_hamiltonian_create", "tbsci_hamiltonian_destroy", "tbsci_prepare", "tbsci_sigma",
     "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson", "tbsci_overlap",
-    "tbsci_overlap_noalloc",
+    "tbsci_overlap_noalloc", "tbsci_server_create", "tbsci_submit", "tbsci_poll", "tbsci_server_load",
+    "tbsci_server_destroy",
 ]
 
 
@@ -71,6 +72,33 @@ class DavidsonInfo(ctypes.Structure):
                     nsigma_f32=self.nsigma_f32, iterations_f32=self.iterations_f32,
                     residual=list(self.residual), energy_f32=list(self.energy_f32),
                     seconds_total=self.seconds_total, seconds_sigma=self.seconds_sigma)
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("max_queue", ctypes.c_int), ("fuse_sigma", ctypes.c_int), ("fail_admission_at", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("norb", ctypes.c_int), ("nalpha", ctypes.c_int), ("nbeta", ctypes.c_int),
+                ("h", ctypes.c_void_p), ("eri", ctypes.c_void_p), ("ecore", ctypes.c_double),
+                ("alpha", ctypes.c_void_p), ("n_alpha", ctypes.c_int64), ("beta", ctypes.c_void_p),
+                ("n_beta", ctypes.c_int64), ("nroots", ctypes.c_int), ("mixed", ctypes.c_int),
+                ("tol_energy", ctypes.c_double), ("tol_residual", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nroots", ctypes.c_int), ("energies", ctypes.c_double * 8),
+                ("residual", ctypes.c_double * 8), ("iterations", ctypes.c_int), ("nsigma", ctypes.c_int),
+                ("nsigma_f32", ctypes.c_int), ("ndet", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_first_sigma", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        n = self.nroots
+        return dict(status=self.status, energies=list(self.energies[:n]), residual=list(self.residual[:n]),
+                    iterations=self.iterations, nsigma=self.nsigma, nsigma_f32=self.nsigma_f32, ndet=self.ndet,
+                    t_submit=self.t_submit, t_admit=self.t_admit, t_first_sigma=self.t_first_sigma,
+                    t_done=self.t_done)
 
 
 class TbsciError(RuntimeError):
@@ -117,6 +145,11 @@ def load(path: str | None = None):
         "tbsci_davidson": ([P, P, P, P, I, ctypes.POINTER(DavidsonOpts), P, P, ctypes.POINTER(DavidsonInfo)], I),
         "tbsci_overlap": ([P, P, I, P, I, I64, P, P], I),
         "tbsci_overlap_noalloc": ([P, P, I, P, I, I64, P, P], I),
+        "tbsci_server_create": ([ctypes.POINTER(ServerOpts), PP], I),
+        "tbsci_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], I),
+        "tbsci_poll": ([P, ctypes.c_uint64, I, ctypes.POINTER(Result)], I),
+        "tbsci_server_load": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "tbsci_server_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -294,3 +327,47 @@ def tbsci_overlap(ctx, A, B, stream=None) -> np.ndarray:
     S = np.zeros((ma, mb))
     _check(ctx, load().tbsci_overlap(ctx, _ptr(A), ma, _ptr(B), mb, n, _ptr(S), _stream(stream)))
     return S
+
+
+# ---------------------------------------------------------------- serving
+
+def tbsci_server_create(device=0, hbm_budget=0, max_active=0, max_queue=0, fuse_sigma=0, fail_admission_at=0):
+    o = ServerOpts(device, hbm_budget, max_active, max_queue, fuse_sigma, fail_admission_at)
+    out = ctypes.c_void_p()
+    st = load().tbsci_server_create(ctypes.byref(o), ctypes.byref(out))
+    if st != TBSCI_OK:
+        raise TbsciError(st, "tbsci_server_create failed")
+    return out
+
+
+def tbsci_submit(srv, norb, nalpha, nbeta, h, eri, ecore=0.0, alpha=None, beta=None, nroots=1, mixed=False,
+                 tol_energy=0.0, tol_residual=0.0, max_iter=0):
+    """Queues one solve; returns ``(status, ticket)`` (status EAGAIN when the queue is full)."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.uint64)
+    b = None if beta is None else np.ascontiguousarray(beta, dtype=np.uint64)
+    r = Request(norb, nalpha, nbeta, h.ctypes.data, eri.ctypes.data, float(ecore),
+                None if a is None else a.ctypes.data, 0 if a is None else len(a),
+                None if b is None else b.ctypes.data, 0 if b is None else len(b),
+                nroots, 1 if mixed else 0, tol_energy, tol_residual, max_iter)
+    t = ctypes.c_uint64()
+    st = load().tbsci_submit(srv, ctypes.byref(r), ctypes.byref(t))
+    return st, t.value
+
+
+def tbsci_poll(srv, ticket, timeout_ms=-1):
+    """``(status, result dict or None)``; status ETIMEOUT when not finished in time."""
+    res = Result()
+    st = load().tbsci_poll(srv, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(res))
+    return st, (res.as_dict() if st == TBSCI_OK else None)
+
+
+def tbsci_server_load(srv):
+    q, a = ctypes.c_int(), ctypes.c_int()
+    load().tbsci_server_load(srv, ctypes.byref(q), ctypes.byref(a))
+    return q.value, a.value
+
+
+def tbsci_server_destroy(srv):
+    load().tbsci_server_destroy(srv)

@@ -81,11 +81,11 @@ __global__ void k_reduce_partials(const double *partial, int nblocks, int ldp, i
 constexpr int kMaxBasis = 128;
 constexpr int kMaxOut = 8;
 
-// out[k][K] = beta * out[k][K] + sum_i Y[i][k] * A[i][K], k < kout <= 8
+// out[k][K] = beta * out[k][K] + yscale * sum_i Y[i][k] * A[i][K], k < kout <= 8
 __global__ void __launch_bounds__(256) k_lincomb(const double *__restrict__ A, int m, double *out, int kout, int64_t N,
-                                                 double beta, const double *__restrict__ Y) {
+                                                 double beta, const double *__restrict__ Y, double yscale) {
     __shared__ double sY[kMaxBasis * kMaxOut];
-    for (int x = threadIdx.x; x < m * kout; x += blockDim.x) sY[x] = Y[x];
+    for (int x = threadIdx.x; x < m * kout; x += blockDim.x) sY[x] = yscale * Y[x];
     __syncthreads();
     for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < N; K += (int64_t)gridDim.x * blockDim.x) {
         double acc[kMaxOut];
@@ -101,6 +101,45 @@ __global__ void __launch_bounds__(256) k_lincomb(const double *__restrict__ A, i
         for (int k = 0; k < kMaxOut; ++k)
             if (k < kout) out[(size_t)k * N + K] = acc[k];
     }
+}
+
+// out[k][K] = sum_i Yc[k][i] * A[i][K] (coefficients stored column by column), k < kout <= 8
+__global__ void __launch_bounds__(256) k_lincomb_cols(const double *__restrict__ A, int m, double *out, int kout,
+                                                      int64_t N, const double *__restrict__ Yc) {
+    __shared__ double sY[kMaxBasis * kMaxOut];
+    for (int x = threadIdx.x; x < m * kout; x += blockDim.x) {
+        const int k = x / m, i = x - k * m;
+        sY[i * kout + k] = Yc[x];
+    }
+    __syncthreads();
+    for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < N; K += (int64_t)gridDim.x * blockDim.x) {
+        double acc[kMaxOut];
+#pragma unroll
+        for (int k = 0; k < kMaxOut; ++k) acc[k] = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double a = __ldg(A + (size_t)i * N + K);
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k)
+                if (k < kout) acc[k] = fma(sY[i * kout + k], a, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxOut; ++k)
+            if (k < kout) out[(size_t)k * N + K] = acc[k];
+    }
+}
+
+// y = x / sqrt(*nrm2) (zero when the norm is zero)
+__global__ void k_normalize(const double *__restrict__ x, const double *__restrict__ nrm2, double *y, int64_t N) {
+    const double n2 = *nrm2;
+    const double s = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+    for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < N; K += (int64_t)gridDim.x * blockDim.x)
+        y[K] = s * x[K];
+}
+
+// V[r][idx[r]] = 1 for r < nroots
+__global__ void k_set_units(double *V, int64_t N, const int64_t *idx, int nroots) {
+    const int r = threadIdx.x;
+    if (r < nroots) V[(size_t)r * N + idx[r]] = 1.0;
 }
 
 // r = wy - theta x; t = r / clamp(theta - diag); partial norms of r
@@ -139,10 +178,6 @@ __global__ void __launch_bounds__(kDotThreads) k_residual(const double *__restri
     }
 }
 
-__global__ void k_scale_copy(const double *__restrict__ x, double s, double *y, int64_t N) {
-    for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < N; K += (int64_t)gridDim.x * blockDim.x)
-        y[K] = s * x[K];
-}
 
 __global__ void k_to_f32(const double *__restrict__ x, float *y, int64_t n) {
     for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < n; K += (int64_t)gridDim.x * blockDim.x)
@@ -242,290 +277,482 @@ void jacobi_eigh(std::vector<double> a, int m, std::vector<double> &w, std::vect
     v.swap(vs);
 }
 
-struct Dav {
-    tbsci_ctx *ctx;
-    tbsci_ham *ham;
-    Plan *plan;
-    cudaStream_t st;
-    int64_t N;
-    int nblocks;
-    DevBuf<double> partial, red, dY, dtheta;
-    DevBuf<float> v32, w32;
-    double t_sigma = 0.0;
-    int nsig = 0, nsig32 = 0;
-
-    tbsci_status dots(const double *A, int ma, const double *B, int mb, std::vector<double> &out) {
-        // out[i*mb + j] = A_i . B_j
-        dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + kMB - 1) / kMB);
-        int ldp = ma * mb;
-        k_dots<<<grid, kDotThreads, 0, st>>>(A, ma, B, mb, N, partial.p, ldp);
-        TB_CUDA(ctx, cudaGetLastError());
-        k_reduce_partials<<<(ldp + 127) / 128, 128, 0, st>>>(partial.p, nblocks, ldp, ldp, red.p);
-        TB_CUDA(ctx, cudaGetLastError());
-        out.resize(ldp);
-        TB_CUDA(ctx, cudaMemcpyAsync(out.data(), red.p, ldp * sizeof(double), cudaMemcpyDeviceToHost, st));
-        TB_CUDA(ctx, cudaStreamSynchronize(st));
-        return TBSCI_OK;
-    }
-    // out[0..kout) = beta*out + sum_i Y[i][k] A[i]
-    tbsci_status lincomb(const double *A, int m, double *out, int kout, double beta, const std::vector<double> &Y) {
-        TB_CUDA(ctx, cudaMemcpyAsync(dY.p, Y.data(), (size_t)m * kout * sizeof(double), cudaMemcpyHostToDevice, st));
-        k_lincomb<<<nblocks, 256, 0, st>>>(A, m, out, kout, N, beta, dY.p);
-        TB_CUDA(ctx, cudaGetLastError());
-        // Y is reused by the next call: finish this one first
-        TB_CUDA(ctx, cudaStreamSynchronize(st));
-        return TBSCI_OK;
-    }
-    tbsci_status sigma(const double *V, double *W, int k, bool f32) {
-        auto t0 = std::chrono::steady_clock::now();
-        if (!f32) {
-            TB_TRY(sigma_launch(ctx, ham, plan, V, W, k, TBSCI_F64, st));
-            nsig += k;
-        } else {
-            int64_t n = N * k;
-            k_to_f32<<<nblocks, 256, 0, st>>>(V, v32.p, n);
-            TB_CUDA(ctx, cudaGetLastError());
-            TB_TRY(sigma_launch(ctx, ham, plan, v32.p, w32.p, k, TBSCI_F32, st));
-            k_to_f64<<<nblocks, 256, 0, st>>>(w32.p, W, n);
-            TB_CUDA(ctx, cudaGetLastError());
-            nsig += k;
-            nsig32 += k;
-        }
-        TB_CUDA(ctx, cudaStreamSynchronize(st));
-        t_sigma += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        return TBSCI_OK;
-    }
-};
-
 }  // namespace
 
-tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
-                          double *energies, double *vecs, tbsci_davidson_info *info) {
-    auto T0 = std::chrono::steady_clock::now();
-    tbsci_davidson_opts opt{};
-    if (o) opt = *o;
-    const int m_max = opt.max_subspace > 0 ? opt.max_subspace : std::max(8 * nroots, nroots + 2);
-    const int keep = opt.restart_keep > 0 ? opt.restart_keep : std::max(nroots, m_max / 2);
-    const int max_iter = opt.max_iter > 0 ? opt.max_iter : 1000;
-    const double tol_e = opt.tol_energy > 0 ? opt.tol_energy : 1e-9;
-    const double tol_r = opt.tol_residual > 0 ? opt.tol_residual : 1e-5;
-    const double tol_rm = opt.tol_mixed_residual > 0 ? opt.tol_mixed_residual : 5e-5;
-    TB_CHECK(ctx, nroots >= 1 && nroots <= kMaxOut, TBSCI_EINVAL, "nroots must be in 1..8");
-    TB_CHECK(ctx, m_max >= nroots + 1 && m_max <= kMaxBasis, TBSCI_EINVAL, "max_subspace must be in nroots+1..128");
-    TB_CHECK(ctx, keep >= nroots && keep < m_max, TBSCI_EINVAL, "restart_keep must be in nroots..max_subspace-1");
-    Dav D;
-    D.ctx = ctx;
-    D.ham = ham;
-    D.plan = plan;
-    D.st = opt.stream ? (cudaStream_t)opt.stream : ctx->stream;
-    D.N = plan->A.l * plan->B.l;
-    const int64_t N = D.N;
-    TB_CHECK(ctx, N >= nroots, TBSCI_EINVAL, "space has fewer determinants than roots");
-    D.nblocks = 2 * ctx->num_sms;
-    // dot partials: up to max_subspace x max_subspace products per block
-    TB_CUDA(ctx, D.partial.alloc((size_t)D.nblocks * kMaxBasis * kMaxBasis));
-    TB_CUDA(ctx, D.red.alloc(kMaxBasis * kMaxBasis));
-    TB_CUDA(ctx, D.dY.alloc(kMaxBasis * kMaxOut));
-    TB_CUDA(ctx, D.dtheta.alloc(kMaxOut));
-    DevBuf<double> V, W, X, WY, T, diag, R;  // R: Ritz block of a thick restart
-    TB_CUDA(ctx, V.alloc((size_t)m_max * N));
-    TB_CUDA(ctx, W.alloc((size_t)m_max * N));
-    TB_CUDA(ctx, X.alloc((size_t)nroots * N));
-    TB_CUDA(ctx, WY.alloc((size_t)nroots * N));
-    TB_CUDA(ctx, T.alloc((size_t)nroots * N));
-    TB_CUDA(ctx, diag.alloc(N));
-    bool f32 = opt.mixed != 0;
-    if (f32) {
-        TB_CUDA(ctx, D.v32.alloc((size_t)nroots * N));
-        TB_CUDA(ctx, D.w32.alloc((size_t)nroots * N));
-    }
-    cudaStream_t st = D.st;
-    TB_TRY(diagonal_launch(ctx, ham, plan, diag.p, st));
+// ---------------------------------------------------------------------------
+// Resumable Davidson engine. Each phase enqueues device work on the engine's
+// stream and ends at one event; the host logic of the next phase runs once that
+// event has completed. Phases per iteration:
+//   NeedSigma  -> images of the newest basis vectors are wanted (driver launches sigma)
+//   WaitG      -> new Rayleigh-matrix columns are on their way to the host
+//   WaitR      -> Ritz vectors, residual norms and preconditioned corrections computed
+//   WaitGS     -> corrections orthonormalised on the device, their norms on the way
+// A driver either blocks on each phase (tbsci_davidson) or polls many engines
+// and batches their sigma work (the serving loop).
 
-    // guess: unit vectors at the lowest (H_KK, K)
-    std::vector<int64_t> chosen;
-    {
+struct DavEngine {
+    tbsci_ctx *ctx = nullptr;
+    tbsci_ham *ham = nullptr;
+    Plan *plan = nullptr;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    cudaEvent_t evt = nullptr;
+    int nroots = 1, m_max = 0, keep = 0, max_iter = 0;
+    double tol_e = 0, tol_r = 0, tol_rm = 0;
+    int64_t N = 0;
+    int nblocks = 0;
+    DevBuf<double> V, W, X, WY, T, diag, R, partial, red, dY, dY2, dtheta, scal, coef;
+    DevBuf<float> v32, w32;
+    double *hG = nullptr, *hY = nullptr, *hY2 = nullptr, *hR = nullptr, *hN = nullptr;  // pinned
+    enum class St { NeedSigma, WaitG, WaitR, WaitGS, Done } state = St::NeedSigma;
+    int m = 0, sig_lo = 0, sig_hi = 0, g_lo = 0;
+    bool f32 = false, sig_prepared = false;
+    std::vector<double> G, theta, theta_prev, rnorm, e32, Yv;
+    std::vector<int> todo;
+    int it = 0, it32 = 0, stall32 = 0, nsig = 0, nsig32 = 0;
+    double best32 = INFINITY;
+    bool converged = false, failed = false;
+    tbsci_status status = TBSCI_OK;
+    std::chrono::steady_clock::time_point t_start;
+
+    ~DavEngine() {
+        if (hG) cudaFreeHost(hG);
+        if (hY) cudaFreeHost(hY);
+        if (hY2) cudaFreeHost(hY2);
+        if (hR) cudaFreeHost(hR);
+        if (hN) cudaFreeHost(hN);
+        if (evt) cudaEventDestroy(evt);
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+
+    tbsci_status dots(const double *A, int ma, const double *B, int mb, double *out) {
+        dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + kMB - 1) / kMB);
+        const int ldp = ma * mb;
+        k_dots<<<grid, kDotThreads, 0, st>>>(A, ma, B, mb, N, partial.p, ldp);
+        TB_CUDA(ctx, cudaGetLastError());
+        k_reduce_partials<<<(ldp + 127) / 128, 128, 0, st>>>(partial.p, nblocks, ldp, ldp, out);
+        TB_CUDA(ctx, cudaGetLastError());
+        return TBSCI_OK;
+    }
+    tbsci_status lincomb(const double *A, int mm, double *out, int kout, double beta, const double *Ydev,
+                         double yscale) {
+        k_lincomb<<<nblocks, 256, 0, st>>>(A, mm, out, kout, N, beta, Ydev, yscale);
+        TB_CUDA(ctx, cudaGetLastError());
+        return TBSCI_OK;
+    }
+    tbsci_status finish_phase(St next) {
+        TB_CUDA(ctx, cudaEventRecord(evt, st));
+        state = next;
+        return TBSCI_OK;
+    }
+
+    tbsci_status init(tbsci_ctx *c, tbsci_ham *h, Plan *p, int nr, const tbsci_davidson_opts &opt) {
+        ctx = c;
+        ham = h;
+        plan = p;
+        nroots = nr;
+        t_start = std::chrono::steady_clock::now();
+        m_max = opt.max_subspace > 0 ? opt.max_subspace : std::max(8 * nroots, nroots + 2);
+        keep = opt.restart_keep > 0 ? opt.restart_keep : std::max(nroots, m_max / 2);
+        max_iter = opt.max_iter > 0 ? opt.max_iter : 1000;
+        tol_e = opt.tol_energy > 0 ? opt.tol_energy : 1e-9;
+        tol_r = opt.tol_residual > 0 ? opt.tol_residual : 1e-5;
+        tol_rm = opt.tol_mixed_residual > 0 ? opt.tol_mixed_residual : 5e-5;
+        TB_CHECK(ctx, nroots >= 1 && nroots <= kMaxOut, TBSCI_EINVAL, "nroots must be in 1..8");
+        TB_CHECK(ctx, m_max >= nroots + 1 && m_max <= kMaxBasis, TBSCI_EINVAL,
+                 "max_subspace must be in nroots+1..128");
+        TB_CHECK(ctx, keep >= nroots && keep < m_max, TBSCI_EINVAL, "restart_keep must be in nroots..max_subspace-1");
+        N = plan->A.l * plan->B.l;
+        TB_CHECK(ctx, N >= nroots, TBSCI_EINVAL, "space has fewer determinants than roots");
+        if (opt.stream) {
+            st = (cudaStream_t)opt.stream;
+        } else {
+            TB_CUDA(ctx, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        TB_CUDA(ctx, cudaEventCreateWithFlags(&evt, cudaEventDisableTiming));
+        // small problems use fewer reduction blocks (fixed per problem size: deterministic)
+        nblocks = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, (N + 4095) / 4096));
+        TB_CUDA(ctx, partial.alloc((size_t)nblocks * std::max(m_max * m_max, kMaxOut)));
+        TB_CUDA(ctx, red.alloc((size_t)m_max * m_max));
+        TB_CUDA(ctx, dY.alloc((size_t)m_max * m_max));
+        TB_CUDA(ctx, dY2.alloc((size_t)m_max * m_max));
+        TB_CUDA(ctx, dtheta.alloc(kMaxOut));
+        TB_CUDA(ctx, scal.alloc(2 * kMaxOut));
+        TB_CUDA(ctx, coef.alloc(m_max));
+        TB_CUDA(ctx, cudaMallocHost(&hG, (size_t)m_max * m_max * sizeof(double)));
+        TB_CUDA(ctx, cudaMallocHost(&hY, (size_t)m_max * m_max * sizeof(double)));
+        TB_CUDA(ctx, cudaMallocHost(&hY2, (size_t)m_max * m_max * sizeof(double)));
+        TB_CUDA(ctx, cudaMallocHost(&hR, kMaxOut * sizeof(double)));
+        TB_CUDA(ctx, cudaMallocHost(&hN, 2 * kMaxOut * sizeof(double)));
+        TB_CUDA(ctx, V.alloc((size_t)m_max * N));
+        TB_CUDA(ctx, W.alloc((size_t)m_max * N));
+        TB_CUDA(ctx, X.alloc((size_t)nroots * N));
+        TB_CUDA(ctx, WY.alloc((size_t)nroots * N));
+        TB_CUDA(ctx, T.alloc((size_t)nroots * N));
+        TB_CUDA(ctx, diag.alloc(N));
+        f32 = opt.mixed != 0;
+        if (f32) {
+            TB_CUDA(ctx, v32.alloc((size_t)nroots * N));
+            TB_CUDA(ctx, w32.alloc((size_t)nroots * N));
+        }
+        G.assign((size_t)m_max * m_max, 0.0);
+        theta.assign(nroots, 0.0);
+        theta_prev.assign(nroots, INFINITY);
+        rnorm.assign(nroots, INFINITY);
+        e32.assign(nroots, 0.0);
+        TB_TRY(diagonal_launch(ctx, ham, plan, diag.p, st));
+        // guess: unit vectors at the lowest (H_KK, K)
+        std::vector<int64_t> chosen;
         DevBuf<double> bv;
         DevBuf<int64_t> bi, dskip;
-        TB_CUDA(ctx, bv.alloc(D.nblocks));
-        TB_CUDA(ctx, bi.alloc(D.nblocks));
+        TB_CUDA(ctx, bv.alloc(nblocks));
+        TB_CUDA(ctx, bi.alloc(nblocks));
         TB_CUDA(ctx, dskip.alloc(kMaxOut));
-        std::vector<double> hv(D.nblocks);
-        std::vector<int64_t> hi(D.nblocks);
+        std::vector<double> hv(nblocks);
+        std::vector<int64_t> hi(nblocks);
         for (int r = 0; r < nroots; ++r) {
             if (!chosen.empty())
                 TB_CUDA(ctx, cudaMemcpyAsync(dskip.p, chosen.data(), chosen.size() * sizeof(int64_t),
                                              cudaMemcpyHostToDevice, st));
-            k_argmin<<<D.nblocks, 256, 0, st>>>(diag.p, N, dskip.p, (int)chosen.size(), bv.p, bi.p);
+            k_argmin<<<nblocks, 256, 0, st>>>(diag.p, N, dskip.p, (int)chosen.size(), bv.p, bi.p);
             TB_CUDA(ctx, cudaGetLastError());
-            TB_CUDA(ctx, cudaMemcpyAsync(hv.data(), bv.p, D.nblocks * sizeof(double), cudaMemcpyDeviceToHost, st));
-            TB_CUDA(ctx, cudaMemcpyAsync(hi.data(), bi.p, D.nblocks * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            TB_CUDA(ctx, cudaMemcpyAsync(hv.data(), bv.p, nblocks * sizeof(double), cudaMemcpyDeviceToHost, st));
+            TB_CUDA(ctx, cudaMemcpyAsync(hi.data(), bi.p, nblocks * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             TB_CUDA(ctx, cudaStreamSynchronize(st));
             double best = INFINITY;
             int64_t bidx = INT64_MAX;
-            for (int b = 0; b < D.nblocks; ++b)
+            for (int b = 0; b < nblocks; ++b)
                 if (hv[b] < best || (hv[b] == best && hi[b] < bidx)) {
                     best = hv[b];
                     bidx = hi[b];
                 }
+            TB_CHECK(ctx, bidx >= 0 && bidx < N, TBSCI_EINVAL, "Davidson guess: the diagonal has no finite minimum");
             chosen.push_back(bidx);
         }
-    }
-    TB_CUDA(ctx, cudaMemsetAsync(V.p, 0, (size_t)nroots * N * sizeof(double), st));
-    const double one = 1.0;
-    for (int r = 0; r < nroots; ++r)
-        TB_CUDA(ctx, cudaMemcpyAsync(V.p + (size_t)r * N + chosen[r], &one, sizeof(double), cudaMemcpyHostToDevice, st));
-    TB_CUDA(ctx, cudaStreamSynchronize(st));
-
-    int m = nroots;
-    TB_TRY(D.sigma(V.p, W.p, m, f32));
-    std::vector<double> G((size_t)m_max * m_max, 0.0), tmp;
-    auto refresh_G = [&](int lo, int hi) -> tbsci_status {
-        // columns lo..hi of G against all rows < hi, mirrored
-        TB_TRY(D.dots(V.p, hi, W.p + (size_t)lo * N, hi - lo, tmp));
-        for (int i = 0; i < hi; ++i)
-            for (int j = lo; j < hi; ++j) {
-                double g = tmp[(size_t)i * (hi - lo) + (j - lo)];
-                G[(size_t)i * m_max + j] = g;
-                if (i < lo) G[(size_t)j * m_max + i] = g;
-            }
-        // symmetrise the new block
-        for (int i = lo; i < hi; ++i)
-            for (int j = i + 1; j < hi; ++j) {
-                double g = 0.5 * (G[(size_t)i * m_max + j] + G[(size_t)j * m_max + i]);
-                G[(size_t)i * m_max + j] = G[(size_t)j * m_max + i] = g;
-            }
+        TB_CUDA(ctx, cudaMemsetAsync(V.p, 0, (size_t)nroots * N * sizeof(double), st));
+        TB_CUDA(ctx, cudaMemcpyAsync(dskip.p, chosen.data(), chosen.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                     st));
+        k_set_units<<<1, kMaxOut, 0, st>>>(V.p, N, dskip.p, nroots);
+        TB_CUDA(ctx, cudaGetLastError());
+        TB_CUDA(ctx, cudaStreamSynchronize(st));  // bv/bi/dskip are freed on return
+        m = 0;
+        sig_lo = 0;
+        sig_hi = nroots;
+        g_lo = 0;
+        state = St::NeedSigma;
         return TBSCI_OK;
-    };
-    TB_TRY(refresh_G(0, m));
-    std::vector<double> theta(nroots), theta_prev(nroots, INFINITY), rnorm(nroots, INFINITY);
-    std::vector<double> e32(nroots, 0.0);
-    int it = 0, it32 = 0;
-    double best32 = INFINITY;  // FP32 phase: smallest max-residual so far
-    int stall32 = 0;
-    bool converged = false;
-    tbsci_status result = TBSCI_OK;
-    for (it = 1; it <= max_iter; ++it) {
+    }
+
+    // The sigma the engine needs next (device pointers, on the engine stream).
+    bool wants_sigma(const void **c, void **s, int *k, tbsci_dtype *dt) {
+        if (state != St::NeedSigma) return false;
+        const int kk = sig_hi - sig_lo;
+        if (f32) {
+            if (!sig_prepared) {
+                k_to_f32<<<nblocks, 256, 0, st>>>(V.p + (size_t)sig_lo * N, v32.p, (int64_t)kk * N);
+                sig_prepared = true;
+            }
+            *c = v32.p;
+            *s = w32.p;
+            *dt = TBSCI_F32;
+        } else {
+            *c = V.p + (size_t)sig_lo * N;
+            *s = W.p + (size_t)sig_lo * N;
+            *dt = TBSCI_F64;
+        }
+        *k = kk;
+        return true;
+    }
+
+    // Called once the sigma of wants_sigma() is enqueued on (or ordered before) the engine stream.
+    tbsci_status sigma_done() {
+        const int kk = sig_hi - sig_lo;
+        if (f32) {
+            k_to_f64<<<nblocks, 256, 0, st>>>(w32.p, W.p + (size_t)sig_lo * N, (int64_t)kk * N);
+            TB_CUDA(ctx, cudaGetLastError());
+            nsig32 += kk;
+        }
+        nsig += kk;
+        sig_prepared = false;
+        m = sig_hi;
+        // Rayleigh-matrix columns g_lo..m against rows 0..m
+        TB_TRY(dots(V.p, m, W.p + (size_t)g_lo * N, m - g_lo, red.p));
+        const int ld = m * (m - g_lo);
+        TB_CUDA(ctx, cudaMemcpyAsync(hG, red.p, (size_t)ld * sizeof(double), cudaMemcpyDeviceToHost, st));
+        return finish_phase(St::WaitG);
+    }
+
+    // Iteration head: subspace eigenproblem, Ritz vectors, residuals.
+    tbsci_status head() {
+        ++it;
         if (f32) ++it32;
-        std::vector<double> Gm((size_t)m * m), w, Yv;
+        std::vector<double> Gm((size_t)m * m), w;
         for (int i = 0; i < m; ++i)
             for (int j = 0; j < m; ++j) Gm[(size_t)i * m + j] = G[(size_t)i * m_max + j];
         jacobi_eigh(Gm, m, w, Yv);
-        std::vector<double> Y((size_t)m * nroots);
-        for (int i = 0; i < m; ++i)
-            for (int k = 0; k < nroots; ++k) Y[(size_t)i * nroots + k] = Yv[(size_t)i * m + k];
         for (int k = 0; k < nroots; ++k) theta[k] = w[k];
-        TB_TRY(D.lincomb(V.p, m, X.p, nroots, 0.0, Y));
-        TB_TRY(D.lincomb(W.p, m, WY.p, nroots, 0.0, Y));
-        TB_CUDA(ctx, cudaMemcpyAsync(D.dtheta.p, theta.data(), nroots * sizeof(double), cudaMemcpyHostToDevice, st));
-        k_residual<<<D.nblocks, kDotThreads, 0, st>>>(X.p, WY.p, diag.p, D.dtheta.p, nroots, N, T.p, D.partial.p);
+        for (int i = 0; i < m; ++i)
+            for (int k = 0; k < nroots; ++k) hY[(size_t)i * nroots + k] = Yv[(size_t)i * m + k];
+        TB_CUDA(ctx, cudaMemcpyAsync(dY.p, hY, (size_t)m * nroots * sizeof(double), cudaMemcpyHostToDevice, st));
+        for (int k = 0; k < nroots; ++k) hR[k] = theta[k];
+        TB_CUDA(ctx, cudaMemcpyAsync(dtheta.p, hR, nroots * sizeof(double), cudaMemcpyHostToDevice, st));
+        TB_TRY(lincomb(V.p, m, X.p, nroots, 0.0, dY.p, 1.0));
+        TB_TRY(lincomb(W.p, m, WY.p, nroots, 0.0, dY.p, 1.0));
+        k_residual<<<nblocks, kDotThreads, 0, st>>>(X.p, WY.p, diag.p, dtheta.p, nroots, N, T.p, partial.p);
         TB_CUDA(ctx, cudaGetLastError());
-        k_reduce_partials<<<1, 32, 0, st>>>(D.partial.p, D.nblocks, kMaxOut, nroots, D.red.p);
+        k_reduce_partials<<<1, 32, 0, st>>>(partial.p, nblocks, kMaxOut, nroots, red.p);
         TB_CUDA(ctx, cudaGetLastError());
-        TB_CUDA(ctx, cudaMemcpyAsync(rnorm.data(), D.red.p, nroots * sizeof(double), cudaMemcpyDeviceToHost, st));
-        TB_CUDA(ctx, cudaStreamSynchronize(st));
+        // hR is reused: the copy below is ordered after the upload above on the same stream
+        TB_CUDA(ctx, cudaMemcpyAsync(hR, red.p, nroots * sizeof(double), cudaMemcpyDeviceToHost, st));
+        return finish_phase(St::WaitR);
+    }
+
+    tbsci_status after_G() {
+        const int cols = m - g_lo;
+        for (int i = 0; i < m; ++i)
+            for (int j = g_lo; j < m; ++j) {
+                const double g = hG[(size_t)i * cols + (j - g_lo)];
+                G[(size_t)i * m_max + j] = g;
+                if (i < g_lo) G[(size_t)j * m_max + i] = g;
+            }
+        for (int i = g_lo; i < m; ++i)
+            for (int j = i + 1; j < m; ++j) {
+                const double g = 0.5 * (G[(size_t)i * m_max + j] + G[(size_t)j * m_max + i]);
+                G[(size_t)i * m_max + j] = G[(size_t)j * m_max + i] = g;
+            }
+        return head();
+    }
+
+    tbsci_status after_R() {
         bool ok = true;
         double rmax = 0.0;
         for (int k = 0; k < nroots; ++k) {
-            rnorm[k] = std::sqrt(rnorm[k]);
+            rnorm[k] = std::sqrt(std::max(hR[k], 0.0));
             rmax = std::max(rmax, rnorm[k]);
-            double dE = std::fabs(theta[k] - theta_prev[k]);
+            const double dE = std::fabs(theta[k] - theta_prev[k]);
             if (f32) ok = ok && rnorm[k] < tol_rm;
             else ok = ok && dE < tol_e && rnorm[k] < tol_r;
         }
         if (f32) {
             // leave the FP32 phase also when its residuals stop falling (FP32 noise floor)
-            if (rmax < 0.9 * best32) {
+            if (rmax < 0.5 * best32) {
                 best32 = rmax;
                 stall32 = 0;
-            } else if (++stall32 >= 8) {
+            } else if (++stall32 >= 30) {
                 ok = true;
             }
         }
         theta_prev = theta;
         if (ok && f32) {
-            // end of the FP32 phase: restart from the Ritz vectors with FP64 sigma
+            // end of the FP32 phase: restart from the roots' Ritz vectors with FP64 sigma
             e32 = theta;
             f32 = false;
             TB_CUDA(ctx, cudaMemcpyAsync(V.p, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            m = nroots;
-            TB_TRY(D.sigma(V.p, W.p, m, false));
-            TB_TRY(refresh_G(0, m));
+            m = 0;
+            sig_lo = 0;
+            sig_hi = nroots;
+            g_lo = 0;
             std::fill(theta_prev.begin(), theta_prev.end(), INFINITY);
-            continue;
+            state = St::NeedSigma;
+            return TBSCI_OK;
         }
         if (ok) {
             converged = true;
-            break;
+            state = St::Done;
+            return TBSCI_OK;
         }
-        std::vector<int> todo;
+        if (it >= max_iter) {
+            state = St::Done;
+            return TBSCI_OK;
+        }
+        todo.clear();
         for (int k = 0; k < nroots; ++k)
             if (rnorm[k] >= (f32 ? tol_rm : tol_r)) todo.push_back(k);
+        bool restarted = false;
         if (m + (int)todo.size() > m_max) {
             // thick restart: keep the lowest `kk` Ritz vectors and their images
             const int kk = std::min(keep, m);
             if (!R.p) TB_CUDA(ctx, R.alloc((size_t)keep * N));
-            std::vector<double> Yk;
+            for (int i = 0; i < m; ++i)
+                for (int k = 0; k < kk; ++k) hY2[(size_t)k * m + i] = Yv[(size_t)i * m + k];  // column-major by k
+            TB_CUDA(ctx, cudaMemcpyAsync(dY2.p, hY2, (size_t)m * kk * sizeof(double), cudaMemcpyHostToDevice, st));
             for (int half = 0; half < 2; ++half) {
                 double *src = half == 0 ? V.p : W.p;
                 for (int k0 = 0; k0 < kk; k0 += kMaxOut) {
                     const int kc = std::min(kMaxOut, kk - k0);
-                    Yk.assign((size_t)m * kc, 0.0);
-                    for (int i = 0; i < m; ++i)
-                        for (int k = 0; k < kc; ++k) Yk[(size_t)i * kc + k] = Yv[(size_t)i * m + k0 + k];
-                    TB_TRY(D.lincomb(src, m, R.p + (size_t)k0 * N, kc, 0.0, Yk));
+                    k_lincomb_cols<<<nblocks, 256, 0, st>>>(src, m, R.p + (size_t)k0 * N, kc, N, dY2.p + (size_t)k0 * m);
+                    TB_CUDA(ctx, cudaGetLastError());
                 }
                 TB_CUDA(ctx, cudaMemcpyAsync(src, R.p, (size_t)kk * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
             }
             m = kk;
-            TB_TRY(refresh_G(0, m));
+            restarted = true;
         }
-        const int m_old = m;
-        for (int k : todo) {
-            if (m >= m_max) break;  // the basis is full: remaining corrections wait for the next iteration
-            double *t = T.p + (size_t)k * N;
-            std::vector<double> nn;
-            TB_TRY(D.dots(t, 1, t, 1, nn));
-            const double t0 = std::sqrt(nn[0]);
+        if (todo.empty()) return head();
+        // two Gram-Schmidt passes per correction against the basis, on the device
+        const int nb = (int)todo.size();
+        for (int j = 0; j < nb; ++j) {
+            double *t = T.p + (size_t)todo[j] * N;
+            TB_TRY(dots(t, 1, t, 1, scal.p + 2 * j));
             for (int pass = 0; pass < 2; ++pass) {
-                std::vector<double> cdot;
-                TB_TRY(D.dots(V.p, m, t, 1, cdot));
-                for (auto &x : cdot) x = -x;
-                TB_TRY(D.lincomb(V.p, m, t, 1, 1.0, cdot));
+                TB_TRY(dots(V.p, m + j, t, 1, coef.p));
+                TB_TRY(lincomb(V.p, m + j, t, 1, 1.0, coef.p, -1.0));
             }
-            TB_TRY(D.dots(t, 1, t, 1, nn));
-            const double nt = std::sqrt(nn[0]);
-            if (!(nt > 1e-10 * t0)) continue;
-            k_scale_copy<<<D.nblocks, 256, 0, st>>>(t, 1.0 / nt, V.p + (size_t)m * N, N);
+            TB_TRY(dots(t, 1, t, 1, scal.p + 2 * j + 1));
+            k_normalize<<<nblocks, 256, 0, st>>>(t, scal.p + 2 * j + 1, V.p + (size_t)(m + j) * N, N);
             TB_CUDA(ctx, cudaGetLastError());
-            ++m;
         }
-        if (m > m_old) {
-            TB_TRY(D.sigma(V.p + (size_t)m_old * N, W.p + (size_t)m_old * N, m - m_old, f32));
-            TB_TRY(refresh_G(m_old, m));
-        }
+        TB_CUDA(ctx, cudaMemcpyAsync(hN, scal.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        g_lo = restarted ? 0 : m;
+        return finish_phase(St::WaitGS);
     }
-    if (it > max_iter) it = max_iter;
-    if (!converged) result = fail(ctx, TBSCI_ENOCONV, "Davidson did not converge within max_iter");
-    for (int k = 0; k < nroots; ++k) energies[k] = theta[k];
-    if (vecs)
-        TB_CUDA(ctx, cudaMemcpyAsync(vecs, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    TB_CUDA(ctx, cudaStreamSynchronize(st));
-    if (info) {
-        *info = tbsci_davidson_info{};
-        info->iterations = it;
-        info->converged = converged ? 1 : 0;
-        info->nsigma = D.nsig;
-        info->nsigma_f32 = D.nsig32;
-        info->iterations_f32 = it32;
-        for (int k = 0; k < nroots && k < 8; ++k) {
-            info->residual[k] = rnorm[k];
-            info->energy_f32[k] = e32[k];
+
+    tbsci_status after_GS() {
+        const int nb = (int)todo.size();
+        int acc = 0;
+        for (int j = 0; j < nb; ++j) {
+            const double t0 = std::sqrt(std::max(hN[2 * j], 0.0)), nt = std::sqrt(std::max(hN[2 * j + 1], 0.0));
+            if (!(nt > 1e-10 * t0)) continue;  // dropped: nothing new in this direction
+            if (acc != j)
+                TB_CUDA(ctx, cudaMemcpyAsync(V.p + (size_t)(m + acc) * N, V.p + (size_t)(m + j) * N, N * sizeof(double),
+                                             cudaMemcpyDeviceToDevice, st));
+            ++acc;
         }
-        info->seconds_sigma = D.t_sigma;
-        info->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - T0).count();
+        if (acc == 0) {
+            if (g_lo == 0 && m > 0) {
+                // a restart happened and nothing was added: refresh the Rayleigh matrix
+                TB_TRY(dots(V.p, m, W.p, m, red.p));
+                TB_CUDA(ctx, cudaMemcpyAsync(hG, red.p, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToHost, st));
+                return finish_phase(St::WaitG);
+            }
+            return head();
+        }
+        sig_lo = m;
+        sig_hi = m + acc;
+        state = St::NeedSigma;
+        return TBSCI_OK;
     }
-    return result;
+
+    // Runs host logic of completed phases. blocking: wait for the pending event.
+    tbsci_status poll(bool blocking, bool *progressed) {
+        *progressed = false;
+        while (state == St::WaitG || state == St::WaitR || state == St::WaitGS) {
+            if (blocking) {
+                TB_CUDA(ctx, cudaEventSynchronize(evt));
+            } else {
+                cudaError_t q = cudaEventQuery(evt);
+                if (q == cudaErrorNotReady) return TBSCI_OK;
+                TB_CUDA(ctx, q);
+            }
+            *progressed = true;
+            const St s = state;
+            if (s == St::WaitG) TB_TRY(after_G());
+            else if (s == St::WaitR) TB_TRY(after_R());
+            else TB_TRY(after_GS());
+            if (!blocking) return TBSCI_OK;  // one phase per poll keeps the driver's round short
+        }
+        return TBSCI_OK;
+    }
+
+    tbsci_status results(double *energies, double *vecs, tbsci_davidson_info *info) {
+        for (int k = 0; k < nroots; ++k) energies[k] = theta[k];
+        if (vecs)
+            TB_CUDA(ctx, cudaMemcpyAsync(vecs, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        TB_CUDA(ctx, cudaStreamSynchronize(st));
+        if (info) {
+            *info = tbsci_davidson_info{};
+            info->iterations = it;
+            info->converged = converged ? 1 : 0;
+            info->nsigma = nsig;
+            info->nsigma_f32 = nsig32;
+            info->iterations_f32 = it32;
+            for (int k = 0; k < nroots && k < 8; ++k) {
+                info->residual[k] = rnorm[k];
+                info->energy_f32[k] = e32[k];
+            }
+            info->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        }
+        return converged ? TBSCI_OK : fail(ctx, TBSCI_ENOCONV, "Davidson did not converge within max_iter");
+    }
+};
+
+tbsci_status engine_create(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
+                           DavEngine **out) {
+    tbsci_davidson_opts opt{};
+    if (o) opt = *o;
+    auto e = std::make_unique<DavEngine>();
+    TB_TRY(e->init(ctx, ham, plan, nroots, opt));
+    *out = e.release();
+    return TBSCI_OK;
+}
+
+void engine_destroy(DavEngine *e) { delete e; }
+
+bool engine_wants_sigma(DavEngine *e, const void **c, void **s, int *k, tbsci_dtype *dt) {
+    return e->wants_sigma(c, s, k, dt);
+}
+
+tbsci_status engine_sigma_done(DavEngine *e) { return e->sigma_done(); }
+
+tbsci_status engine_poll(DavEngine *e, bool blocking, bool *progressed) { return e->poll(blocking, progressed); }
+
+bool engine_done(const DavEngine *e) { return e->state == DavEngine::St::Done; }
+
+cudaStream_t engine_stream(const DavEngine *e) { return e->st; }
+
+tbsci_status engine_results(DavEngine *e, double *energies, double *vecs, tbsci_davidson_info *info) {
+    return e->results(energies, vecs, info);
+}
+
+size_t engine_device_bytes(int64_t N, int nroots, const tbsci_davidson_opts *o) {
+    const int m_max = (o && o->max_subspace > 0) ? o->max_subspace : std::max(8 * nroots, nroots + 2);
+    const int keep = (o && o->restart_keep > 0) ? o->restart_keep : std::max(nroots, m_max / 2);
+    size_t vec = (size_t)(2 * m_max + keep + 3 * nroots + 1) * N * sizeof(double);
+    if (o && o->mixed) vec += (size_t)2 * nroots * N * sizeof(float);
+    return vec + (size_t)2 * 152 * m_max * m_max * sizeof(double);
+}
+
+tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
+                          double *energies, double *vecs, tbsci_davidson_info *info) {
+    tbsci_davidson_opts opt{};
+    if (o) opt = *o;
+    if (!opt.stream) opt.stream = (tbsci_stream)ctx->stream;
+    DavEngine *raw = nullptr;
+    TB_TRY(engine_create(ctx, ham, plan, nroots, &opt, &raw));
+    std::unique_ptr<DavEngine> e(raw);
+    cudaEvent_t s0, s1;
+    TB_CUDA(ctx, cudaEventCreate(&s0));
+    TB_CUDA(ctx, cudaEventCreate(&s1));
+    double t_sigma = 0.0;
+    tbsci_status st = TBSCI_OK;
+    while (!engine_done(e.get())) {
+        const void *c;
+        void *s;
+        int k;
+        tbsci_dtype dt;
+        if (e->wants_sigma(&c, &s, &k, &dt)) {
+            cudaEventRecord(s0, e->st);
+            st = sigma_launch(ctx, ham, plan, c, s, k, dt, e->st);
+            if (st != TBSCI_OK) break;
+            cudaEventRecord(s1, e->st);
+            st = e->sigma_done();
+            if (st != TBSCI_OK) break;
+            cudaEventSynchronize(s1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, s0, s1);
+            t_sigma += ms * 1e-3;
+        }
+        bool prog;
+        st = e->poll(true, &prog);
+        if (st != TBSCI_OK) break;
+    }
+    cudaEventDestroy(s0);
+    cudaEventDestroy(s1);
+    if (st != TBSCI_OK) return st;
+    st = e->results(energies, vecs, info);
+    if (info) info->seconds_sigma = t_sigma;
+    return st;
 }
 
 tbsci_status overlap_run(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n, double *S,

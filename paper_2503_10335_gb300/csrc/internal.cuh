@@ -130,6 +130,7 @@ struct Plan {
     DevBuf<double> d_U;      // [npair][l_b]: sum_{r in occ(Ib)} (pair|rr)
     DevBuf<float> d_Uf;
     DevBuf<int32_t> d_permb; // beta columns ordered by single-link count (descending)
+    DevBuf<int32_t> d_permb2; // beta columns ordered by single + double link count (descending)
     DevBuf<int32_t> d_rowsa; // alpha rows ordered by work (descending)
     tbsci_sigma_counts counts{};
 };
@@ -161,10 +162,47 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
 // sigma.cu
 tbsci_status sigma_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const void *c, void *s,
                           int nvec, tbsci_dtype dt, cudaStream_t st);
+// One sigma of a batch: nvec vectors of one prepared space.
+struct SigmaJob {
+    const tbsci_ham *ham;
+    const Plan *plan;
+    const void *c;
+    void *s;
+    int nvec;
+};
+// Device/pinned staging of batched launches (owned by the caller, reused).
+struct BatchScratch {
+    DevBuf<unsigned char> d_stage;
+    void *h_stage[2] = {nullptr, nullptr};
+    size_t h_bytes[2] = {0, 0};
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    int flip = 0;
+    BatchScratch() = default;
+    BatchScratch(const BatchScratch &) = delete;
+    BatchScratch &operator=(const BatchScratch &) = delete;
+    ~BatchScratch();
+};
+// All jobs (same dtype) in one launch on `st`; jobs whose rows do not fit the
+// staged variant get launches of their own.
+tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs, tbsci_dtype dt, cudaStream_t st,
+                                BatchScratch *scr);
 tbsci_status diagonal_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, double *diag,
                              cudaStream_t st);
 
-// davidson.cu
+// davidson.cu: resumable Davidson engine (one solve) and its drivers
+struct DavEngine;
+tbsci_status engine_create(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
+                           DavEngine **out);
+void engine_destroy(DavEngine *e);
+// The sigma the engine needs next: c/s device pointers ([k][N], dtype dt), on the engine stream.
+bool engine_wants_sigma(DavEngine *e, const void **c, void **s, int *k, tbsci_dtype *dt);
+// Call once that sigma is enqueued on, or ordered before, the engine stream.
+tbsci_status engine_sigma_done(DavEngine *e);
+tbsci_status engine_poll(DavEngine *e, bool blocking, bool *progressed);
+bool engine_done(const DavEngine *e);
+cudaStream_t engine_stream(const DavEngine *e);
+tbsci_status engine_results(DavEngine *e, double *energies, double *vecs, tbsci_davidson_info *info);
+size_t engine_device_bytes(int64_t N, int nroots, const tbsci_davidson_opts *o);
 tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
                           double *energies, double *vecs, tbsci_davidson_info *info);
 

@@ -168,6 +168,11 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
     std::iota(idx_b.begin(), idx_b.end(), 0);
     std::stable_sort(idx_b.begin(), idx_b.end(), [&](int64_t x, int64_t y) { return s1b[x] > s1b[y]; });
     std::vector<int32_t> permb(idx_b.begin(), idx_b.end());
+    std::vector<int64_t> tot_b(lb);
+    for (int64_t i = 0; i < lb; ++i) tot_b[i] = s1b[i] + (b->h_off2[i + 1] - b->h_off2[i]);
+    std::iota(idx_b.begin(), idx_b.end(), 0);
+    std::stable_sort(idx_b.begin(), idx_b.end(), [&](int64_t x, int64_t y) { return tot_b[x] > tot_b[y]; });
+    std::vector<int32_t> permb2(idx_b.begin(), idx_b.end());
     std::vector<double> work(la);
     std::vector<int64_t> idx_a(la);
     int64_t S1a = 0, D2a = 0;
@@ -182,6 +187,8 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
     std::stable_sort(idx_a.begin(), idx_a.end(), [&](int64_t x, int64_t y) { return work[x] > work[y]; });
     std::vector<int32_t> rowsa(idx_a.begin(), idx_a.end());
     TB_CUDA(ctx, plan->d_permb.alloc(lb));
+    TB_CUDA(ctx, plan->d_permb2.alloc(lb));
+    if (lb > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_permb2.p, permb2.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice));
     TB_CUDA(ctx, plan->d_rowsa.alloc(la));
     if (lb > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_permb.p, permb.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (la > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_rowsa.p, rowsa.data(), la * sizeof(int32_t), cudaMemcpyHostToDevice));

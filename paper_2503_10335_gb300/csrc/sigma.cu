@@ -23,6 +23,8 @@
 // lives in shared memory, threads own beta columns in an order sorted by
 // single-link count so a warp's lanes have nearly equal trip counts.
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -49,22 +51,19 @@ struct SigArgs {
     const T *Eb;
     const T *V;  // [npair][npair]
     const T *U;  // [npair][lb]
-    const int32_t *permb, *rowsa;
+    const int32_t *permb, *permb2, *rowsa;
     T ecore;
 };
 
-constexpr int kThreads = 256;
-
-template <typename T, int NV, bool STAGE, bool ACCS>
-__global__ void __launch_bounds__(kThreads) k_sigma(SigArgs<T> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// One alpha row Ia of sigma (the whole body of a CTA).
+template <typename T, int NV, bool STAGE, bool ACCS, int kThreads>
+__device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia, unsigned char *smem_raw) {
     const int npair = A.npair;
     const int64_t lb = A.lb, vs = A.vstride;
     T *sV2 = reinterpret_cast<T *>(smem_raw);
     int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair);
     T *sC = reinterpret_cast<T *>(smem_raw + ((2 * npair * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15)));
     T *sAcc = sC + (STAGE ? NV * lb : 0);
-    const int64_t Ia = A.rowsa[blockIdx.x];
     const T *__restrict__ C = A.C;
     T *__restrict__ S = A.S;
     T *gAcc = S + Ia * lb;  // accumulator row when not in shared memory
@@ -103,28 +102,52 @@ __global__ void __launch_bounds__(kThreads) k_sigma(SigArgs<T> A) {
     // ---- Ja = Ia
     const T eIa = A.ecore + A.Ea[Ia];
     for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
-        const int64_t ib = A.permb[j];
+        const int64_t ib = A.permb2[j];
         T ed = eIa + A.Eb[ib];
         for (int k = 0; k < na; ++k) ed += __ldg(A.U + (size_t)sOcc[k] * lb + ib);
-        T acc[NV];
+        T acc[NV], acc2[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = ed * cval(v, Ia, ib);
+        for (int v = 0; v < NV; ++v) {
+            acc[v] = ed * cval(v, Ia, ib);
+            acc2[v] = T(0);
+        }
         const int64_t s0 = A.b_soff[ib], s1 = A.b_soff[ib + 1];
-        for (int64_t k = s0; k < s1; ++k) {
+        int64_t k = s0;
+        for (; k + 1 < s1; k += 2) {
+            const int2 e0 = __ldg(A.b_sci + k), e1 = __ldg(A.b_sci + k + 1);
+            const T x0 = __ldg(A.b_sval + k) + sV2[e0.y];
+            const T x1 = __ldg(A.b_sval + k + 1) + sV2[e1.y];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                acc[v] += x0 * cval(v, Ia, e0.x);
+                acc2[v] += x1 * cval(v, Ia, e1.x);
+            }
+        }
+        if (k < s1) {
             const int2 e = __ldg(A.b_sci + k);
             const T x = __ldg(A.b_sval + k) + sV2[e.y];
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, e.x);
         }
         const int64_t d0 = A.b_doff[ib], d1 = A.b_doff[ib + 1];
-        for (int64_t k = d0; k < d1; ++k) {
+        k = d0;
+        for (; k + 1 < d1; k += 2) {
+            const int c0 = __ldg(A.b_dcol + k), c1 = __ldg(A.b_dcol + k + 1);
+            const T x0 = __ldg(A.b_dval + k), x1 = __ldg(A.b_dval + k + 1);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                acc[v] += x0 * cval(v, Ia, c0);
+                acc2[v] += x1 * cval(v, Ia, c1);
+            }
+        }
+        if (k < d1) {
             const int col = __ldg(A.b_dcol + k);
             const T x = __ldg(A.b_dval + k);
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, col);
         }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v];
+        for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v] + acc2[v];
     }
 
     // ---- Ja = alpha singles of Ia
@@ -147,18 +170,31 @@ __global__ void __launch_bounds__(kThreads) k_sigma(SigArgs<T> A) {
         for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
             const int64_t ib = A.permb[j];
             const T coef = ha + sa * __ldg(Urow + ib);
-            T acc[NV];
+            T acc[NV], acc2[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] = acc_ref(v, ib) + coef * cval(v, Ja, ib);
+            for (int v = 0; v < NV; ++v) {
+                acc[v] = acc_ref(v, ib) + coef * cval(v, Ja, ib);
+                acc2[v] = T(0);
+            }
             const int64_t s0 = A.b_soff[ib], s1 = A.b_soff[ib + 1];
-            for (int64_t k = s0; k < s1; ++k) {
+            int64_t k = s0;
+            for (; k + 1 < s1; k += 2) {
+                const int2 e0 = __ldg(A.b_sci + k), e1 = __ldg(A.b_sci + k + 1);
+                const T x0 = sV2[e0.y], x1 = sV2[e1.y];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    acc[v] += x0 * cval(v, Ja, e0.x);
+                    acc2[v] += x1 * cval(v, Ja, e1.x);
+                }
+            }
+            if (k < s1) {
                 const int2 e = __ldg(A.b_sci + k);
                 const T x = sV2[e.y];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ja, e.x);
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v];
+            for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v] + acc2[v];
         }
     }
     __syncthreads();
@@ -166,18 +202,67 @@ __global__ void __launch_bounds__(kThreads) k_sigma(SigArgs<T> A) {
     // ---- Ja = alpha doubles of Ia, natural column order, c rows read coalesced
     const int64_t u0 = A.a_doff[Ia], u1 = A.a_doff[Ia + 1];
     for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
-        T acc[NV];
+        T acc[NV], acc2[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = acc_ref(v, j);
-        for (int64_t t = u0; t < u1; ++t) {
+        for (int v = 0; v < NV; ++v) {
+            acc[v] = acc_ref(v, j);
+            acc2[v] = T(0);
+        }
+        int64_t t = u0;
+        for (; t + 3 < u1; t += 4) {
+            const int64_t J0 = __ldg(A.a_dcol + t), J1 = __ldg(A.a_dcol + t + 1);
+            const int64_t J2 = __ldg(A.a_dcol + t + 2), J3 = __ldg(A.a_dcol + t + 3);
+            const T x0 = __ldg(A.a_dval + t), x1 = __ldg(A.a_dval + t + 1);
+            const T x2 = __ldg(A.a_dval + t + 2), x3 = __ldg(A.a_dval + t + 3);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const T c0 = __ldg(C + v * vs + J0 * lb + j), c1 = __ldg(C + v * vs + J1 * lb + j);
+                const T c2 = __ldg(C + v * vs + J2 * lb + j), c3 = __ldg(C + v * vs + J3 * lb + j);
+                acc[v] += x0 * c0;
+                acc2[v] += x1 * c1;
+                acc[v] += x2 * c2;
+                acc2[v] += x3 * c3;
+            }
+        }
+        for (; t < u1; ++t) {
             const int64_t Ja = __ldg(A.a_dcol + t);
             const T x = __ldg(A.a_dval + t);
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] += x * __ldg(C + v * vs + Ja * lb + j);
         }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) S[v * vs + Ia * lb + j] = acc[v];
+        for (int v = 0; v < NV; ++v) S[v * vs + Ia * lb + j] = acc[v] + acc2[v];
     }
+}
+
+template <typename T, int NV, bool STAGE, bool ACCS, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_sigma(SigArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sigma_row<T, NV, STAGE, ACCS, kThreads>(A, A.rowsa[blockIdx.x], smem_raw);
+}
+
+// One launch over the alpha rows of several jobs (a job = one vector of one
+// space): CTA b serves row b - cta_off[j] of job j, the last j with
+// cta_off[j] <= b. Jobs are independent, so results equal per-job launches.
+template <typename T, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_sigma_batch(const SigArgs<T> *__restrict__ jobs,
+                                                          const int64_t *__restrict__ cta_off, int njobs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SigArgs<T> sA;
+    __shared__ int64_t sRow;
+    if (threadIdx.x == 0) {
+        const int64_t b = blockIdx.x;
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cta_off[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        sA = jobs[lo];
+        sRow = sA.rowsa[b - cta_off[lo]];
+    }
+    __syncthreads();
+    sigma_row<T, 1, true, true, kThreads>(sA, sRow, smem_raw);
 }
 
 // Hd(Ia,Ib) = ecore + E_a(Ia) + E_b(Ib) + sum_{p in Ia} U[pp][Ib]
@@ -223,6 +308,7 @@ SigArgs<double> make_args<double>(const tbsci_ham *ham, const Plan *P) {
     A.V = ham->d_V.p;
     A.U = P->d_U.p;
     A.permb = P->d_permb.p;
+    A.permb2 = P->d_permb2.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = ham->ecore;
     return A;
@@ -254,6 +340,7 @@ SigArgs<float> make_args<float>(const tbsci_ham *ham, const Plan *P) {
     A.V = ham->d_Vf.p;
     A.U = P->d_Uf.p;
     A.permb = P->d_permb.p;
+    A.permb2 = P->d_permb2.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = (float)ham->ecore;
     return A;
@@ -267,9 +354,16 @@ size_t smem_bytes(int npair, int64_t lb, int nv, bool stage, bool accs) {
 
 template <typename T, int NV, bool STAGE, bool ACCS>
 tbsci_status launch_one(tbsci_ctx *ctx, SigArgs<T> A, size_t smem, cudaStream_t st) {
-    auto kern = k_sigma<T, NV, STAGE, ACCS>;
-    TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)A.la, kThreads, smem, st>>>(A);
+    // wide CTAs (16 warps) keep the FP64 pipe fed on long rows; short rows take 4 warps
+    if (A.lb >= 1024) {
+        auto kern = k_sigma<T, NV, STAGE, ACCS, 512>;
+        TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<(unsigned)A.la, 512, smem, st>>>(A);
+    } else {
+        auto kern = k_sigma<T, NV, STAGE, ACCS, 128>;
+        TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<(unsigned)A.la, 128, smem, st>>>(A);
+    }
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
 }
@@ -310,7 +404,82 @@ tbsci_status launch_typed(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, c
     return TBSCI_OK;
 }
 
+constexpr int kBatchThreads = 256;
+
+template <typename T>
+tbsci_status launch_batch_typed(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs, cudaStream_t st, BatchScratch *scr) {
+    std::vector<SigArgs<T>> args;
+    std::vector<int64_t> off;
+    size_t smem = 0;
+    int64_t ctas = 0;
+    for (int j = 0; j < njobs; ++j) {
+        SigArgs<T> A = make_args<T>(jobs[j].ham, jobs[j].plan);
+        if (A.la == 0 || A.lb == 0) continue;
+        const size_t sm = smem_bytes<T>(A.npair, A.lb, 1, true, true);
+        if (sm > ctx->smem_optin) {  // rows too long to stage: a launch of its own
+            TB_TRY(launch_typed<T>(ctx, jobs[j].ham, jobs[j].plan, static_cast<const T *>(jobs[j].c),
+                                   static_cast<T *>(jobs[j].s), jobs[j].nvec, st));
+            continue;
+        }
+        smem = std::max(smem, sm);
+        for (int v = 0; v < jobs[j].nvec; ++v) {
+            A.C = static_cast<const T *>(jobs[j].c) + (size_t)v * A.vstride;
+            A.S = static_cast<T *>(jobs[j].s) + (size_t)v * A.vstride;
+            args.push_back(A);
+            off.push_back(ctas);
+            ctas += A.la;
+        }
+    }
+    if (args.empty()) return TBSCI_OK;
+    TB_CHECK(ctx, ctas <= INT32_MAX, TBSCI_EINVAL, "batched sigma: too many rows in one launch");
+    const size_t abytes = args.size() * sizeof(SigArgs<T>), obytes = off.size() * sizeof(int64_t);
+    const size_t need = ((abytes + 255) & ~size_t(255)) + obytes;
+    // double-buffered pinned staging: wait for the copy that last used this half
+    const int half = scr->flip ^= 1;
+    if (scr->h_bytes[half] < need) {
+        if (scr->h_stage[half]) {
+            TB_CUDA(ctx, cudaEventSynchronize(scr->copied[half]));
+            cudaFreeHost(scr->h_stage[half]);
+            scr->h_stage[half] = nullptr;
+        }
+        TB_CUDA(ctx, cudaMallocHost(&scr->h_stage[half], 2 * need));
+        scr->h_bytes[half] = 2 * need;
+    }
+    if (!scr->copied[half]) TB_CUDA(ctx, cudaEventCreateWithFlags(&scr->copied[half], cudaEventDisableTiming));
+    TB_CUDA(ctx, cudaEventSynchronize(scr->copied[half]));
+    unsigned char *h = static_cast<unsigned char *>(scr->h_stage[half]);
+    std::memcpy(h, args.data(), abytes);
+    std::memcpy(h + ((abytes + 255) & ~size_t(255)), off.data(), obytes);
+    if (scr->d_stage.n < need) TB_CUDA(ctx, scr->d_stage.alloc(2 * need));
+    TB_CUDA(ctx, cudaMemcpyAsync(scr->d_stage.p, h, need, cudaMemcpyHostToDevice, st));
+    TB_CUDA(ctx, cudaEventRecord(scr->copied[half], st));
+    const SigArgs<T> *dargs = reinterpret_cast<const SigArgs<T> *>(scr->d_stage.p);
+    const int64_t *doff = reinterpret_cast<const int64_t *>(scr->d_stage.p + ((abytes + 255) & ~size_t(255)));
+    auto kern = k_sigma_batch<T, kBatchThreads>;
+    TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)ctas, kBatchThreads, smem, st>>>(dargs, doff, (int)args.size());
+    TB_CUDA(ctx, cudaGetLastError());
+    return TBSCI_OK;
+}
+
 }  // namespace
+
+BatchScratch::~BatchScratch() {
+    for (int i = 0; i < 2; ++i) {
+        if (copied[i]) {
+            cudaEventSynchronize(copied[i]);
+            cudaEventDestroy(copied[i]);
+        }
+        if (h_stage[i]) cudaFreeHost(h_stage[i]);
+    }
+}
+
+tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs, tbsci_dtype dt, cudaStream_t st,
+                                BatchScratch *scr) {
+    if (dt == TBSCI_F64) return launch_batch_typed<double>(ctx, jobs, njobs, st, scr);
+    if (dt == TBSCI_F32) return launch_batch_typed<float>(ctx, jobs, njobs, st, scr);
+    return fail(ctx, TBSCI_EINVAL, "unknown dtype");
+}
 
 tbsci_status sigma_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const void *c, void *s, int nvec,
                           tbsci_dtype dt, cudaStream_t st) {
