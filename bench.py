@@ -180,6 +180,84 @@ def _config(wl, nvec, dtype):
             else "L2 flushed between steps"}
 
 
+def _serving_requests(nreq, seed, max_count):
+    """The serving stream's requests (host data), in arrival order."""
+    from tbsci_inputs import selected_strings, serving_stream, synth_hamiltonian
+    reqs = []
+    for r in serving_stream(nreq=nreq, seed=seed, rate_hz=1.0, hi=max_count):
+        h, eri, ecore = synth_hamiltonian(r["norb"], r["seed_ints"])
+        sel = selected_strings(r["norb"], r["nelec"], r["count"], r["seed_sel"])
+        reqs.append(dict(norb=r["norb"], nalpha=r["nelec"], nbeta=r["nelec"], h=h, eri=eri, ecore=ecore,
+                         alpha=sel, beta=sel, nroots=r["nroots"], gap=r["t_arrival"]))
+    return reqs
+
+
+def _fifo_latencies(arrivals, service):
+    """Latencies of a single FIFO server (one solve at a time)."""
+    t_free, lat = 0.0, []
+    for a, s in zip(arrivals, service):
+        start = max(a, t_free)
+        t_free = start + s
+        lat.append(t_free - a)
+    return lat, t_free
+
+
+def run_serving(args):
+    """Serving stream (Poisson arrivals, norb 8..16, 50..max strings per spin, 1-3
+    roots): FP64 one-at-a-time vs the mixed-precision continuous-batching server,
+    at arrival rates 0.5x and 2x the FP64 sequential service rate."""
+    import torch
+    import paper_2503_10335_gb300 as tb
+    reqs = _serving_requests(args.nreq, 5005, args.max_count)
+    ctx = tb.Context(0)
+    # calibration: FP64 one-at-a-time service times (set-up + solve through the C ABI)
+    service, e64 = [], []
+    for r in reqs:
+        t0 = time.perf_counter()
+        sp = tb.Space(ctx, r["norb"], r["nalpha"], r["nbeta"], r["h"], r["eri"], r["ecore"], alpha=r["alpha"],
+                      beta=r["beta"])
+        e, info = sp.davidson(r["nroots"])
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+        e64.append(e)
+        sp.close()
+    ctx.close()
+    mu = len(reqs) / sum(service)
+    base_gaps = np.array([r["gap"] for r in reqs])  # unit-rate Poisson arrival times
+    out = {"metric": METRIC, "mode": "serving", "nreq": len(reqs), "fp64_service_rate_per_s": mu,
+           "fp64_total_service_s": sum(service), "max_strings": args.max_count, "rates": []}
+    for mult in (0.5, 2.0):
+        lam = mult * mu
+        arrivals = base_gaps / lam
+        lat64, end64 = _fifo_latencies(arrivals, service)
+        srv = tb.Server(0)
+        t0 = time.perf_counter()
+        tickets = []
+        for r, a in zip(reqs, arrivals):
+            delay = a - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            kw = {k: r[k] for k in ("norb", "nalpha", "nbeta", "h", "eri", "ecore", "alpha", "beta", "nroots")}
+            tickets.append(srv.submit(mixed=True, **kw))
+        res = []
+        for t in tickets:
+            st, d = srv.poll(t, timeout_ms=-1)
+            res.append(d)
+        makespan = time.perf_counter() - t0
+        srv.close()
+        lat = [d["t_done"] - d["t_submit"] for d in res]
+        err = max(float(np.max(np.abs(np.array(d["energies"]) - e))) for d, e in zip(res, e64))
+        out["rates"].append({
+            "arrival_rate_per_s": lam, "x_fp64_rate": mult,
+            "fp64_one_at_a_time": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                                   "throughput_per_s": len(reqs) / end64},
+            "mixed_batched": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                              "throughput_per_s": len(reqs) / makespan,
+                              "statuses": sorted(set(d["status"] for d in res))},
+            "max_energy_diff_vs_fp64_Eh": err})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,11 +270,16 @@ def main():
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--serving", action="store_true", help="serving stream instead of the sigma bench")
+    ap.add_argument("--nreq", type=int, default=48)
+    ap.add_argument("--max-count", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
     import paper_2503_10335_gb300 as tb

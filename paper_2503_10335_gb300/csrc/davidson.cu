@@ -38,16 +38,24 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(const double *__restrict__
     for (int i = 0; i < kMA; ++i)
 #pragma unroll
         for (int j = 0; j < kMB; ++j) acc[i][j] = 0.0;
-    for (int64_t K = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; K < N; K += (int64_t)gridDim.x * kDotThreads) {
-        double b[kMB];
+    // two elements per thread per step: up to 2 * (8 + 4) independent loads in flight
+    const int64_t step = (int64_t)gridDim.x * kDotThreads * 2;
+    for (int64_t K0 = blockIdx.x * (int64_t)kDotThreads * 2 + threadIdx.x; K0 < N; K0 += step) {
+        const int64_t K1 = K0 + kDotThreads;
+        const bool h1 = K1 < N;
+        double b0[kMB], b1[kMB];
 #pragma unroll
-        for (int j = 0; j < kMB; ++j) b[j] = j < nb ? __ldg(B + (size_t)(j0 + j) * N + K) : 0.0;
+        for (int j = 0; j < kMB; ++j) {
+            b0[j] = j < nb ? __ldg(B + (size_t)(j0 + j) * N + K0) : 0.0;
+            b1[j] = (j < nb && h1) ? __ldg(B + (size_t)(j0 + j) * N + K1) : 0.0;
+        }
 #pragma unroll
         for (int i = 0; i < kMA; ++i) {
             if (i < na) {
-                double a = __ldg(A + (size_t)(i0 + i) * N + K);
+                const double a0 = __ldg(A + (size_t)(i0 + i) * N + K0);
+                const double a1 = h1 ? __ldg(A + (size_t)(i0 + i) * N + K1) : 0.0;
 #pragma unroll
-                for (int j = 0; j < kMB; ++j) acc[i][j] = fma(a, b[j], acc[i][j]);
+                for (int j = 0; j < kMB; ++j) acc[i][j] = fma(a1, b1[j], fma(a0, b0[j], acc[i][j]));
             }
         }
     }
@@ -81,25 +89,48 @@ __global__ void k_reduce_partials(const double *partial, int nblocks, int ldp, i
 constexpr int kMaxBasis = 128;
 constexpr int kMaxOut = 8;
 
-// out[k][K] = beta * out[k][K] + yscale * sum_i Y[i][k] * A[i][K], k < kout <= 8
+// out[k][K] = beta * out[k][K] + yscale * sum_i Y[i][k] * A[i][K], k < kout <= 8.
+// Each thread handles 4 elements spaced blockDim apart per step, so every row
+// read issues 4 independent loads (memory-level parallelism for HBM).
 __global__ void __launch_bounds__(256) k_lincomb(const double *__restrict__ A, int m, double *out, int kout, int64_t N,
                                                  double beta, const double *__restrict__ Y, double yscale) {
     __shared__ double sY[kMaxBasis * kMaxOut];
     for (int x = threadIdx.x; x < m * kout; x += blockDim.x) sY[x] = yscale * Y[x];
     __syncthreads();
-    for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < N; K += (int64_t)gridDim.x * blockDim.x) {
-        double acc[kMaxOut];
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t K0 = (int64_t)blockIdx.x * blockDim.x * 4 + threadIdx.x; K0 < N; K0 += step) {
+        double acc[kMaxOut][4];
 #pragma unroll
-        for (int k = 0; k < kMaxOut; ++k) acc[k] = (k < kout && beta != 0.0) ? beta * out[(size_t)k * N + K] : 0.0;
+        for (int k = 0; k < kMaxOut; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t K = K0 + (int64_t)u * blockDim.x;
+                acc[k][u] = (k < kout && beta != 0.0 && K < N) ? beta * out[(size_t)k * N + K] : 0.0;
+            }
+#pragma unroll 2
         for (int i = 0; i < m; ++i) {
-            double a = __ldg(A + (size_t)i * N + K);
+            double a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t K = K0 + (int64_t)u * blockDim.x;
+                a[u] = K < N ? __ldg(A + (size_t)i * N + K) : 0.0;
+            }
 #pragma unroll
             for (int k = 0; k < kMaxOut; ++k)
-                if (k < kout) acc[k] = fma(sY[i * kout + k], a, acc[k]);
+                if (k < kout) {
+                    const double y = sY[i * kout + k];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[k][u] = fma(y, a[u], acc[k][u]);
+                }
         }
 #pragma unroll
         for (int k = 0; k < kMaxOut; ++k)
-            if (k < kout) out[(size_t)k * N + K] = acc[k];
+            if (k < kout)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t K = K0 + (int64_t)u * blockDim.x;
+                    if (K < N) out[(size_t)k * N + K] = acc[k][u];
+                }
     }
 }
 
@@ -128,8 +159,8 @@ __global__ void __launch_bounds__(256) k_lincomb_cols(const double *__restrict__
     }
 }
 
-// y = x / sqrt(*nrm2) (zero when the norm is zero)
-__global__ void k_normalize(const double *__restrict__ x, const double *__restrict__ nrm2, double *y, int64_t N) {
+// y = x / sqrt(*nrm2) (zero when the norm is zero); y may be x
+__global__ void k_normalize(const double *x, const double *__restrict__ nrm2, double *y, int64_t N) {
     const double n2 = *nrm2;
     const double s = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
     for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < N; K += (int64_t)gridDim.x * blockDim.x)
@@ -150,16 +181,22 @@ __global__ void __launch_bounds__(kDotThreads) k_residual(const double *__restri
     double acc[kMaxOut];
 #pragma unroll
     for (int k = 0; k < kMaxOut; ++k) acc[k] = 0.0;
-    for (int64_t K = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; K < N; K += (int64_t)gridDim.x * kDotThreads) {
-        double d = diag[K];
+    const int64_t step = (int64_t)gridDim.x * kDotThreads * 2;
+    for (int64_t K0 = blockIdx.x * (int64_t)kDotThreads * 2 + threadIdx.x; K0 < N; K0 += step) {
 #pragma unroll
-        for (int k = 0; k < kMaxOut; ++k) {
-            if (k < nroots) {
-                double r = WY[(size_t)k * N + K] - theta[k] * X[(size_t)k * N + K];
-                acc[k] = fma(r, r, acc[k]);
-                double den = theta[k] - d;
-                if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
-                T[(size_t)k * N + K] = r / den;
+        for (int u = 0; u < 2; ++u) {
+            const int64_t K = K0 + (int64_t)u * kDotThreads;
+            if (K >= N) break;
+            const double d = diag[K];
+#pragma unroll
+            for (int k = 0; k < kMaxOut; ++k) {
+                if (k < nroots) {
+                    const double r = WY[(size_t)k * N + K] - theta[k] * X[(size_t)k * N + K];
+                    acc[k] = fma(r, r, acc[k]);
+                    double den = theta[k] - d;
+                    if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
+                    T[(size_t)k * N + K] = r / den;
+                }
             }
         }
     }
@@ -379,7 +416,7 @@ struct DavEngine {
         TB_CUDA(ctx, dY2.alloc((size_t)m_max * m_max));
         TB_CUDA(ctx, dtheta.alloc(kMaxOut));
         TB_CUDA(ctx, scal.alloc(2 * kMaxOut));
-        TB_CUDA(ctx, coef.alloc(m_max));
+        TB_CUDA(ctx, coef.alloc((size_t)m_max * kMaxOut));
         TB_CUDA(ctx, cudaMallocHost(&hG, (size_t)m_max * m_max * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hY, (size_t)m_max * m_max * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hY2, (size_t)m_max * m_max * sizeof(double)));
@@ -590,17 +627,28 @@ struct DavEngine {
             restarted = true;
         }
         if (todo.empty()) return head();
-        // two Gram-Schmidt passes per correction against the basis, on the device
+        // Corrections into the free basis slots, then block Gram-Schmidt on the
+        // device: two passes of S = V^T T, T -= V S against the basis (reads the
+        // basis 4 times per iteration), then two in-block passes per vector.
         const int nb = (int)todo.size();
+        double *Tb = V.p + (size_t)m * N;
         for (int j = 0; j < nb; ++j) {
-            double *t = T.p + (size_t)todo[j] * N;
-            TB_TRY(dots(t, 1, t, 1, scal.p + 2 * j));
-            for (int pass = 0; pass < 2; ++pass) {
-                TB_TRY(dots(V.p, m + j, t, 1, coef.p));
-                TB_TRY(lincomb(V.p, m + j, t, 1, 1.0, coef.p, -1.0));
+            TB_CUDA(ctx, cudaMemcpyAsync(Tb + (size_t)j * N, T.p + (size_t)todo[j] * N, N * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+            TB_TRY(dots(Tb + (size_t)j * N, 1, Tb + (size_t)j * N, 1, scal.p + 2 * j));
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            TB_TRY(dots(V.p, m, Tb, nb, coef.p));
+            TB_TRY(lincomb(V.p, m, Tb, nb, 1.0, coef.p, -1.0));
+        }
+        for (int j = 0; j < nb; ++j) {
+            double *t = Tb + (size_t)j * N;
+            for (int pass = 0; pass < 2 && j > 0; ++pass) {
+                TB_TRY(dots(Tb, j, t, 1, coef.p));
+                TB_TRY(lincomb(Tb, j, t, 1, 1.0, coef.p, -1.0));
             }
             TB_TRY(dots(t, 1, t, 1, scal.p + 2 * j + 1));
-            k_normalize<<<nblocks, 256, 0, st>>>(t, scal.p + 2 * j + 1, V.p + (size_t)(m + j) * N, N);
+            k_normalize<<<nblocks, 256, 0, st>>>(t, scal.p + 2 * j + 1, t, N);
             TB_CUDA(ctx, cudaGetLastError());
         }
         TB_CUDA(ctx, cudaMemcpyAsync(hN, scal.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -131,6 +131,17 @@ struct Plan {
     DevBuf<float> d_Uf;
     DevBuf<int32_t> d_permb; // beta columns ordered by single-link count (descending)
     DevBuf<int32_t> d_permb2; // beta columns ordered by single + double link count (descending)
+    // Beta links in sliced-ELL layout: per slice of 32 consecutive columns of a
+    // column order, entry k of lane i at off[slice] + 32 k + i, padded to the
+    // slice's longest list with zero-coefficient entries (coalesced warp loads).
+    DevBuf<int64_t> d_s1_off, d_s2_off, d_d2_off;
+    DevBuf<int32_t> d_s1_w, d_s2_w, d_d2_w;
+    DevBuf<int2> d_s1_ci, d_s2_ci;       // singles {target, 2*pair + neg}; s1: permb order, s2: permb2 order
+    DevBuf<double> d_s2_val, d_d2_val;   // string-Hamiltonian values (permb2 order)
+    DevBuf<float> d_s2_valf, d_d2_valf;
+    DevBuf<int32_t> d_d2_col;            // doubles target (permb2 order)
+    DevBuf<double> d_U1, d_U2, d_Eb2;    // Coulomb table / beta energies with columns in permb / permb2 order
+    DevBuf<float> d_U1f, d_U2f, d_Eb2f;
     DevBuf<int32_t> d_rowsa; // alpha rows ordered by work (descending)
     tbsci_sigma_counts counts{};
 };

@@ -90,6 +90,85 @@ __global__ void k_coulomb_table(const uint64_t *__restrict__ strb, int64_t lb, i
     Uf[(size_t)pr * lb + ib] = (float)u;
 }
 
+// Sliced-ELL copy of CSR rows taken in the column order `perm` (see Plan).
+__global__ void k_sell_singles(const int32_t *__restrict__ perm, int64_t lb, const int64_t *__restrict__ off,
+                               const int2 *__restrict__ sci, const double *__restrict__ sval,
+                               const int64_t *__restrict__ soff, const int32_t *__restrict__ sw, int64_t nsl,
+                               int zero_idx, int2 *out_ci, double *out_val, float *out_valf) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nsl * 32) return;
+    const int64_t sl = t >> 5, j = t;
+    const int lane = (int)(t & 31);
+    const int64_t ib = j < lb ? perm[j] : 0;
+    const int64_t a = j < lb ? off[ib] : 0, cnt = j < lb ? off[ib + 1] - a : 0;
+    const int64_t base = soff[sl] + lane;
+    const int w = sw[sl];
+    for (int k = 0; k < w; ++k) {
+        const int64_t pos = base + 32 * (int64_t)k;
+        if (k < cnt) {
+            out_ci[pos] = sci[a + k];
+            if (out_val) {
+                out_val[pos] = sval[a + k];
+                out_valf[pos] = (float)sval[a + k];
+            }
+        } else {
+            out_ci[pos] = make_int2((int)ib, zero_idx);
+            if (out_val) {
+                out_val[pos] = 0.0;
+                out_valf[pos] = 0.f;
+            }
+        }
+    }
+}
+
+__global__ void k_sell_doubles(const int32_t *__restrict__ perm, int64_t lb, const int64_t *__restrict__ off,
+                               const int32_t *__restrict__ dcol, const double *__restrict__ dval,
+                               const int64_t *__restrict__ soff, const int32_t *__restrict__ sw, int64_t nsl,
+                               int32_t *out_col, double *out_val, float *out_valf) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nsl * 32) return;
+    const int64_t sl = t >> 5, j = t;
+    const int lane = (int)(t & 31);
+    const int64_t ib = j < lb ? perm[j] : 0;
+    const int64_t a = j < lb ? off[ib] : 0, cnt = j < lb ? off[ib + 1] - a : 0;
+    const int64_t base = soff[sl] + lane;
+    const int w = sw[sl];
+    for (int k = 0; k < w; ++k) {
+        const int64_t pos = base + 32 * (int64_t)k;
+        const bool real = k < cnt;
+        out_col[pos] = real ? dcol[a + k] : (int32_t)ib;
+        out_val[pos] = real ? dval[a + k] : 0.0;
+        out_valf[pos] = real ? (float)dval[a + k] : 0.f;
+    }
+}
+
+// out[pr][j] = in[pr][perm[j]] (rows of length lb)
+__global__ void k_permute_cols(const double *__restrict__ in, int64_t rows, int64_t lb, const int32_t *__restrict__ perm,
+                               double *out, float *outf) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = blockIdx.y;
+    if (j >= lb || r >= rows) return;
+    const double v = in[r * lb + perm[j]];
+    out[r * lb + j] = v;
+    outf[r * lb + j] = (float)v;
+}
+
+// per-slice widths and offsets of a sliced-ELL layout over `perm`
+void sell_shape(const std::vector<int32_t> &perm, const std::vector<int64_t> &off, std::vector<int64_t> &soff,
+                std::vector<int32_t> &sw, int64_t &total) {
+    const int64_t lb = (int64_t)perm.size(), nsl = (lb + 31) / 32;
+    soff.assign(nsl, 0);
+    sw.assign(nsl, 0);
+    total = 0;
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+        int64_t w = 0;
+        for (int64_t j = sl * 32; j < std::min(lb, sl * 32 + 32); ++j) w = std::max(w, off[perm[j] + 1] - off[perm[j]]);
+        soff[sl] = total;
+        sw[sl] = (int32_t)w;
+        total += 32 * w;
+    }
+}
+
 tbsci_status build_spin(tbsci_ctx *ctx, const tbsci_ham *ham, const tbsci_tables *t, SpinPlan &sp, cudaStream_t st) {
     const int n = ham->norb;
     sp.l = t->count;
@@ -192,6 +271,73 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
     TB_CUDA(ctx, plan->d_rowsa.alloc(la));
     if (lb > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_permb.p, permb.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (la > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_rowsa.p, rowsa.data(), la * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // sliced-ELL beta links and column-permuted tables
+    {
+        const int64_t nsl = (lb + 31) / 32;
+        std::vector<int64_t> so;
+        std::vector<int32_t> sw;
+        int64_t tot = 0;
+        const unsigned g = (unsigned)std::max<int64_t>(1, (nsl * 32 + 255) / 256);
+        const int zero_idx = 2 * ham->npair;
+        // singles in permb order
+        sell_shape(permb, b->h_off1, so, sw, tot);
+        TB_CUDA(ctx, plan->d_s1_off.alloc(nsl));
+        TB_CUDA(ctx, plan->d_s1_w.alloc(nsl));
+        TB_CUDA(ctx, plan->d_s1_ci.alloc(std::max<int64_t>(tot, 1)));
+        if (nsl > 0) {
+            TB_CUDA(ctx, cudaMemcpy(plan->d_s1_off.p, so.data(), nsl * sizeof(int64_t), cudaMemcpyHostToDevice));
+            TB_CUDA(ctx, cudaMemcpy(plan->d_s1_w.p, sw.data(), nsl * sizeof(int32_t), cudaMemcpyHostToDevice));
+            k_sell_singles<<<g, 256, 0, st>>>(plan->d_permb.p, lb, b->d_off1.p, plan->B.d_sci.p, nullptr,
+                                              plan->d_s1_off.p, plan->d_s1_w.p, nsl, zero_idx, plan->d_s1_ci.p,
+                                              nullptr, nullptr);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+        // singles with values in permb2 order
+        sell_shape(permb2, b->h_off1, so, sw, tot);
+        TB_CUDA(ctx, plan->d_s2_off.alloc(nsl));
+        TB_CUDA(ctx, plan->d_s2_w.alloc(nsl));
+        TB_CUDA(ctx, plan->d_s2_ci.alloc(std::max<int64_t>(tot, 1)));
+        TB_CUDA(ctx, plan->d_s2_val.alloc(std::max<int64_t>(tot, 1)));
+        TB_CUDA(ctx, plan->d_s2_valf.alloc(std::max<int64_t>(tot, 1)));
+        if (nsl > 0) {
+            TB_CUDA(ctx, cudaMemcpy(plan->d_s2_off.p, so.data(), nsl * sizeof(int64_t), cudaMemcpyHostToDevice));
+            TB_CUDA(ctx, cudaMemcpy(plan->d_s2_w.p, sw.data(), nsl * sizeof(int32_t), cudaMemcpyHostToDevice));
+            k_sell_singles<<<g, 256, 0, st>>>(plan->d_permb2.p, lb, b->d_off1.p, plan->B.d_sci.p, plan->B.d_sval.p,
+                                              plan->d_s2_off.p, plan->d_s2_w.p, nsl, zero_idx, plan->d_s2_ci.p,
+                                              plan->d_s2_val.p, plan->d_s2_valf.p);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+        // doubles in permb2 order
+        sell_shape(permb2, b->h_off2, so, sw, tot);
+        TB_CUDA(ctx, plan->d_d2_off.alloc(nsl));
+        TB_CUDA(ctx, plan->d_d2_w.alloc(nsl));
+        TB_CUDA(ctx, plan->d_d2_col.alloc(std::max<int64_t>(tot, 1)));
+        TB_CUDA(ctx, plan->d_d2_val.alloc(std::max<int64_t>(tot, 1)));
+        TB_CUDA(ctx, plan->d_d2_valf.alloc(std::max<int64_t>(tot, 1)));
+        if (nsl > 0) {
+            TB_CUDA(ctx, cudaMemcpy(plan->d_d2_off.p, so.data(), nsl * sizeof(int64_t), cudaMemcpyHostToDevice));
+            TB_CUDA(ctx, cudaMemcpy(plan->d_d2_w.p, sw.data(), nsl * sizeof(int32_t), cudaMemcpyHostToDevice));
+            k_sell_doubles<<<g, 256, 0, st>>>(plan->d_permb2.p, lb, b->d_off2.p, plan->B.d_dcol.p, plan->B.d_dval.p,
+                                              plan->d_d2_off.p, plan->d_d2_w.p, nsl, plan->d_d2_col.p,
+                                              plan->d_d2_val.p, plan->d_d2_valf.p);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+        const int64_t np = ham->npair;
+        TB_CUDA(ctx, plan->d_U1.alloc(np * lb));
+        TB_CUDA(ctx, plan->d_U1f.alloc(np * lb));
+        TB_CUDA(ctx, plan->d_U2.alloc(np * lb));
+        TB_CUDA(ctx, plan->d_U2f.alloc(np * lb));
+        TB_CUDA(ctx, plan->d_Eb2.alloc(lb));
+        TB_CUDA(ctx, plan->d_Eb2f.alloc(lb));
+        if (lb > 0) {
+            dim3 gu((unsigned)((lb + 127) / 128), (unsigned)np);
+            k_permute_cols<<<gu, 128, 0, st>>>(plan->d_U.p, np, lb, plan->d_permb.p, plan->d_U1.p, plan->d_U1f.p);
+            k_permute_cols<<<gu, 128, 0, st>>>(plan->d_U.p, np, lb, plan->d_permb2.p, plan->d_U2.p, plan->d_U2f.p);
+            dim3 ge((unsigned)((lb + 127) / 128), 1);
+            k_permute_cols<<<ge, 128, 0, st>>>(plan->B.d_E.p, 1, lb, plan->d_permb2.p, plan->d_Eb2.p, plan->d_Eb2f.p);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+    }
     // work counts: non-zeros of H by class (Sec. II.C, Table I)
     tbsci_sigma_counts &c = plan->counts;
     c.ndet = la * lb;

@@ -53,6 +53,14 @@ struct SigArgs {
     const T *U;  // [npair][lb]
     const int32_t *permb, *permb2, *rowsa;
     T ecore;
+    // sliced-ELL beta links (see Plan): singles in permb order; singles with
+    // values and doubles in permb2 order; tables with columns in those orders
+    const int64_t *s1_off, *s2_off, *d2_off;
+    const int32_t *s1_w, *s2_w, *d2_w;
+    const int2 *s1_ci, *s2_ci;
+    const T *s2_val, *d2_val;
+    const int32_t *d2_col;
+    const T *U1, *U2, *Eb2;
 };
 
 // One alpha row Ia of sigma (the whole body of a CTA).
@@ -60,9 +68,9 @@ template <typename T, int NV, bool STAGE, bool ACCS, int kThreads>
 __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia, unsigned char *smem_raw) {
     const int npair = A.npair;
     const int64_t lb = A.lb, vs = A.vstride;
-    T *sV2 = reinterpret_cast<T *>(smem_raw);
-    int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair);
-    T *sC = reinterpret_cast<T *>(smem_raw + ((2 * npair * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15)));
+    T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2*npair + 2], last two entries zero (padding)
+    int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair + 2);
+    T *sC = reinterpret_cast<T *>(smem_raw + (((2 * npair + 2) * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15)));
     T *sAcc = sC + (STAGE ? NV * lb : 0);
     const T *__restrict__ C = A.C;
     T *__restrict__ S = A.S;
@@ -86,6 +94,8 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
             int p = __ffsll((long long)s) - 1;
             sOcc[k++] = p * (p + 1) / 2 + p;
         }
+        sV2[2 * npair] = T(0);
+        sV2[2 * npair + 1] = T(0);
     }
     __syncthreads();
     const int na = A.na;
@@ -99,58 +109,68 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
     stage(Ia);
     __syncthreads();
 
-    // ---- Ja = Ia
+    // ---- Ja = Ia: columns in permb2 order, beta links read as coalesced sliced-ELL rows
     const T eIa = A.ecore + A.Ea[Ia];
     for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
         const int64_t ib = A.permb2[j];
-        T ed = eIa + A.Eb[ib];
-        for (int k = 0; k < na; ++k) ed += __ldg(A.U + (size_t)sOcc[k] * lb + ib);
+        const int64_t sl = j >> 5;
+        const int lane = (int)(j & 31);
+        T ed = eIa + __ldg(A.Eb2 + j);
+        for (int k = 0; k < na; ++k) ed += __ldg(A.U2 + (size_t)sOcc[k] * lb + j);
         T acc[NV], acc2[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             acc[v] = ed * cval(v, Ia, ib);
             acc2[v] = T(0);
         }
-        const int64_t s0 = A.b_soff[ib], s1 = A.b_soff[ib + 1];
-        int64_t k = s0;
-        for (; k + 1 < s1; k += 2) {
-            const int2 e0 = __ldg(A.b_sci + k), e1 = __ldg(A.b_sci + k + 1);
-            const T x0 = __ldg(A.b_sval + k) + sV2[e0.y];
-            const T x1 = __ldg(A.b_sval + k + 1) + sV2[e1.y];
+        {
+            const int2 *ci = A.s2_ci + A.s2_off[sl] + lane;
+            const T *cv = A.s2_val + A.s2_off[sl] + lane;
+            const int w = A.s2_w[sl];
+            int k = 0;
+            for (; k + 1 < w; k += 2) {
+                const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                const T x0 = __ldg(cv + 32 * k) + sV2[e0.y];
+                const T x1 = __ldg(cv + 32 * (k + 1)) + sV2[e1.y];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                acc[v] += x0 * cval(v, Ia, e0.x);
-                acc2[v] += x1 * cval(v, Ia, e1.x);
+                for (int v = 0; v < NV; ++v) {
+                    acc[v] += x0 * cval(v, Ia, e0.x);
+                    acc2[v] += x1 * cval(v, Ia, e1.x);
+                }
+            }
+            if (k < w) {
+                const int2 e = __ldg(ci + 32 * k);
+                const T x = __ldg(cv + 32 * k) + sV2[e.y];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, e.x);
             }
         }
-        if (k < s1) {
-            const int2 e = __ldg(A.b_sci + k);
-            const T x = __ldg(A.b_sval + k) + sV2[e.y];
+        {
+            const int32_t *dc = A.d2_col + A.d2_off[sl] + lane;
+            const T *dv = A.d2_val + A.d2_off[sl] + lane;
+            const int w = A.d2_w[sl];
+            int k = 0;
+            for (; k + 1 < w; k += 2) {
+                const int c0 = __ldg(dc + 32 * k), c1 = __ldg(dc + 32 * (k + 1));
+                const T x0 = __ldg(dv + 32 * k), x1 = __ldg(dv + 32 * (k + 1));
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, e.x);
-        }
-        const int64_t d0 = A.b_doff[ib], d1 = A.b_doff[ib + 1];
-        k = d0;
-        for (; k + 1 < d1; k += 2) {
-            const int c0 = __ldg(A.b_dcol + k), c1 = __ldg(A.b_dcol + k + 1);
-            const T x0 = __ldg(A.b_dval + k), x1 = __ldg(A.b_dval + k + 1);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                acc[v] += x0 * cval(v, Ia, c0);
-                acc2[v] += x1 * cval(v, Ia, c1);
+                for (int v = 0; v < NV; ++v) {
+                    acc[v] += x0 * cval(v, Ia, c0);
+                    acc2[v] += x1 * cval(v, Ia, c1);
+                }
             }
-        }
-        if (k < d1) {
-            const int col = __ldg(A.b_dcol + k);
-            const T x = __ldg(A.b_dval + k);
+            if (k < w) {
+                const int col = __ldg(dc + 32 * k);
+                const T x = __ldg(dv + 32 * k);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, col);
+                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, col);
+            }
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v] + acc2[v];
     }
 
-    // ---- Ja = alpha singles of Ia
+    // ---- Ja = alpha singles of Ia: columns in permb order
     const int64_t t0 = A.a_soff[Ia], t1 = A.a_soff[Ia + 1];
     for (int64_t t = t0; t < t1; ++t) {
         const int2 ea = __ldg(A.a_sci + t);
@@ -166,20 +186,23 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
         }
         stage(Ja);
         __syncthreads();
-        const T *__restrict__ Urow = A.U + (size_t)pr * lb;
+        const T *__restrict__ Urow = A.U1 + (size_t)pr * lb;
         for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
             const int64_t ib = A.permb[j];
-            const T coef = ha + sa * __ldg(Urow + ib);
+            const int64_t sl = j >> 5;
+            const int lane = (int)(j & 31);
+            const T coef = ha + sa * __ldg(Urow + j);
             T acc[NV], acc2[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 acc[v] = acc_ref(v, ib) + coef * cval(v, Ja, ib);
                 acc2[v] = T(0);
             }
-            const int64_t s0 = A.b_soff[ib], s1 = A.b_soff[ib + 1];
-            int64_t k = s0;
-            for (; k + 1 < s1; k += 2) {
-                const int2 e0 = __ldg(A.b_sci + k), e1 = __ldg(A.b_sci + k + 1);
+            const int2 *ci = A.s1_ci + A.s1_off[sl] + lane;
+            const int w = A.s1_w[sl];
+            int k = 0;
+            for (; k + 1 < w; k += 2) {
+                const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
                 const T x0 = sV2[e0.y], x1 = sV2[e1.y];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
@@ -187,8 +210,8 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
                     acc2[v] += x1 * cval(v, Ja, e1.x);
                 }
             }
-            if (k < s1) {
-                const int2 e = __ldg(A.b_sci + k);
+            if (k < w) {
+                const int2 e = __ldg(ci + 32 * k);
                 const T x = sV2[e.y];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ja, e.x);
@@ -280,6 +303,19 @@ __global__ void k_diagonal(const uint64_t *__restrict__ stra, int64_t la, int64_
 }
 
 template <typename T>
+void set_sell(SigArgs<T> &A, const Plan *P) {
+    A.s1_off = P->d_s1_off.p;
+    A.s2_off = P->d_s2_off.p;
+    A.d2_off = P->d_d2_off.p;
+    A.s1_w = P->d_s1_w.p;
+    A.s2_w = P->d_s2_w.p;
+    A.d2_w = P->d_d2_w.p;
+    A.s1_ci = P->d_s1_ci.p;
+    A.s2_ci = P->d_s2_ci.p;
+    A.d2_col = P->d_d2_col.p;
+}
+
+template <typename T>
 SigArgs<T> make_args(const tbsci_ham *ham, const Plan *P);
 
 template <>
@@ -311,6 +347,12 @@ SigArgs<double> make_args<double>(const tbsci_ham *ham, const Plan *P) {
     A.permb2 = P->d_permb2.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = ham->ecore;
+    A.s2_val = P->d_s2_val.p;
+    A.d2_val = P->d_d2_val.p;
+    A.U1 = P->d_U1.p;
+    A.U2 = P->d_U2.p;
+    A.Eb2 = P->d_Eb2.p;
+    set_sell(A, P);
     return A;
 }
 
@@ -343,12 +385,18 @@ SigArgs<float> make_args<float>(const tbsci_ham *ham, const Plan *P) {
     A.permb2 = P->d_permb2.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = (float)ham->ecore;
+    A.s2_val = P->d_s2_valf.p;
+    A.d2_val = P->d_d2_valf.p;
+    A.U1 = P->d_U1f.p;
+    A.U2 = P->d_U2f.p;
+    A.Eb2 = P->d_Eb2f.p;
+    set_sell(A, P);
     return A;
 }
 
 template <typename T>
 size_t smem_bytes(int npair, int64_t lb, int nv, bool stage, bool accs) {
-    size_t head = (2 * npair * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15);
+    size_t head = ((2 * npair + 2) * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15);
     return head + ((stage ? 1 : 0) + (accs ? 1 : 0)) * (size_t)nv * lb * sizeof(T);
 }
 
