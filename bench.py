@@ -265,7 +265,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default="sel16", choices=sorted(WORKLOADS))
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "tf32tc", "bf16tc"])
     ap.add_argument("--ref-rows", type=int, default=20000)
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -303,13 +303,16 @@ def main():
     counts = sp.counts()
     Cn = random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec)
     tdt = torch.float64 if args.dtype == "f64" else torch.float32
+    sdt = {"f64": tb.TBSCI_F64, "f32": tb.TBSCI_F32, "tf32tc": tb.TBSCI_F32_TC_TF32,
+           "bf16tc": tb.TBSCI_F32_TC_BF16}[args.dtype]
     C = torch.from_numpy(Cn).to(dev).to(tdt)
     S = torch.empty_like(C)
     stream = torch.cuda.current_stream()
-    launches_per_step = (nvec + 3) // 4
+    # fused kernel: one launch per <= 4 vectors; tensor-core modes: SIMT rest + tensor kernel per vector
+    launches_per_step = (nvec + 3) // 4 if sdt in (tb.TBSCI_F64, tb.TBSCI_F32) else 2 * nvec
 
     for _ in range(args.warmup):
-        sp.sigma(C, S, stream=stream)
+        sp.sigma(C, S, stream=stream, dtype=sdt)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -320,7 +323,7 @@ def main():
     torch.cuda.synchronize()
     ev[0].record(stream)
     for k in range(args.steps):
-        sp.sigma(C, S, stream=stream)
+        sp.sigma(C, S, stream=stream, dtype=sdt)
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()

@@ -45,9 +45,19 @@ typedef enum tbsci_status {
     TBSCI_EBUSY = 7     /* object in use */
 } tbsci_status;
 
-/* Arithmetic of a sigma evaluation. F64 and F32 name the type of c and sigma
- * and of all arithmetic. */
-typedef enum tbsci_dtype { TBSCI_F64 = 0, TBSCI_F32 = 1 } tbsci_dtype;
+/* Arithmetic of a sigma evaluation. F64 and F32: c, sigma and all arithmetic
+ * in that type (SIMT). F32_TC_TF32 / F32_TC_BF16: c and sigma FP32; the
+ * alpha-beta classes, alpha singles and the diagonal run on the tensor cores
+ * with FP32 accumulation, their products from split TF32 (3 products per term,
+ * FP32-level accuracy) or from single BF16 values (about 3 significant digits);
+ * the other classes on the FP32 SIMT path. Tensor-core modes need norb <= 16
+ * and otherwise fall back to F32. */
+typedef enum tbsci_dtype {
+    TBSCI_F64 = 0,
+    TBSCI_F32 = 1,
+    TBSCI_F32_TC_TF32 = 2,
+    TBSCI_F32_TC_BF16 = 3
+} tbsci_dtype;
 
 /* Same object as cudaStream_t; NULL = the legacy default stream. */
 typedef struct CUstream_st *tbsci_stream;
@@ -188,7 +198,8 @@ typedef struct tbsci_davidson_opts {
     int max_iter;        /* 0 -> 1000 */
     double tol_energy;   /* |theta - theta_prev| per root; 0 -> 1e-9 */
     double tol_residual; /* ||r||_2 per root; 0 -> 1e-5 */
-    int mixed;           /* 0: FP64 sigma throughout. 1: FP32 sigma until every
+    int mixed;           /* 0: FP64 sigma throughout. 1 (F32), 2 (F32_TC_TF32) or
+                            3 (F32_TC_BF16): that low-precision sigma until every
                             residual is below tol_mixed_residual (or stops falling
                             for 8 iterations), then restart from the roots' Ritz
                             vectors with FP64 sigma and converge to the FP64

@@ -69,15 +69,19 @@ class Space:
     def strings(self):
         return B.tbsci_strings_export(self.ctx.handle, self.sa), B.tbsci_strings_export(self.ctx.handle, self.sb)
 
-    def sigma(self, c, out=None, stream=None):
-        """sigma = H c for a device tensor ``c`` [nvec, la, lb] (float64 or float32)."""
+    def sigma(self, c, out=None, stream=None, dtype=None):
+        """sigma = H c for a device tensor ``c`` [nvec, la, lb]: float64 -> TBSCI_F64,
+        float32 -> TBSCI_F32 unless ``dtype`` names a tensor-core mode
+        (TBSCI_F32_TC_TF32 / TBSCI_F32_TC_BF16, float32 tensors)."""
         import torch
         nvec = c.shape[0] if c.dim() == 3 else 1
         assert c.is_cuda and c.is_contiguous() and c.numel() == nvec * self.ndet
         if out is None:
             out = torch.empty_like(c)
-        dt = B.TBSCI_F64 if c.dtype == torch.float64 else B.TBSCI_F32
-        B.tbsci_sigma(self.ctx.handle, self.ham, self.ta, self.tb, c, out, nvec, dt, stream)
+        if dtype is None:
+            dtype = B.TBSCI_F64 if c.dtype == torch.float64 else B.TBSCI_F32
+        assert (c.dtype == torch.float64) == (dtype == B.TBSCI_F64)
+        B.tbsci_sigma(self.ctx.handle, self.ham, self.ta, self.tb, c, out, nvec, dtype, stream)
         return out
 
     def sigma_host(self, c: np.ndarray) -> np.ndarray:

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtbsci.so")
 
 TBSCI_OK, TBSCI_EINVAL, TBSCI_ENOMEM, TBSCI_ECUDA, TBSCI_ENOCONV, TBSCI_EAGAIN, TBSCI_ETIMEOUT, TBSCI_EBUSY = range(8)
-TBSCI_F64, TBSCI_F32 = 0, 1
+TBSCI_F64, TBSCI_F32, TBSCI_F32_TC_TF32, TBSCI_F32_TC_BF16 = 0, 1, 2, 3
 TBSCI_TABLES_SINGLES_ONLY, TBSCI_TABLES_COUNT_ONLY = 1, 2
 
 # exported names declared in include/tbsci.h
@@ -303,7 +303,7 @@ def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max
                    restart_keep=0):
     """Lowest ``nroots`` energies (numpy) and the info dict; ``vecs`` (device FP64
     tensor [nroots][la][lb]) receives the eigenvectors when given."""
-    o = DavidsonOpts(max_subspace, restart_keep, max_iter, tol_energy, tol_residual, 1 if mixed else 0,
+    o = DavidsonOpts(max_subspace, restart_keep, max_iter, tol_energy, tol_residual, int(mixed),
                      tol_mixed_residual,
                      None if stream is None else _stream(stream).value)
     e = np.zeros(nroots)

@@ -344,6 +344,7 @@ struct DavEngine {
     enum class St { NeedSigma, WaitG, WaitR, WaitGS, Done } state = St::NeedSigma;
     int m = 0, sig_lo = 0, sig_hi = 0, g_lo = 0;
     bool f32 = false, sig_prepared = false;
+    tbsci_dtype lowp = TBSCI_F32;  // sigma type of the low-precision phase
     std::vector<double> G, theta, theta_prev, rnorm, e32, Yv;
     std::vector<int> todo;
     int it = 0, it32 = 0, stall32 = 0, nsig = 0, nsig32 = 0;
@@ -429,6 +430,8 @@ struct DavEngine {
         TB_CUDA(ctx, T.alloc((size_t)nroots * N));
         TB_CUDA(ctx, diag.alloc(N));
         f32 = opt.mixed != 0;
+        TB_CHECK(ctx, opt.mixed >= 0 && opt.mixed <= 3, TBSCI_EINVAL, "mixed must be 0..3");
+        lowp = opt.mixed == 2 ? TBSCI_F32_TC_TF32 : opt.mixed == 3 ? TBSCI_F32_TC_BF16 : TBSCI_F32;
         if (f32) {
             TB_CUDA(ctx, v32.alloc((size_t)nroots * N));
             TB_CUDA(ctx, w32.alloc((size_t)nroots * N));
@@ -492,7 +495,7 @@ struct DavEngine {
             }
             *c = v32.p;
             *s = w32.p;
-            *dt = TBSCI_F32;
+            *dt = lowp;
         } else {
             *c = V.p + (size_t)sig_lo * N;
             *s = W.p + (size_t)sig_lo * N;

@@ -143,6 +143,12 @@ struct Plan {
     DevBuf<double> d_U1, d_U2, d_Eb2;    // Coulomb table / beta energies with columns in permb / permb2 order
     DevBuf<float> d_U1f, d_U2f, d_Eb2f;
     DevBuf<int32_t> d_rowsa; // alpha rows ordered by work (descending)
+    // Tensor-core alpha-beta path (norb <= 16): beta single links indexed by
+    // (source string Jb, off-diagonal orbital pair r > s): (Ib << 1 | sign<0) or -1,
+    // and the map from off-diagonal pair index to the full pair index.
+    int npoff = 0;
+    DevBuf<int32_t> d_lbp, d_offpair;
+    DevBuf<int> d_tc_err;
     tbsci_sigma_counts counts{};
 };
 
@@ -197,6 +203,14 @@ struct BatchScratch {
 // staged variant get launches of their own.
 tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs, tbsci_dtype dt, cudaStream_t st,
                                 BatchScratch *scr);
+// FP32 sigma without the diagonal, alpha singles and alpha-beta classes (the
+// part the tensor-core kernel does not cover); overwrites s.
+tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
+                               int nvec, cudaStream_t st);
+// sigma_tc.cu: the diagonal, alpha singles and all alpha-beta classes on the
+// tensor cores (3xTF32 or BF16 products, FP32 accumulation), added into s.
+tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s, int nvec,
+                          bool bf16, cudaStream_t st);
 tbsci_status diagonal_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, double *diag,
                              cudaStream_t st);
 

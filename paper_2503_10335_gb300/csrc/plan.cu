@@ -153,6 +153,19 @@ __global__ void k_permute_cols(const double *__restrict__ in, int64_t rows, int6
     outf[r * lb + j] = (float)v;
 }
 
+// LBP[Jb][off(p,q)] = (Ib << 1) | (sign < 0) for each single link Ib = a+_p a_q Jb
+__global__ void k_link_by_pair(int64_t lb, const int64_t *__restrict__ off, const tbsci_single_link *__restrict__ ent,
+                               int npoff, int32_t *lbp) {
+    const int64_t jb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (jb >= lb) return;
+    for (int64_t k = off[jb]; k < off[jb + 1]; ++k) {
+        const tbsci_single_link e = ent[k];
+        const int hi = e.p > e.q ? e.p : e.q, lo = e.p > e.q ? e.q : e.p;
+        const int x = hi * (hi - 1) / 2 + lo;
+        lbp[jb * npoff + x] = (e.target << 1) | (e.sign < 0 ? 1 : 0);
+    }
+}
+
 // per-slice widths and offsets of a sliced-ELL layout over `perm`
 void sell_shape(const std::vector<int32_t> &perm, const std::vector<int64_t> &off, std::vector<int64_t> &soff,
                 std::vector<int32_t> &sw, int64_t &total) {
@@ -336,6 +349,25 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
             dim3 ge((unsigned)((lb + 127) / 128), 1);
             k_permute_cols<<<ge, 128, 0, st>>>(plan->B.d_E.p, 1, lb, plan->d_permb2.p, plan->d_Eb2.p, plan->d_Eb2f.p);
             TB_CUDA(ctx, cudaGetLastError());
+        }
+    }
+    // tensor-core alpha-beta tables (only when the off-diagonal pairs fit one 128-row tile)
+    {
+        const int n = ham->norb;
+        plan->npoff = n * (n - 1) / 2;
+        if (plan->npoff <= 128 && lb > 0) {
+            TB_CUDA(ctx, plan->d_lbp.alloc((size_t)lb * plan->npoff));
+            TB_CUDA(ctx, cudaMemsetAsync(plan->d_lbp.p, 0xFF, plan->d_lbp.bytes(), st));
+            k_link_by_pair<<<(unsigned)((lb + 127) / 128), 128, 0, st>>>(lb, b->d_off1.p, b->d_ent1.p, plan->npoff,
+                                                                          plan->d_lbp.p);
+            TB_CUDA(ctx, cudaGetLastError());
+            std::vector<int32_t> op(plan->npoff);
+            for (int r = 1; r < n; ++r)
+                for (int q = 0; q < r; ++q) op[r * (r - 1) / 2 + q] = r * (r + 1) / 2 + q;
+            TB_CUDA(ctx, plan->d_offpair.alloc(plan->npoff));
+            TB_CUDA(ctx, cudaMemcpy(plan->d_offpair.p, op.data(), op.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            TB_CUDA(ctx, plan->d_tc_err.alloc(1));
+            TB_CUDA(ctx, cudaMemsetAsync(plan->d_tc_err.p, 0, sizeof(int), st));
         }
     }
     // work counts: non-zeros of H by class (Sec. II.C, Table I)

@@ -63,8 +63,10 @@ struct SigArgs {
     const T *U1, *U2, *Eb2;
 };
 
-// One alpha row Ia of sigma (the whole body of a CTA).
-template <typename T, int NV, bool STAGE, bool ACCS, int kThreads>
+// One alpha row Ia of sigma (the whole body of a CTA). REST: only the classes
+// the tensor-core kernel leaves out (same-spin beta singles and doubles, alpha
+// doubles); the diagonal, alpha singles and every alpha-beta term are skipped.
+template <typename T, int NV, bool STAGE, bool ACCS, int kThreads, bool REST = false>
 __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia, unsigned char *smem_raw) {
     const int npair = A.npair;
     const int64_t lb = A.lb, vs = A.vstride;
@@ -102,7 +104,8 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
     // W_Ia[x] = sum_{p in Ia} (pp|x), stored with both signs
     for (int x = threadIdx.x; x < npair; x += kThreads) {
         T w = 0;
-        for (int k = 0; k < na; ++k) w += A.V[(size_t)sOcc[k] * npair + x];
+        if (!REST)
+            for (int k = 0; k < na; ++k) w += A.V[(size_t)sOcc[k] * npair + x];
         sV2[2 * x] = w;
         sV2[2 * x + 1] = -w;
     }
@@ -115,12 +118,15 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
         const int64_t ib = A.permb2[j];
         const int64_t sl = j >> 5;
         const int lane = (int)(j & 31);
-        T ed = eIa + __ldg(A.Eb2 + j);
-        for (int k = 0; k < na; ++k) ed += __ldg(A.U2 + (size_t)sOcc[k] * lb + j);
+        T ed = T(0);
+        if (!REST) {
+            ed = eIa + __ldg(A.Eb2 + j);
+            for (int k = 0; k < na; ++k) ed += __ldg(A.U2 + (size_t)sOcc[k] * lb + j);
+        }
         T acc[NV], acc2[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            acc[v] = ed * cval(v, Ia, ib);
+            acc[v] = REST ? T(0) : ed * cval(v, Ia, ib);
             acc2[v] = T(0);
         }
         {
@@ -171,7 +177,7 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
     }
 
     // ---- Ja = alpha singles of Ia: columns in permb order
-    const int64_t t0 = A.a_soff[Ia], t1 = A.a_soff[Ia + 1];
+    const int64_t t0 = A.a_soff[Ia], t1 = REST ? t0 : A.a_soff[Ia + 1];
     for (int64_t t = t0; t < t1; ++t) {
         const int2 ea = __ldg(A.a_sci + t);
         const int64_t Ja = ea.x;
@@ -258,10 +264,10 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
     }
 }
 
-template <typename T, int NV, bool STAGE, bool ACCS, int kThreads>
+template <typename T, int NV, bool STAGE, bool ACCS, int kThreads, bool REST = false>
 __global__ void __launch_bounds__(kThreads) k_sigma(SigArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sigma_row<T, NV, STAGE, ACCS, kThreads>(A, A.rowsa[blockIdx.x], smem_raw);
+    sigma_row<T, NV, STAGE, ACCS, kThreads, REST>(A, A.rowsa[blockIdx.x], smem_raw);
 }
 
 // One launch over the alpha rows of several jobs (a job = one vector of one
@@ -526,7 +532,43 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
                                 BatchScratch *scr) {
     if (dt == TBSCI_F64) return launch_batch_typed<double>(ctx, jobs, njobs, st, scr);
     if (dt == TBSCI_F32) return launch_batch_typed<float>(ctx, jobs, njobs, st, scr);
-    return fail(ctx, TBSCI_EINVAL, "unknown dtype");
+    for (int j = 0; j < njobs; ++j)
+        TB_TRY(sigma_launch(ctx, jobs[j].ham, jobs[j].plan, jobs[j].c, jobs[j].s, jobs[j].nvec, dt, st));
+    return TBSCI_OK;
+}
+
+tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
+                               int nvec, cudaStream_t st) {
+    SigArgs<float> A = make_args<float>(ham, plan);
+    if (A.la == 0 || A.lb == 0) return TBSCI_OK;
+    const size_t sm_stage = smem_bytes<float>(A.npair, A.lb, 1, true, true);
+    const size_t sm_acc = smem_bytes<float>(A.npair, A.lb, 1, false, true);
+    const size_t sm_none = smem_bytes<float>(A.npair, A.lb, 1, false, false);
+    for (int v = 0; v < nvec; ++v) {
+        A.C = c + (size_t)v * A.vstride;
+        A.S = s + (size_t)v * A.vstride;
+        if (sm_stage <= ctx->smem_optin) {
+            if (A.lb >= 1024) {
+                auto k = k_sigma<float, 1, true, true, 512, true>;
+                TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
+                k<<<(unsigned)A.la, 512, sm_stage, st>>>(A);
+            } else {
+                auto k = k_sigma<float, 1, true, true, 128, true>;
+                TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
+                k<<<(unsigned)A.la, 128, sm_stage, st>>>(A);
+            }
+        } else if (sm_acc <= ctx->smem_optin) {
+            auto k = k_sigma<float, 1, false, true, 512, true>;
+            TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_acc));
+            k<<<(unsigned)A.la, 512, sm_acc, st>>>(A);
+        } else {
+            auto k = k_sigma<float, 1, false, false, 512, true>;
+            TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_none));
+            k<<<(unsigned)A.la, 512, sm_none, st>>>(A);
+        }
+        TB_CUDA(ctx, cudaGetLastError());
+    }
+    return TBSCI_OK;
 }
 
 tbsci_status sigma_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const void *c, void *s, int nvec,
@@ -535,6 +577,14 @@ tbsci_status sigma_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan
         return launch_typed<double>(ctx, ham, plan, static_cast<const double *>(c), static_cast<double *>(s), nvec, st);
     if (dt == TBSCI_F32)
         return launch_typed<float>(ctx, ham, plan, static_cast<const float *>(c), static_cast<float *>(s), nvec, st);
+    if (dt == TBSCI_F32_TC_TF32 || dt == TBSCI_F32_TC_BF16) {
+        const float *cf = static_cast<const float *>(c);
+        float *sf = static_cast<float *>(s);
+        if (plan->npoff > 128 || !plan->d_lbp.p)  // no tensor-core tile for this norb: FP32 on the SIMT path
+            return launch_typed<float>(ctx, ham, plan, cf, sf, nvec, st);
+        TB_TRY(sigma_launch_rest(ctx, ham, plan, cf, sf, nvec, st));
+        return sigma_tc_add(ctx, ham, plan, cf, sf, nvec, dt == TBSCI_F32_TC_BF16, st);
+    }
     return fail(ctx, TBSCI_EINVAL, "unknown dtype");
 }
 

@@ -1,0 +1,86 @@
+"""Tensor-core sigma modes (tcgen05, row a6): the alpha-beta classes, alpha
+singles and diagonal from split-TF32 (3 products per term) or BF16 products
+with FP32 accumulation, the other classes on the FP32 SIMT path. Compared with
+the oracle applied to the FP32-rounded vector: split TF32 within FP32-level
+accumulation error, BF16 within its 8-bit-mantissa error."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_sigma_close
+from tbsci_inputs import WORKLOADS, random_vectors, selected_strings, synth_hamiltonian
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TOL = {"tf32": (2e-5, 1e-5), "bf16": (2e-2, 1e-2)}
+
+
+@pytest.fixture(scope="module")
+def tb():
+    import paper_2503_10335_gb300 as tb
+    return tb
+
+
+@pytest.fixture(scope="module")
+def ctx(tb):
+    c = tb.Context(0)
+    yield c
+    c.close()
+
+
+CASES = [
+    (8, 4, 4, None, None, 1),
+    (10, 5, 5, 120, 257, 2),   # ragged: 257 beta columns, a partial last 64-column tile
+    (12, 6, 6, 300, 300, 1),
+    (12, 4, 6, None, 200, 1),
+    (16, 8, 8, 700, 650, 1),   # the largest norb of the tensor-core tile (120 pairs)
+    (18, 9, 9, 300, 300, 1),   # 153 pairs: falls back to the FP32 SIMT path
+]
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("n,na,nb,acnt,bcnt,nvec", CASES)
+def test_tc_sigma_parity(tb, ctx, mode, n, na, nb, acnt, bcnt, nvec):
+    import torch
+    h, eri, _ = synth_hamiltonian(n, seed=300 + n)
+    asel = None if acnt is None else selected_strings(n, na, acnt, 31 + n)
+    bsel = None if bcnt is None else selected_strings(n, nb, bcnt, 37 + n)
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.2, alpha=asel, beta=bsel)
+    osp = oracle.make_space(n, na, nb, asel, bsel)
+    C = random_vectors(nvec, sp.la, sp.lb, seed=n).astype(np.float32)
+    dt = tb.TBSCI_F32_TC_TF32 if mode == "tf32" else tb.TBSCI_F32_TC_BF16
+    s = sp.sigma(torch.from_numpy(C).cuda(), dtype=dt).double().cpu().numpy().reshape(nvec, -1)
+    ref, bound = oracle.sigma(osp, h, eri, 0.2, C.astype(np.float64), with_bound=True)
+    rel, norm_rel = TOL[mode] if n <= 16 else (64 * 2.0 ** -24, 1e-5)
+    assert_sigma_close(s, ref, bound, rel=rel, norm_rel=norm_rel)
+    sp.close()
+
+
+def test_tc_sigma_sel16_sampled(tb, ctx):
+    """norb=16, 3,000 x 3,000 (9.0M determinants), split TF32, 3 vectors."""
+    import torch
+    wl = WORKLOADS["sel16"]
+    h, eri, ecore = wl.hamiltonian()
+    asel, bsel = wl.alpha_selection(), wl.beta_selection()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=asel, beta=bsel)
+    osp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, asel, bsel)
+    C = random_vectors(3, sp.la, sp.lb, seed=wl.seed_vec).astype(np.float32)
+    s = sp.sigma(torch.from_numpy(C).cuda(), dtype=tb.TBSCI_F32_TC_TF32).double().cpu().numpy().reshape(3, -1)
+    rows = np.random.default_rng(5).choice(sp.ndet, 2000, replace=False)
+    ref, bound = oracle.sigma(osp, h, eri, ecore, C.astype(np.float64).reshape(3, -1), rows=rows, with_bound=True)
+    assert_sigma_close(s[:, rows], ref, bound, rel=2e-5, norm_rel=1e-5)
+    sp.close()
+
+
+@pytest.mark.parametrize("mixed", [2, 3])
+def test_tc_mixed_davidson_golden(tb, ctx, mixed):
+    wl = WORKLOADS["fci8"]
+    h, eri, ecore = wl.hamiltonian()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore)
+    ref = np.loadtxt(os.path.join(GOLDEN, "fci8_energies.txt"))
+    e, info = sp.davidson(3, mixed=mixed)
+    assert info["converged"] and info["nsigma_f32"] > 0
+    assert np.max(np.abs(e - ref[:3])) < 1e-8
+    sp.close()
