@@ -114,6 +114,21 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def max_over_ranks(value: float, dist_mod=None, device="cpu") -> float:
+    """The slowest rank's time (replicas run independently; the job ends with the last)."""
+    if dist_mod is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world_size: int, units_per_rank: float, max_seconds: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's units over the max time."""
+    return world_size * units_per_rank / max_seconds
+
+
 def cpu_baseline(wl, nvec, budget_s=15.0, impl_rows=None):
     """Oracle sigma over a bounded, seeded row sample of the workload."""
     import oracle
@@ -271,6 +286,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--serving", action="store_true", help="serving stream instead of the sigma bench")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--nreq", type=int, default=48)
     ap.add_argument("--max-count", type=int, default=3000)
     args = ap.parse_args()
@@ -311,6 +327,10 @@ def main():
     # fused kernel: one launch per <= 4 vectors; tensor-core modes: SIMT rest + tensor kernel per vector
     launches_per_step = (nvec + 3) // 4 if sdt in (tb.TBSCI_F64, tb.TBSCI_F32) else 2 * nvec
 
+    tuned_ms = None
+    if sdt in (tb.TBSCI_F64, tb.TBSCI_F32) and not args.no_autotune:
+        # set-up, untimed: pick the launch shape of the SIMT kernel for this space
+        tuned_ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, nvec, sdt, stream)
     for _ in range(args.warmup):
         sp.sigma(C, S, stream=stream, dtype=sdt)
     torch.cuda.synchronize()
@@ -331,11 +351,9 @@ def main():
     total_ms = ev[0].elapsed_time(ev[-1])
     if dist:
         dist.barrier()
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
     ms_step = total_ms / args.steps
-    value = ws * nvec * sp.ndet / (ms_step * 1e-3) / 1e9
+    value = replica_throughput(ws, nvec * sp.ndet, ms_step * 1e-3) / 1e9
 
     # roofline of the fused sigma kernel (one launch per step for nvec <= 4)
     flops_step = 2.0 * counts["nnz"] * nvec
@@ -391,7 +409,7 @@ def main():
             "config": dict(_config(wl, nvec, args.dtype), parallelism="replicas" if ws > 1 else "single"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks, "davidson": dav,
-            "counts": counts, "setup_seconds": t_setup,
+            "counts": counts, "setup_seconds": t_setup, "autotune_ms": tuned_ms,
             "step_ms_min": min(per_step), "step_ms_max": max(per_step),
         }
         print(json.dumps(line), flush=True)

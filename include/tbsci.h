@@ -167,6 +167,16 @@ tbsci_status tbsci_prepare(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a
 tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
                          const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream);
 
+/* Autotuner of the SIMT sigma kernel (F64 or F32): times every launch shape
+ * (4, 8 or 16 warps per CTA x 1..4 vectors per CTA) on the caller's c and
+ * sigma, keeps the fastest for this space and type (later tbsci_sigma calls use
+ * it) and leaves sigma = H c computed. Each column is summed in the same order
+ * in every shape, so tuning never changes results. *best_ms: the chosen shape's
+ * time (may be NULL). Synchronises `stream`. Errors as tbsci_sigma. */
+tbsci_status tbsci_sigma_autotune(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                                  const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream,
+                                  double *best_ms);
+
 /* Same product with HOST vectors: copies c in, evaluates in FP64, copies sigma
  * out and returns when done (uses a device buffer owned by the context). */
 tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,

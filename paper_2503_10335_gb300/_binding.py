@@ -28,7 +28,7 @@ EXPORTS = [
     "tbsci_hamiltonian_create", "tbsci_hamiltonian_destroy", "tbsci_prepare", "tbsci_sigma",
     "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson", "tbsci_overlap",
     "tbsci_overlap_noalloc", "tbsci_server_create", "tbsci_submit", "tbsci_poll", "tbsci_server_load",
-    "tbsci_server_destroy",
+    "tbsci_server_destroy", "tbsci_sigma_autotune",
 ]
 
 
@@ -150,6 +150,7 @@ def load(path: str | None = None):
         "tbsci_poll": ([P, ctypes.c_uint64, I, ctypes.POINTER(Result)], I),
         "tbsci_server_load": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "tbsci_server_destroy": ([P], None),
+        "tbsci_sigma_autotune": ([P, P, P, P, P, P, I, I, P, ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -279,6 +280,14 @@ def tbsci_prepare(ctx, ham, ta, tb):
 def tbsci_sigma(ctx, ham, ta, tb, c, sigma, nvec: int, dtype: int = TBSCI_F64, stream=None):
     """sigma <- H c on device tensors [nvec][la][lb] (F64 or F32)."""
     _check(ctx, load().tbsci_sigma(ctx, ham, ta, tb, _ptr(c), _ptr(sigma), int(nvec), int(dtype), _stream(stream)))
+
+
+def tbsci_sigma_autotune(ctx, ham, ta, tb, c, sigma, nvec: int, dtype: int = TBSCI_F64, stream=None) -> float:
+    """Tunes the sigma launch shape on (c, sigma); returns the chosen shape's time in ms."""
+    ms = ctypes.c_double()
+    _check(ctx, load().tbsci_sigma_autotune(ctx, ham, ta, tb, _ptr(c), _ptr(sigma), int(nvec), int(dtype),
+                                            _stream(stream), ctypes.byref(ms)))
+    return ms.value
 
 
 def tbsci_sigma_host(ctx, ham, ta, tb, c: np.ndarray, sigma: np.ndarray, nvec: int):

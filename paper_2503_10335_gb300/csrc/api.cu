@@ -249,6 +249,18 @@ tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, 
     return sigma_launch(ctx, ham, p, c, sigma, nvec, dtype, (cudaStream_t)stream);
 }
 
+tbsci_status tbsci_sigma_autotune(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                                  const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream,
+                                  double *best_ms) {
+    TB_GUARD_CTX(ctx);
+    if (nvec < 1) return fail(ctx, TBSCI_EINVAL, "nvec must be >= 1");
+    Plan *p = nullptr;
+    TB_TRY(plan_get(ctx, ham, a, b, &p));
+    if (p->A.l * p->B.l == 0) return TBSCI_OK;
+    if (!c || !sigma || c == sigma) return fail(ctx, TBSCI_EINVAL, "bad vector pointers");
+    return sigma_autotune(ctx, ham, p, c, sigma, nvec, dtype, (cudaStream_t)stream, best_ms);
+}
+
 tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
                               const double *c, double *sigma, int nvec) {
     TB_GUARD_CTX(ctx);

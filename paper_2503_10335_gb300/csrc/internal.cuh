@@ -149,6 +149,8 @@ struct Plan {
     int npoff = 0;
     DevBuf<int32_t> d_lbp, d_offpair;
     DevBuf<int> d_tc_err;
+    // autotuned launch shape per sigma type (index = tbsci_dtype F64 / F32): threads per CTA, vectors per CTA
+    int tune_threads[2] = {0, 0}, tune_nv[2] = {0, 0};
     tbsci_sigma_counts counts{};
 };
 
@@ -205,6 +207,9 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
                                 BatchScratch *scr);
 // FP32 sigma without the diagonal, alpha singles and alpha-beta classes (the
 // part the tensor-core kernel does not cover); overwrites s.
+// Times every launch shape of the SIMT kernel on (c, s) and keeps the fastest in the plan.
+tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const void *c, void *s, int nvec,
+                            tbsci_dtype dt, cudaStream_t st, double *best_ms);
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
                                int nvec, cudaStream_t st);
 // sigma_tc.cu: the diagonal, alpha singles and all alpha-beta classes on the

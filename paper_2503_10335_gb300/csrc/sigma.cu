@@ -406,52 +406,59 @@ size_t smem_bytes(int npair, int64_t lb, int nv, bool stage, bool accs) {
     return head + ((stage ? 1 : 0) + (accs ? 1 : 0)) * (size_t)nv * lb * sizeof(T);
 }
 
-template <typename T, int NV, bool STAGE, bool ACCS>
-tbsci_status launch_one(tbsci_ctx *ctx, SigArgs<T> A, size_t smem, cudaStream_t st) {
-    // wide CTAs (16 warps) keep the FP64 pipe fed on long rows; short rows take 4 warps
-    if (A.lb >= 1024) {
-        auto kern = k_sigma<T, NV, STAGE, ACCS, 512>;
-        TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)A.la, 512, smem, st>>>(A);
-    } else {
-        auto kern = k_sigma<T, NV, STAGE, ACCS, 128>;
-        TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<(unsigned)A.la, 128, smem, st>>>(A);
-    }
+template <typename T, int NV, bool STAGE, bool ACCS, int TH>
+tbsci_status launch_th(tbsci_ctx *ctx, SigArgs<T> A, size_t smem, cudaStream_t st) {
+    auto kern = k_sigma<T, NV, STAGE, ACCS, TH>;
+    TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)A.la, TH, smem, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
 }
 
+// threads per CTA: 0 = by row length (16 warps on long rows, 4 on short ones)
+template <typename T, int NV, bool STAGE, bool ACCS>
+tbsci_status launch_one(tbsci_ctx *ctx, SigArgs<T> A, size_t smem, cudaStream_t st, int threads) {
+    if (threads == 0) threads = A.lb >= 1024 ? 512 : 128;
+    if (threads == 512) return launch_th<T, NV, STAGE, ACCS, 512>(ctx, A, smem, st);
+    if (threads == 256) return launch_th<T, NV, STAGE, ACCS, 256>(ctx, A, smem, st);
+    return launch_th<T, NV, STAGE, ACCS, 128>(ctx, A, smem, st);
+}
+
 template <typename T, int NV>
-tbsci_status launch_nv(tbsci_ctx *ctx, SigArgs<T> A, cudaStream_t st) {
+tbsci_status launch_nv(tbsci_ctx *ctx, SigArgs<T> A, cudaStream_t st, int threads) {
     const size_t limit = ctx->smem_optin;
     size_t sm;
     if ((sm = smem_bytes<T>(A.npair, A.lb, NV, true, true)) <= limit)
-        return launch_one<T, NV, true, true>(ctx, A, sm, st);
+        return launch_one<T, NV, true, true>(ctx, A, sm, st, threads);
     if ((sm = smem_bytes<T>(A.npair, A.lb, NV, false, true)) <= limit)
-        return launch_one<T, NV, false, true>(ctx, A, sm, st);
+        return launch_one<T, NV, false, true>(ctx, A, sm, st, threads);
     sm = smem_bytes<T>(A.npair, A.lb, NV, false, false);
-    return launch_one<T, NV, false, false>(ctx, A, sm, st);
+    return launch_one<T, NV, false, false>(ctx, A, sm, st, threads);
 }
 
+// nv_max / threads: 0 = defaults (as many vectors per CTA as fit with staging, up to 4)
 template <typename T>
 tbsci_status launch_typed(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, const T *c, T *s, int nvec,
-                          cudaStream_t st) {
+                          cudaStream_t st, int nv_max = 0, int threads = 0) {
     SigArgs<T> A = make_args<T>(ham, P);
     if (A.la == 0 || A.lb == 0) return TBSCI_OK;
-    // vectors per CTA: as many as fit (up to 4) with staging and a shared accumulator
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (nv_max == 0 && P->tune_nv[ti] > 0) {
+        nv_max = P->tune_nv[ti];
+        threads = P->tune_threads[ti];
+    }
     int v = 0;
     while (v < nvec) {
         int rem = nvec - v;
-        int nv = std::min(rem, 4);
+        int nv = std::min(rem, nv_max > 0 ? nv_max : 4);
         while (nv > 1 && smem_bytes<T>(A.npair, A.lb, nv, true, true) > ctx->smem_optin) --nv;
         A.C = c + (size_t)v * A.vstride;
         A.S = s + (size_t)v * A.vstride;
         switch (nv) {
-            case 4: TB_TRY((launch_nv<T, 4>(ctx, A, st))); break;
-            case 3: TB_TRY((launch_nv<T, 3>(ctx, A, st))); break;
-            case 2: TB_TRY((launch_nv<T, 2>(ctx, A, st))); break;
-            default: TB_TRY((launch_nv<T, 1>(ctx, A, st))); break;
+            case 4: TB_TRY((launch_nv<T, 4>(ctx, A, st, threads))); break;
+            case 3: TB_TRY((launch_nv<T, 3>(ctx, A, st, threads))); break;
+            case 2: TB_TRY((launch_nv<T, 2>(ctx, A, st, threads))); break;
+            default: TB_TRY((launch_nv<T, 1>(ctx, A, st, threads))); break;
         }
         v += nv;
     }
@@ -535,6 +542,51 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
     for (int j = 0; j < njobs; ++j)
         TB_TRY(sigma_launch(ctx, jobs[j].ham, jobs[j].plan, jobs[j].c, jobs[j].s, jobs[j].nvec, dt, st));
     return TBSCI_OK;
+}
+
+tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const void *c, void *s, int nvec,
+                            tbsci_dtype dt, cudaStream_t st, double *best_ms) {
+    TB_CHECK(ctx, dt == TBSCI_F64 || dt == TBSCI_F32, TBSCI_EINVAL, "autotune: F64 or F32 only");
+    const int ti = dt == TBSCI_F64 ? 0 : 1;
+    cudaEvent_t e0, e1;
+    TB_CUDA(ctx, cudaEventCreate(&e0));
+    TB_CUDA(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bt = 0, bn = 0;
+    const int threads[3] = {128, 256, 512};
+    tbsci_status st_ret = TBSCI_OK;
+    for (int nv = 1; nv <= std::min(nvec, 4) && st_ret == TBSCI_OK; ++nv) {
+        for (int ti2 = 0; ti2 < 3 && st_ret == TBSCI_OK; ++ti2) {
+            float tot = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                st_ret = dt == TBSCI_F64
+                             ? launch_typed<double>(ctx, ham, plan, static_cast<const double *>(c),
+                                                    static_cast<double *>(s), nvec, st, nv, threads[ti2])
+                             : launch_typed<float>(ctx, ham, plan, static_cast<const float *>(c),
+                                                   static_cast<float *>(s), nvec, st, nv, threads[ti2]);
+                if (st_ret != TBSCI_OK) break;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;  // the first run warms the caches
+            }
+            if (st_ret == TBSCI_OK && tot / 2 < best) {
+                best = tot / 2;
+                bt = threads[ti2];
+                bn = nv;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TB_TRY(st_ret);
+    plan->tune_threads[ti] = bt;
+    plan->tune_nv[ti] = bn;
+    if (best_ms) *best_ms = best;
+    // leave sigma computed with the chosen shape
+    return sigma_launch(ctx, ham, plan, c, s, nvec, dt, st);
 }
 
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,

@@ -219,3 +219,19 @@ def test_large_configs_sigma_sampled_rows(tb, ctx, name, dtype):
     del C
     sp.close()
     torch.cuda.empty_cache()
+
+
+def test_autotune_keeps_results_bitwise(tb, ctx):
+    """The autotuner picks a launch shape by timing; every shape sums each column
+    in the same order, so sigma is bit-identical before and after tuning."""
+    import torch
+    sp, osp, h, eri = _case(tb, ctx, 12, 6, 6, 400, 380, seed=17)
+    for dt, tdt in ((tb.TBSCI_F64, torch.float64), (tb.TBSCI_F32, torch.float32)):
+        C = torch.from_numpy(random_vectors(3, sp.la, sp.lb, seed=18)).to(tdt).cuda()
+        before = sp.sigma(C).cpu().numpy()
+        out = torch.empty_like(C)
+        ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, out, 3, dt)
+        assert ms > 0
+        assert np.array_equal(out.cpu().numpy(), before)
+        assert np.array_equal(sp.sigma(C).cpu().numpy(), before)
+    sp.close()
