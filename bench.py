@@ -273,6 +273,41 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def run_precision_study(args):
+    """Davidson on one workload with every low-precision sigma type: the energy
+    reached by the low-precision phase, its error against the final FP64-refined
+    energy, sigma counts and wall time per mode."""
+    import torch
+    import paper_2503_10335_gb300 as tb
+    wl = WORKLOADS[args.workload]
+    h, eri, ecore = wl.hamiltonian()
+    ctx = tb.Context(0)
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=wl.alpha_selection(),
+                  beta=wl.beta_selection())
+    out = {"metric": METRIC, "mode": "precision_study", "workload": wl.notes, "ndet": sp.ndet,
+           "nroots": wl.nroots, "runs": []}
+    names = {0: "f64", 1: "f32", 2: "f32+tf32x3 tensor", 3: "f32+bf16 tensor"}
+    modes = [int(x) for x in args.modes.split(",")]
+    for m in modes:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, info = sp.davidson(wl.nroots, mixed=m, max_iter=args.max_iter, check=False)
+        dt = time.perf_counter() - t0
+        e_low = info["energy_f32"][:wl.nroots] if m else None
+        out["runs"].append({"sigma": names[m], "seconds": dt, "iterations": info["iterations"],
+                            "iterations_lowp": info["iterations_f32"], "nsigma": info["nsigma"],
+                            "nsigma_lowp": info["nsigma_f32"], "energies": [float(x) for x in e],
+                            "converged": info["converged"], "status": info["status"],
+                            "energy_lowp_phase": e_low,
+                            "lowp_phase_error_Eh": (max(abs(a - b) for a, b in zip(e_low, e)) if m else 0.0)})
+    ref = out["runs"][0]["energies"]
+    for r in out["runs"]:
+        r["final_vs_first_mode_Eh"] = max(abs(a - b) for a, b in zip(r["energies"], ref))
+    sp.close()
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,6 +322,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--serving", action="store_true", help="serving stream instead of the sigma bench")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--precision-study", action="store_true")
+    ap.add_argument("--modes", default="1,2,3", help="Davidson mixed modes for --precision-study")
+    ap.add_argument("--max-iter", type=int, default=0)
     ap.add_argument("--nreq", type=int, default=48)
     ap.add_argument("--max-count", type=int, default=3000)
     args = ap.parse_args()
@@ -296,6 +334,8 @@ def main():
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.precision_study:
+        return run_precision_study(args)
 
     import torch
     import paper_2503_10335_gb300 as tb

@@ -96,11 +96,11 @@ template <bool BF16>
 __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
     constexpr int ES = BF16 ? 2 : 4;  // element bytes
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int sJa[256], sPq[256], sOccP[64];
     __shared__ float sSa[256], sHa[256];
-    __shared__ int sAbort;
+    __shared__ int sAbort, sAbortTile;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t lb = A.lb;
@@ -111,9 +111,8 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
     const uint32_t a_bytes = (uint32_t)kTileM * Kp * ES, b_bytes = (uint32_t)kTileN * Kp * ES;
     unsigned char *sAh = smem;
     unsigned char *sAl = sAh + (BF16 ? 0 : a_bytes);
-    unsigned char *sBh = sAh + (BF16 ? 1 : 2) * a_bytes;
-    unsigned char *sBl = sBh + (BF16 ? 0 : b_bytes);
-    float *sAcc = reinterpret_cast<float *>(sBh + (BF16 ? 1 : 2) * b_bytes);
+    unsigned char *sBh = sAh + (BF16 ? 1 : 2) * a_bytes;  // two F buffers of (BF16 ? 1 : 2) planes each
+    float *sAcc = reinterpret_cast<float *>(sBh + 2 * (BF16 ? 1 : 2) * b_bytes);
 
     // alpha terms of this row
     if (tid == 0) {
@@ -123,7 +122,8 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
             sOccP[k++] = p * (p + 1) / 2 + p;
         }
         sAbort = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
     }
     for (int k = tid; k < K; k += kTcThreads) {
         if (k == 0) {
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kTileN));
+                     "r"(2 * kTileN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -167,15 +167,20 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
     // instruction descriptor: D F32, A/B BF16 (kind::f16) or TF32 (kind::tf32), K-major, M = 128, N = 64
     const uint32_t idesc = (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) |
                            ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-    const uint32_t sboA = (uint32_t)(Kp * ES / 16) * 128, sboB = sboA;
+    const uint32_t sbo = (uint32_t)(Kp * ES / 16) * 128;
     const int ntiles = (int)((lb + kTileN - 1) / kTileN);
-    const int jb = tid & (kTileN - 1), kq = tid / kTileN;  // staging: column jb, alpha terms kq, kq+4, ...
-    for (int t = 0; t < ntiles; ++t) {
-        const int64_t Jb0 = (int64_t)t * kTileN;
-        const int64_t Jb = Jb0 + jb;
-        // ---- stage F (B operand) and add the diagonal / beta-diagonal / alpha-single terms
+
+    // F tile t into buffer `buf` by `nth` threads starting at thread `t0`; adds the
+    // diagonal, beta-diagonal and alpha-single terms of those columns into sAcc
+    auto stage = [&](int t, int buf, int tid0, int nth) {
+        const int me = tid - tid0;
+        const int jb = me & (kTileN - 1), kstride = nth / kTileN;
+        const int64_t Jb = (int64_t)t * kTileN + jb;
+        unsigned char *bh = sBh + (size_t)buf * (BF16 ? 1 : 2) * b_bytes;
+        unsigned char *bl = bh + (BF16 ? 0 : b_bytes);
         float part = 0.f;
-        for (int k = kq; k < Kp; k += kTcThreads / kTileN) {
+#pragma unroll 4
+        for (int k = me / kTileN; k < Kp; k += kstride) {
             float c = 0.f;
             if (k < K && Jb < lb) {
                 c = __ldg(A.C + (size_t)sJa[k] * lb + Jb);
@@ -188,102 +193,124 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
                 }
                 part = fmaf(coef, c, part);
             }
-            put<BF16>(sBh, sBl, core_off<ES>(jb, k, Kp), core_off<ES>(jb, k, Kp), c);
+            put<BF16>(bh, bl, core_off<ES>(jb, k, Kp), core_off<ES>(jb, k, Kp), c);
         }
         if (Jb < lb && part != 0.f) atomicAdd(&sAcc[Jb], part);
         asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- one thread issues the MMAs of this tile
-        if (tid == 0) {
-            const uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl), bH = smem_u32(sBh), bL = smem_u32(sBl);
-            const int ksteps = BF16 ? Kp / 16 : Kp / 8;  // each step = two core columns = 32 bytes of K
-            for (int ks = 0; ks < ksteps; ++ks) {
-                const uint32_t o = (uint32_t)ks * 256;
-                const uint32_t acc0 = ks > 0 ? 1u : 0u;
-                const uint64_t dAh = smem_desc(aH + o, 128, sboA), dBh = smem_desc(bH + o, 128, sboB);
-                if (BF16) {
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                        "l"(dAh), "l"(dBh), "r"(idesc), "r"(acc0));
-                } else {
-                    const uint64_t dAl = smem_desc(aL + o, 128, sboA), dBl = smem_desc(bL + o, 128, sboB);
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                        "l"(dAh), "l"(dBh), "r"(idesc), "r"(acc0));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(dAh),
-                                 "l"(dBl), "r"(idesc));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(dAl),
-                                 "l"(dBh), "r"(idesc));
-                }
+    };
+    auto issue = [&](int t) {
+        const int buf = t & 1;
+        const uint32_t d = tmem + (uint32_t)(buf * kTileN);
+        const uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl);
+        const uint32_t bH = smem_u32(sBh + (size_t)buf * (BF16 ? 1 : 2) * b_bytes), bL = bH + (BF16 ? 0 : b_bytes);
+        const int ksteps = BF16 ? Kp / 16 : Kp / 8;  // each step = two core columns = 32 bytes of K
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const uint32_t o = (uint32_t)ks * 256;
+            const uint32_t acc0 = ks > 0 ? 1u : 0u;
+            const uint64_t dAh = smem_desc(aH + o, 128, sbo), dBh = smem_desc(bH + o, 128, sbo);
+            if (BF16) {
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                    "l"(dAh), "l"(dBh), "r"(idesc), "r"(acc0));
+            } else {
+                const uint64_t dAl = smem_desc(aL + o, 128, sbo), dBl = smem_desc(bL + o, 128, sbo);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                    "l"(dAh), "l"(dBh), "r"(idesc), "r"(acc0));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dAh), "l"(dBl),
+                             "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dAl), "l"(dBh),
+                             "r"(idesc));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar)));
         }
-        // ---- bounded wait for this tile's MMAs (phase parity = tile index & 1)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&mbar[buf])));
+    };
+    auto wait_tile = [&](int t) -> uint32_t {
         uint32_t done = 0;
         for (int it = 0; it < (1 << 22) && !done; ++it) {
             asm volatile(
                 "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                 : "=r"(done)
-                : "r"(smem_u32(&mbar)), "r"((uint32_t)(t & 1)));
+                : "r"(smem_u32(&mbar[t & 1])), "r"((uint32_t)((t >> 1) & 1)));
         }
-        done = __syncthreads_and(done);  // block-uniform: tcgen05.ld below is warp-collective
-        if (!done) {
-            sAbort = 1;
-            // give the MMAs in flight a second bounded chance to finish before TMEM is freed
-            uint32_t late = 0;
-            for (int it = 0; it < (1 << 22) && !late; ++it)
-                asm volatile(
-                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
-                    "p;\n}"
-                    : "=r"(late)
-                    : "r"(smem_u32(&mbar)), "r"((uint32_t)(t & 1)));
-        }
+        return done;
+    };
+
+    // Pipeline: while the tensor cores run tile t, warps 4-7 stage tile t+1 into
+    // the other F buffer and warps 0-3 drain tile t-1... here tile t, from its
+    // TMEM buffer, as soon as its MMAs complete; one barrier per tile.
+    if (ntiles > 0) {
+        stage(0, 0, 0, kTcThreads);
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- epilogue: warps 0-3 own TMEM lanes (rows rs) 32w .. 32w+31
-        if (done && warp < 4) {
-            const int rs = warp * 32 + lane;
+        if (tid == 0) issue(0);
+    }
+    for (int t = 0; t < ntiles; ++t) {
+        if (warp >= 4) {
+            if (t + 1 < ntiles) stage(t + 1, (t + 1) & 1, 128, kTcThreads - 128);
+        } else {
+            uint32_t done = __all_sync(0xffffffffu, wait_tile(t));  // warp-uniform: tcgen05.ld is collective
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!done) {
+                if (lane == 0) {
+                    sAbort = 1;
+                    sAbortTile = t;
+                }
+            } else {
+                const int rs = warp * 32 + lane;
+                const int64_t Jb0 = (int64_t)t * kTileN;
+                const uint32_t dcol = (uint32_t)((t & 1) * kTileN);
 #pragma unroll
-            for (int c0 = 0; c0 < kTileN; c0 += 16) {
-                uint32_t r[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                      "=r"(r[14]), "=r"(r[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (rs < A.npoff) {
+                for (int c0 = 0; c0 < kTileN; c0 += 16) {
+                    uint32_t r[16];
+                    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + dcol + (uint32_t)c0;
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (rs < A.npoff) {
+                        int32_t e[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t col = Jb0 + c0 + j;
-                        if (col < lb) {
-                            const int32_t e = __ldg(A.lbp + col * A.npoff + rs);
-                            if (e >= 0) {
-                                const float g = __uint_as_float(r[j]);
-                                atomicAdd(&sAcc[e >> 1], (e & 1) ? -g : g);
-                            }
+                        for (int j = 0; j < 16; ++j) {
+                            const int64_t col = Jb0 + c0 + j;
+                            e[j] = col < lb ? __ldg(A.lbp + col * A.npoff + rs) : -1;
                         }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (e[j] >= 0) {
+                                const float g = __uint_as_float(r[j]);
+                                atomicAdd(&sAcc[e[j] >> 1], (e[j] & 1) ? -g : g);
+                            }
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
         if (sAbort) break;
+        if (tid == 0 && t + 1 < ntiles) issue(t + 1);
     }
-    // ---- sigma row += this CTA's contributions
-    if (!sAbort)
+    if (sAbort) {
+        // only the timed-out tile's MMAs can still be in flight: give them a second
+        // bounded chance to finish before TMEM is freed
+        if (tid == 0) {
+            wait_tile(sAbortTile);
+            atomicExch(A.err, 1);
+        }
+    } else {
         for (int64_t j = tid; j < lb; j += kTcThreads) A.S[Ia * lb + j] += sAcc[j];
-    else if (tid == 0)
-        atomicExch(A.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTileN));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTileN));
 }
 
 }  // namespace
@@ -298,7 +325,7 @@ tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, c
     TB_CHECK(ctx, kmax <= 256, TBSCI_EINVAL, "tensor-core sigma: more than 255 alpha singles per string");
     const int kp = (kmax + kKStep - 1) / kKStep * kKStep;
     const size_t es = bf16 ? 2 : 4, planes = bf16 ? 1 : 2;
-    const size_t smem = planes * ((size_t)kTileM * kp * es + (size_t)kTileN * kp * es) + (size_t)lb * sizeof(float);
+    const size_t smem = planes * ((size_t)kTileM * kp * es + 2 * (size_t)kTileN * kp * es) + (size_t)lb * sizeof(float);
     TB_CHECK(ctx, smem <= ctx->smem_optin, TBSCI_EINVAL, "tensor-core sigma: row too long for shared memory");
     TcArgs A{};
     A.la = la;
