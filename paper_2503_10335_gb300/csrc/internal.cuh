@@ -15,11 +15,6 @@ namespace tbsci {
 
 // ------------------------------------------------------------ error plumbing
 
-struct Error {
-    tbsci_status st;
-    std::string msg;
-};
-
 // Records `msg` in the context and returns `st`.
 tbsci_status fail(tbsci_ctx *ctx, tbsci_status st, const std::string &msg);
 

@@ -176,26 +176,38 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
         const int me = tid - tid0;
         const int jb = me & (kTileN - 1), kstride = nth / kTileN;
         const int64_t Jb = (int64_t)t * kTileN + jb;
+        const bool col_ok = Jb < lb;
         unsigned char *bh = sBh + (size_t)buf * (BF16 ? 1 : 2) * b_bytes;
         unsigned char *bl = bh + (BF16 ? 0 : b_bytes);
         float part = 0.f;
-#pragma unroll 4
-        for (int k = me / kTileN; k < Kp; k += kstride) {
-            float c = 0.f;
-            if (k < K && Jb < lb) {
-                c = __ldg(A.C + (size_t)sJa[k] * lb + Jb);
-                float coef;
-                if (k == 0) {
-                    coef = A.ecore + A.Ea[Ia] + __ldg(A.Eb + Jb);
-                    for (int i = 0; i < A.na; ++i) coef += __ldg(A.Uf + (size_t)sOccP[i] * lb + Jb);
-                } else {
-                    coef = sHa[k] + sSa[k] * __ldg(A.Uf + (size_t)sPq[k] * lb + Jb);
-                }
-                part = fmaf(coef, c, part);
+        // batches of 8 alpha terms: all loads of a batch are issued before any use
+        for (int kb = me / kTileN; kb < Kp; kb += 8 * kstride) {
+            float c[8], u[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = kb + q * kstride;
+                const bool ok = k < K && col_ok;
+                c[q] = ok ? __ldg(A.C + (size_t)sJa[k] * lb + Jb) : 0.f;
+                u[q] = (ok && k > 0) ? __ldg(A.Uf + (size_t)sPq[k] * lb + Jb) : 0.f;
             }
-            put<BF16>(bh, bl, core_off<ES>(jb, k, Kp), core_off<ES>(jb, k, Kp), c);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = kb + q * kstride;
+                if (k >= Kp) break;
+                if (k < K && col_ok) {
+                    float coef;
+                    if (k == 0) {
+                        coef = A.ecore + A.Ea[Ia] + __ldg(A.Eb + Jb);
+                        for (int i = 0; i < A.na; ++i) coef += __ldg(A.Uf + (size_t)sOccP[i] * lb + Jb);
+                    } else {
+                        coef = sHa[k] + sSa[k] * u[q];
+                    }
+                    part = fmaf(coef, c[q], part);
+                }
+                put<BF16>(bh, bl, core_off<ES>(jb, k, Kp), core_off<ES>(jb, k, Kp), c[q]);
+            }
         }
-        if (Jb < lb && part != 0.f) atomicAdd(&sAcc[Jb], part);
+        if (col_ok && part != 0.f) atomicAdd(&sAcc[Jb], part);
         asm volatile("fence.proxy.async.shared::cta;");
     };
     auto issue = [&](int t) {
