@@ -49,6 +49,26 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (recipe nominal)
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FMA = 2 flops
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sigma launch
+# from an ncu capture of the default workload, keyed by dtype, with the sha1 of
+# the kernel source it was taken on: a changed kernel reports null until
+# re-captured (profiles/k_sigma_f64_sel16.md).
+NCU_TRAFFIC = {}
+
+
+def _kernel_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2503_10335_gb300", "csrc", "sigma.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def _traffic(dtype):
+    rec = NCU_TRAFFIC.get(dtype)
+    if rec and rec["sha1"] == _kernel_hash():
+        return rec["bytes"]
+    return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -401,7 +421,7 @@ def main():
     achieved = flops_step / launches_per_step / (kern_ms * 1e-3) / 1e12
     peak = FP64_NOMINAL_TFLOPS if args.dtype == "f64" else FP32_NOMINAL_TFLOPS
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_sigma (fused, all classes)",
+                "traffic": _traffic(args.dtype), "kernel": "k_sigma (fused, all classes)",
                 "peak_source": "nominal %s ALU (152 SMs, 2070 MHz)" % ("FP64" if args.dtype == "f64" else "FP32"),
                 "algorithmic_flops_per_launch": flops_step / launches_per_step}
 

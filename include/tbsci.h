@@ -233,8 +233,10 @@ typedef struct tbsci_davidson_info {
 /* Lowest nroots (1..8) eigenpairs of H on a x b by standard Davidson (Sec. III.A)
  * with restart to the lowest restart_keep Ritz vectors when the basis is full
  * (Sec. III.C). Memory: 2 * max_subspace + restart_keep + 3 * nroots FP64
- * vectors (+ 2 * nroots FP32 in mixed mode). Guess:
- * unit vectors at the nroots lowest H_KK (ties by K). Each iteration: Rayleigh
+ * vectors (+ 2 * nroots FP32 in mixed mode). Guess: guess k is the unit vector
+ * at the k-th lowest H_KK (ties by K) plus 0.1 (1 + ((j + k) mod 4)) / 4 times
+ * the unit vector at the (nroots + j)-th lowest, j < 4, orthonormalised, so
+ * every symmetry sector is present. Each iteration: Rayleigh
  * matrix, its eigenpairs, Ritz vectors and residuals, stop when every root has
  * |dE| < tol_energy and ||r|| < tol_residual, else precondition residuals by
  * (theta - H_KK)^-1 (|denominator| clamped at 1e-8), orthonormalise twice

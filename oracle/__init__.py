@@ -263,9 +263,13 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     the new directions twice against the basis and each other, normalise, and
     drop those whose norm fell below 1e-10 of their pre-projection norm.
 
-    ``apply_h(V)`` maps ``[k, N]`` to ``[k, N]``. The guess is the ``nroots``
-    unit vectors at the lowest diagonal entries, ties broken by index.
-    Returns ``(energies, vectors[nroots, N], info)``.
+    ``apply_h(V)`` maps ``[k, N]`` to ``[k, N]``. Guess: guess k is the unit
+    vector at the k-th lowest diagonal entry (ties broken by index) plus
+    0.1 * (1 + ((j + k) mod 4)) / 4 times the unit vector at the (nroots + j)-th
+    lowest, j < 4, orthonormalised in order -- every guess then has components in
+    every symmetry sector (with identical alpha and beta sets H commutes with the
+    alpha-beta transpose, and a closed-shell guess alone would never leave its
+    sector). Returns ``(energies, vectors[nroots, N], info)``.
     """
     diag = np.asarray(diag, dtype=np.float64)
     N = len(diag)
@@ -274,9 +278,16 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     if restart_keep is None:
         restart_keep = max(nroots, max_subspace // 2)
     order = np.lexsort((np.arange(N), diag))
+    extra = min(4, N - nroots)
     V = np.zeros((nroots, N))
     for k in range(nroots):
         V[k, order[k]] = 1.0
+        for j in range(extra):
+            V[k, order[nroots + j]] += 0.1 * (1.0 + ((j + k) % 4)) / 4.0
+    for k in range(nroots):
+        for i in range(k):
+            V[k] -= (V[i] @ V[k]) * V[i]
+        V[k] /= np.linalg.norm(V[k])
     W = apply_h(V)
     nsigma = nroots
     theta_prev = None

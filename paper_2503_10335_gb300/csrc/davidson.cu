@@ -167,10 +167,12 @@ __global__ void k_normalize(const double *x, const double *__restrict__ nrm2, do
         y[K] = s * x[K];
 }
 
-// V[r][idx[r]] = 1 for r < nroots
-__global__ void k_set_units(double *V, int64_t N, const int64_t *idx, int nroots) {
-    const int r = threadIdx.x;
-    if (r < nroots) V[(size_t)r * N + idx[r]] = 1.0;
+// V[r][idx[j]] = M[r][j] for r < nroots, j < ncol (guess vectors on a few determinants)
+__global__ void k_set_guess(double *V, int64_t N, const int64_t *idx, const double *M, int nroots, int ncol) {
+    const int t = threadIdx.x;
+    if (t >= nroots * ncol) return;
+    const int r = t / ncol, j = t - r * ncol;
+    V[(size_t)r * N + idx[j]] = M[t];
 }
 
 // r = wy - theta x; t = r / clamp(theta - diag); partial norms of r
@@ -442,16 +444,20 @@ struct DavEngine {
         rnorm.assign(nroots, INFINITY);
         e32.assign(nroots, 0.0);
         TB_TRY(diagonal_launch(ctx, ham, plan, diag.p, st));
-        // guess: unit vectors at the lowest (H_KK, K)
+        // guess: unit vectors at the nroots lowest (H_KK, K), each mixed with the next
+        // four lowest determinants so that every symmetry sector is present
+        const int extra = (int)std::min<int64_t>(4, N - nroots);
+        const int ncol = nroots + extra;
         std::vector<int64_t> chosen;
-        DevBuf<double> bv;
+        DevBuf<double> bv, dM;
         DevBuf<int64_t> bi, dskip;
         TB_CUDA(ctx, bv.alloc(nblocks));
         TB_CUDA(ctx, bi.alloc(nblocks));
-        TB_CUDA(ctx, dskip.alloc(kMaxOut));
+        TB_CUDA(ctx, dskip.alloc(kMaxOut + 4));
+        TB_CUDA(ctx, dM.alloc((size_t)kMaxOut * (kMaxOut + 4)));
         std::vector<double> hv(nblocks);
         std::vector<int64_t> hi(nblocks);
-        for (int r = 0; r < nroots; ++r) {
+        for (int r = 0; r < ncol; ++r) {
             if (!chosen.empty())
                 TB_CUDA(ctx, cudaMemcpyAsync(dskip.p, chosen.data(), chosen.size() * sizeof(int64_t),
                                              cudaMemcpyHostToDevice, st));
@@ -470,10 +476,27 @@ struct DavEngine {
             TB_CHECK(ctx, bidx >= 0 && bidx < N, TBSCI_EINVAL, "Davidson guess: the diagonal has no finite minimum");
             chosen.push_back(bidx);
         }
+        std::vector<double> M((size_t)nroots * ncol, 0.0);
+        for (int k = 0; k < nroots; ++k) {
+            M[(size_t)k * ncol + k] = 1.0;
+            for (int j = 0; j < extra; ++j) M[(size_t)k * ncol + nroots + j] += 0.1 * (1.0 + ((j + k) % 4)) / 4.0;
+        }
+        for (int k = 0; k < nroots; ++k) {  // Gram-Schmidt in order, on the coefficients
+            for (int i = 0; i < k; ++i) {
+                double d = 0.0;
+                for (int j = 0; j < ncol; ++j) d += M[(size_t)i * ncol + j] * M[(size_t)k * ncol + j];
+                for (int j = 0; j < ncol; ++j) M[(size_t)k * ncol + j] -= d * M[(size_t)i * ncol + j];
+            }
+            double nn = 0.0;
+            for (int j = 0; j < ncol; ++j) nn += M[(size_t)k * ncol + j] * M[(size_t)k * ncol + j];
+            nn = std::sqrt(nn);
+            for (int j = 0; j < ncol; ++j) M[(size_t)k * ncol + j] /= nn;
+        }
         TB_CUDA(ctx, cudaMemsetAsync(V.p, 0, (size_t)nroots * N * sizeof(double), st));
         TB_CUDA(ctx, cudaMemcpyAsync(dskip.p, chosen.data(), chosen.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                                      st));
-        k_set_units<<<1, kMaxOut, 0, st>>>(V.p, N, dskip.p, nroots);
+        TB_CUDA(ctx, cudaMemcpyAsync(dM.p, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_set_guess<<<1, kMaxOut * (kMaxOut + 4), 0, st>>>(V.p, N, dskip.p, dM.p, nroots, ncol);
         TB_CUDA(ctx, cudaGetLastError());
         TB_CUDA(ctx, cudaStreamSynchronize(st));  // bv/bi/dskip are freed on return
         m = 0;

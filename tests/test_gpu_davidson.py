@@ -90,3 +90,20 @@ def test_sel16_mixed_matches_fp64(tb, ctx):
     assert i64["converged"] and i32["converged"]
     assert np.max(np.abs(e64 - e32)) < 1e-8
     sp.close()
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_transpose_antisymmetric_ground_state(tb, ctx, mixed):
+    """Identical alpha/beta sets, lowest state antisymmetric under the transpose,
+    lowest diagonal entry closed-shell (norb 6, 3+3, seed 12): FP64 and mixed
+    Davidson both reach the dense lowest eigenvalues."""
+    n, N = 6, 3
+    h, eri, _ = synth_hamiltonian(n, seed=12)
+    osp = oracle.make_space(n, N, N)
+    w = np.linalg.eigvalsh(oracle.hamiltonian_dense(osp, h, eri, 0.0))
+    sp = tb.Space(ctx, n, N, N, h, eri)
+    for nroots in (1, 2, 3):
+        e, info = sp.davidson(nroots, mixed=mixed)
+        assert info["converged"]
+        assert np.max(np.abs(e - w[:nroots])) < 1e-8, (nroots, e, w[:nroots])
+    sp.close()

@@ -348,3 +348,23 @@ def test_fci8_golden_energies():
     e, X, info = oracle.solve(sp, h, eri, ecore, nroots=3)
     assert info["converged"]
     assert np.max(np.abs(e - ref[:3])) < 1e-8
+
+
+def test_davidson_finds_a_transpose_antisymmetric_ground_state():
+    """norb 6, 3+3 electrons, all strings, seed 12: the lowest eigenvector is
+    antisymmetric under the alpha-beta transpose while the lowest diagonal entry is
+    a closed-shell determinant; the Davidson guess must still reach it."""
+    n, N = 6, 3
+    h, eri, _ = synth_hamiltonian(n, seed=12)
+    sp = oracle.make_space(n, N, N)
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.0)
+    w, U = np.linalg.eigh(H)
+    x = U[:, 0].reshape(sp.la, sp.lb)
+    assert np.linalg.norm(x + x.T) < 1e-8
+    d = np.diag(H)
+    K = np.lexsort((np.arange(len(d)), d))[0]
+    assert K // sp.lb == K % sp.lb
+    for nroots in (1, 2, 3):
+        e, X, info = oracle.davidson(lambda V: V @ H.T, d, nroots)
+        assert info["converged"]
+        assert np.max(np.abs(e - w[:nroots])) < 1e-8
