@@ -416,6 +416,10 @@ def main():
     value = replica_throughput(ws, nvec * sp.ndet, ms_step * 1e-3) / 1e9
 
     # roofline of the fused sigma kernel (one launch per step for nvec <= 4)
+    counts = sp.counts()  # after tuning: carries the chosen launch shape
+    if sdt in (tb.TBSCI_F64, tb.TBSCI_F32):
+        nv_used = counts["tuned_nv"][0 if sdt == tb.TBSCI_F64 else 1] or min(nvec, 4)
+        launches_per_step = (nvec + nv_used - 1) // nv_used
     flops_step = 2.0 * counts["nnz"] * nvec
     kern_ms = statistics.mean(per_step) / launches_per_step
     achieved = flops_step / launches_per_step / (kern_ms * 1e-3) / 1e12

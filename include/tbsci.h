@@ -196,6 +196,8 @@ typedef struct tbsci_sigma_counts {
     int64_t nnz_bb;      /* beta singles + doubles ([0,1], [0,2]) */
     int64_t nnz_ab;      /* alpha-single x beta-single ([1,1]) */
     int64_t bytes_tables;
+    int32_t tuned_threads[2]; /* autotuned CTA size for F64 / F32 (0 = not tuned) */
+    int32_t tuned_nv[2];      /* autotuned vectors per CTA for F64 / F32 */
 } tbsci_sigma_counts;
 tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                                     const tbsci_tables *b, tbsci_sigma_counts *out);

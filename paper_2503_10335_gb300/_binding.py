@@ -51,7 +51,8 @@ assert SINGLE_DTYPE.itemsize == 8 and DOUBLE_DTYPE.itemsize == 12
 
 class SigmaCounts(ctypes.Structure):
     _fields_ = [("ndet", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_aa", ctypes.c_int64),
-                ("nnz_bb", ctypes.c_int64), ("nnz_ab", ctypes.c_int64), ("bytes_tables", ctypes.c_int64)]
+                ("nnz_bb", ctypes.c_int64), ("nnz_ab", ctypes.c_int64), ("bytes_tables", ctypes.c_int64),
+                ("tuned_threads", ctypes.c_int32 * 2), ("tuned_nv", ctypes.c_int32 * 2)]
 
 
 class DavidsonOpts(ctypes.Structure):
@@ -304,7 +305,10 @@ def tbsci_diagonal(ctx, ham, ta, tb, diag, stream=None):
 def tbsci_sigma_counts_get(ctx, ham, ta, tb) -> dict:
     c = SigmaCounts()
     _check(ctx, load().tbsci_sigma_counts_get(ctx, ham, ta, tb, ctypes.byref(c)))
-    return {k: getattr(c, k) for k, _ in SigmaCounts._fields_}
+    d = {k: getattr(c, k) for k, _ in SigmaCounts._fields_}
+    d["tuned_threads"] = list(c.tuned_threads)
+    d["tuned_nv"] = list(c.tuned_nv)
+    return d
 
 
 def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max_iter=0, tol_energy=0.0,

@@ -299,6 +299,10 @@ tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_
     Plan *p = nullptr;
     TB_TRY(plan_get(ctx, ham, a, b, &p));
     *out = p->counts;
+    for (int i = 0; i < 2; ++i) {
+        out->tuned_threads[i] = p->tune_threads[i];
+        out->tuned_nv[i] = p->tune_nv[i];
+    }
     return TBSCI_OK;
 }
 
