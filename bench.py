@@ -53,7 +53,10 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FM
 # from an ncu capture of the default workload, keyed by dtype, with the sha1 of
 # the kernel source it was taken on: a changed kernel reports null until
 # re-captured (profiles/k_sigma_f64_sel16.md).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # tuned shape (512 threads, 2 + 1 vectors per CTA): 6.834 GB + 1.559 GB per 3-vector step
+    "f64": {"sha1": "ac92dfba77b64044e2c81f455e3726490d658570", "bytes": (6.834e9 + 1.559e9) / 2},
+}
 
 
 def _kernel_hash():

@@ -8,10 +8,12 @@
 //   2. polls every admitted solve's Davidson engine without blocking, so the
 //      host logic of whichever solves have finished a phase runs while the
 //      device keeps working on the others (each solve has its own stream);
-//   3. gathers the sigma work that solves are waiting for and issues it as one
-//      batched launch per precision (every job computed exactly as a launch of
-//      its own would: CTAs never mix jobs), ordered after each solve's stream
-//      and before the solve continues;
+//   3. gathers the sigma work that solves are waiting for and issues the small
+//      jobs as one batched launch per precision (every job computed exactly as a
+//      launch of its own would: CTAs never mix jobs), ordered after each solve's
+//      stream and before the solve continues; jobs above 2^20 determinant-vectors
+//      get launches of their own on their solve's stream, so the small batch runs
+//      beside them instead of waiting for them;
 //   4. retires finished solves, releasing their memory for the next admissions.
 #include <algorithm>
 #include <chrono>
@@ -50,11 +52,14 @@ struct Req {
     tbsci::Plan *plan = nullptr;
     tbsci::DavEngine *eng = nullptr;
     cudaEvent_t ready = nullptr;
+    cudaStream_t stream = nullptr;  // the solve's stream (priority by size)
     bool waiting_sigma = false;
 
     void release() {
         if (eng) tbsci::engine_destroy(eng);
         eng = nullptr;
+        if (stream) cudaStreamDestroy(stream);
+        stream = nullptr;
         if (ready) cudaEventDestroy(ready);
         ready = nullptr;
         tbsci_hamiltonian_destroy(ham);
@@ -99,6 +104,8 @@ struct tbsci_server {
     cudaEvent_t sig_done = nullptr;
     tbsci::BatchScratch scratch;
     Clock::time_point t0;
+    int64_t big_job_det = 1 << 20;  // determinants x vectors above which a sigma is not batched
+    int prio_low = 0, prio_high = 0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 
@@ -141,11 +148,16 @@ struct tbsci_server {
         TB_TRY(tbsci_build_excitation_tables(c, q.sb, 0, &q.tb));
         TB_TRY(tbsci_hamiltonian_create(c, q.r.norb, q.h.data(), q.eri.data(), q.r.ecore, &q.ham));
         TB_TRY(tbsci::plan_get(c, q.ham, q.ta, q.tb, &q.plan));
+        // small solves get the highest stream priority: the block scheduler then
+        // prefers their CTAs over the queued CTAs of large solves
+        const bool small = (double)q.la * (double)q.lb * q.r.nroots <= (double)big_job_det;
+        TB_CUDA(c, cudaStreamCreateWithPriority(&q.stream, cudaStreamNonBlocking, small ? prio_high : prio_low));
         tbsci_davidson_opts o{};
         o.mixed = q.r.mixed;
         o.tol_energy = q.r.tol_energy;
         o.tol_residual = q.r.tol_residual;
         o.max_iter = q.r.max_iter;
+        o.stream = (tbsci_stream)q.stream;
         TB_TRY(tbsci::engine_create(c, q.ham, q.plan, q.r.nroots, &o, &q.eng));
         TB_CUDA(c, cudaEventCreateWithFlags(&q.ready, cudaEventDisableTiming));
         return TBSCI_OK;
@@ -213,7 +225,10 @@ struct tbsci_server {
             int k;
             tbsci_dtype dt;
             if (!tbsci::engine_wants_sigma(q->eng, &c, &s, &k, &dt)) continue;
-            if (opts.fuse_sigma < 0) {
+            // large jobs get a launch of their own on their solve's stream, so the
+            // batch of small jobs does not wait behind them (it runs beside them)
+            const bool big = (double)q->la * (double)q->lb * k > (double)big_job_det;
+            if (opts.fuse_sigma < 0 || big) {
                 tbsci_status st = tbsci::sigma_launch(ctx, q->ham, q->plan, c, s, k, dt, tbsci::engine_stream(q->eng));
                 if (st == TBSCI_OK) st = tbsci::engine_sigma_done(q->eng);
                 if (q->t_first < 0) q->t_first = now();
@@ -294,7 +309,8 @@ tbsci_status tbsci_server_create(const tbsci_server_opts *o, tbsci_server **out)
     if (srv->opts.max_queue <= 0) srv->opts.max_queue = 4096;
     tbsci_status st = tbsci_create(srv->opts.device, &srv->ctx);
     if (st != TBSCI_OK) return st;
-    if (cudaStreamCreateWithFlags(&srv->sstream, cudaStreamNonBlocking) != cudaSuccess ||
+    cudaDeviceGetStreamPriorityRange(&srv->prio_low, &srv->prio_high);
+    if (cudaStreamCreateWithPriority(&srv->sstream, cudaStreamNonBlocking, srv->prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&srv->sig_done, cudaEventDisableTiming) != cudaSuccess) {
         tbsci_destroy(srv->ctx);
         return TBSCI_ECUDA;
