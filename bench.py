@@ -314,10 +314,13 @@ def run_precision_study(args):
     for m in modes:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e, info = sp.davidson(wl.nroots, mixed=m, max_iter=args.max_iter, check=False)
+        e, info = sp.davidson(wl.nroots, mixed=m, max_iter=args.max_iter, check=False,
+                              basis_f32=bool(args.basis_f32 and m), max_subspace=args.max_subspace,
+                              restart_keep=args.restart_keep)
         dt = time.perf_counter() - t0
         e_low = info["energy_f32"][:wl.nroots] if m else None
-        out["runs"].append({"sigma": names[m], "seconds": dt, "iterations": info["iterations"],
+        out["runs"].append({"sigma": names[m], "basis": "f32" if (args.basis_f32 and m) else "f64",
+                            "seconds": dt, "iterations": info["iterations"],
                             "iterations_lowp": info["iterations_f32"], "nsigma": info["nsigma"],
                             "nsigma_lowp": info["nsigma_f32"], "energies": [float(x) for x in e],
                             "converged": info["converged"], "status": info["status"],
@@ -348,6 +351,9 @@ def main():
     ap.add_argument("--precision-study", action="store_true")
     ap.add_argument("--modes", default="1,2,3", help="Davidson mixed modes for --precision-study")
     ap.add_argument("--max-iter", type=int, default=0)
+    ap.add_argument("--basis-f32", action="store_true", help="--precision-study: FP32-stored Davidson basis")
+    ap.add_argument("--max-subspace", type=int, default=0)
+    ap.add_argument("--restart-keep", type=int, default=0)
     ap.add_argument("--nreq", type=int, default=48)
     ap.add_argument("--max-count", type=int, default=3000)
     args = ap.parse_args()

@@ -218,6 +218,19 @@ typedef struct tbsci_davidson_opts {
                             tolerances; everything else in FP64 */
     double tol_mixed_residual; /* residual target of the FP32 phase; 0 -> 5e-5 */
     tbsci_stream stream; /* stream for all work; NULL -> the context's stream */
+    int basis_f32;       /* 1 (needs mixed != 0): during the low-precision phase the
+                            basis and its sigma images are stored in FP32 and sigma
+                            reads and writes them in place; dot products and linear
+                            combinations accumulate in FP64, and the Rayleigh matrix
+                            is solved against the measured overlap V^T V (Cholesky),
+                            so rounding of the stored basis does not bias the Ritz
+                            values. The FP32 basis is then released and the FP64
+                            refinement restarts from the Ritz vectors, orthonormalised
+                            in FP64, on a basis of max_subspace_refine vectors.
+                            0: FP64 basis throughout */
+    int max_subspace_refine; /* FP64 basis size after an FP32 basis (restart keeps
+                            max(nroots, max_subspace_refine / 2));
+                            0 -> max(nroots + 1, max_subspace / 2) */
 } tbsci_davidson_opts;
 
 typedef struct tbsci_davidson_info {
@@ -234,8 +247,10 @@ typedef struct tbsci_davidson_info {
 
 /* Lowest nroots (1..8) eigenpairs of H on a x b by standard Davidson (Sec. III.A)
  * with restart to the lowest restart_keep Ritz vectors when the basis is full
- * (Sec. III.C). Memory: 2 * max_subspace + restart_keep + 3 * nroots FP64
- * vectors (+ 2 * nroots FP32 in mixed mode). Guess: guess k is the unit vector
+ * (Sec. III.C). Memory: 2 * max_subspace + restart_keep + 3 * nroots + 1 FP64
+ * vectors (+ 2 * nroots FP32 in mixed mode); with basis_f32, 3 * nroots + 1 FP64
+ * vectors plus the larger of 2 * max_subspace + restart_keep FP32 vectors and
+ * 2 * m_ref + m_ref / 2 FP64 vectors (m_ref = the refinement basis size). Guess: guess k is the unit vector
  * at the k-th lowest H_KK (ties by K) plus 0.1 (1 + ((j + k) mod 4)) / 4 times
  * the unit vector at the (nroots + j)-th lowest, j < 4, orthonormalised, so
  * every symmetry sector is present. Each iteration: Rayleigh

@@ -59,7 +59,8 @@ class DavidsonOpts(ctypes.Structure):
     _fields_ = [("max_subspace", ctypes.c_int), ("restart_keep", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("tol_energy", ctypes.c_double),
                 ("tol_residual", ctypes.c_double), ("mixed", ctypes.c_int),
-                ("tol_mixed_residual", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("tol_mixed_residual", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("basis_f32", ctypes.c_int), ("max_subspace_refine", ctypes.c_int)]
 
 
 class DavidsonInfo(ctypes.Structure):
@@ -313,12 +314,12 @@ def tbsci_sigma_counts_get(ctx, ham, ta, tb) -> dict:
 
 def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max_iter=0, tol_energy=0.0,
                    tol_residual=0.0, mixed=False, tol_mixed_residual=0.0, stream=None, check=True,
-                   restart_keep=0):
+                   restart_keep=0, basis_f32=False, max_subspace_refine=0):
     """Lowest ``nroots`` energies (numpy) and the info dict; ``vecs`` (device FP64
     tensor [nroots][la][lb]) receives the eigenvectors when given."""
     o = DavidsonOpts(max_subspace, restart_keep, max_iter, tol_energy, tol_residual, int(mixed),
                      tol_mixed_residual,
-                     None if stream is None else _stream(stream).value)
+                     None if stream is None else _stream(stream).value, int(basis_f32), max_subspace_refine)
     e = np.zeros(nroots)
     info = DavidsonInfo()
     st = load().tbsci_davidson(ctx, ham, ta, tb, nroots, ctypes.byref(o), _ptr(e), _ptr(vecs), ctypes.byref(info))

@@ -27,9 +27,11 @@ constexpr int kDotThreads = 256;
 constexpr int kMA = 8;  // rows of A per dot block
 constexpr int kMB = 4;  // rows of B per dot block
 
-// partial[b][i][j] over this block's slice of K: sum A[i][K] * B[j][K]
-__global__ void __launch_bounds__(kDotThreads) k_dots(const double *__restrict__ A, int ma, const double *__restrict__ B,
-                                                      int mb, int64_t N, double *partial, int ldp) {
+// partial[b][i][j] over this block's slice of K: sum A[i][K] * B[j][K], in FP64
+// whatever the storage type T of the vectors
+template <typename T>
+__global__ void __launch_bounds__(kDotThreads) k_dots(const T *__restrict__ A, int ma, const T *__restrict__ B, int mb,
+                                                      int64_t N, double *partial, int ldp) {
     __shared__ double sh[kDotThreads / 32][kMA * kMB];
     const int i0 = blockIdx.y * kMA, j0 = blockIdx.z * kMB;
     const int na = min(kMA, ma - i0), nb = min(kMB, mb - j0);
@@ -46,14 +48,14 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(const double *__restrict__
         double b0[kMB], b1[kMB];
 #pragma unroll
         for (int j = 0; j < kMB; ++j) {
-            b0[j] = j < nb ? __ldg(B + (size_t)(j0 + j) * N + K0) : 0.0;
-            b1[j] = (j < nb && h1) ? __ldg(B + (size_t)(j0 + j) * N + K1) : 0.0;
+            b0[j] = j < nb ? (double)__ldg(B + (size_t)(j0 + j) * N + K0) : 0.0;
+            b1[j] = (j < nb && h1) ? (double)__ldg(B + (size_t)(j0 + j) * N + K1) : 0.0;
         }
 #pragma unroll
         for (int i = 0; i < kMA; ++i) {
             if (i < na) {
-                const double a0 = __ldg(A + (size_t)(i0 + i) * N + K0);
-                const double a1 = h1 ? __ldg(A + (size_t)(i0 + i) * N + K1) : 0.0;
+                const double a0 = (double)__ldg(A + (size_t)(i0 + i) * N + K0);
+                const double a1 = h1 ? (double)__ldg(A + (size_t)(i0 + i) * N + K1) : 0.0;
 #pragma unroll
                 for (int j = 0; j < kMB; ++j) acc[i][j] = fma(a1, b1[j], fma(a0, b0[j], acc[i][j]));
             }
@@ -89,10 +91,12 @@ __global__ void k_reduce_partials(const double *partial, int nblocks, int ldp, i
 constexpr int kMaxBasis = 128;
 constexpr int kMaxOut = 8;
 
-// out[k][K] = beta * out[k][K] + yscale * sum_i Y[i][k] * A[i][K], k < kout <= 8.
-// Each thread handles 4 elements spaced blockDim apart per step, so every row
-// read issues 4 independent loads (memory-level parallelism for HBM).
-__global__ void __launch_bounds__(256) k_lincomb(const double *__restrict__ A, int m, double *out, int kout, int64_t N,
+// out[k][K] = beta * out[k][K] + yscale * sum_i Y[i][k] * A[i][K], k < kout <= 8,
+// accumulated in FP64 and stored as TO. Each thread handles 4 elements spaced
+// blockDim apart per step, so every row read issues 4 independent loads
+// (memory-level parallelism for HBM).
+template <typename TA, typename TO>
+__global__ void __launch_bounds__(256) k_lincomb(const TA *__restrict__ A, int m, TO *out, int kout, int64_t N,
                                                  double beta, const double *__restrict__ Y, double yscale) {
     __shared__ double sY[kMaxBasis * kMaxOut];
     for (int x = threadIdx.x; x < m * kout; x += blockDim.x) sY[x] = yscale * Y[x];
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(256) k_lincomb(const double *__restrict__ A, i
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t K = K0 + (int64_t)u * blockDim.x;
-                acc[k][u] = (k < kout && beta != 0.0 && K < N) ? beta * out[(size_t)k * N + K] : 0.0;
+                acc[k][u] = (k < kout && beta != 0.0 && K < N) ? beta * (double)out[(size_t)k * N + K] : 0.0;
             }
 #pragma unroll 2
         for (int i = 0; i < m; ++i) {
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(256) k_lincomb(const double *__restrict__ A, i
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t K = K0 + (int64_t)u * blockDim.x;
-                a[u] = K < N ? __ldg(A + (size_t)i * N + K) : 0.0;
+                a[u] = K < N ? (double)__ldg(A + (size_t)i * N + K) : 0.0;
             }
 #pragma unroll
             for (int k = 0; k < kMaxOut; ++k)
@@ -129,14 +133,15 @@ __global__ void __launch_bounds__(256) k_lincomb(const double *__restrict__ A, i
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int64_t K = K0 + (int64_t)u * blockDim.x;
-                    if (K < N) out[(size_t)k * N + K] = acc[k][u];
+                    if (K < N) out[(size_t)k * N + K] = (TO)acc[k][u];
                 }
     }
 }
 
 // out[k][K] = sum_i Yc[k][i] * A[i][K] (coefficients stored column by column), k < kout <= 8
-__global__ void __launch_bounds__(256) k_lincomb_cols(const double *__restrict__ A, int m, double *out, int kout,
-                                                      int64_t N, const double *__restrict__ Yc) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_lincomb_cols(const T *__restrict__ A, int m, T *out, int kout, int64_t N,
+                                                      const double *__restrict__ Yc) {
     __shared__ double sY[kMaxBasis * kMaxOut];
     for (int x = threadIdx.x; x < m * kout; x += blockDim.x) {
         const int k = x / m, i = x - k * m;
@@ -148,31 +153,33 @@ __global__ void __launch_bounds__(256) k_lincomb_cols(const double *__restrict__
 #pragma unroll
         for (int k = 0; k < kMaxOut; ++k) acc[k] = 0.0;
         for (int i = 0; i < m; ++i) {
-            const double a = __ldg(A + (size_t)i * N + K);
+            const double a = (double)__ldg(A + (size_t)i * N + K);
 #pragma unroll
             for (int k = 0; k < kMaxOut; ++k)
                 if (k < kout) acc[k] = fma(sY[i * kout + k], a, acc[k]);
         }
 #pragma unroll
         for (int k = 0; k < kMaxOut; ++k)
-            if (k < kout) out[(size_t)k * N + K] = acc[k];
+            if (k < kout) out[(size_t)k * N + K] = (T)acc[k];
     }
 }
 
 // y = x / sqrt(*nrm2) (zero when the norm is zero); y may be x
-__global__ void k_normalize(const double *x, const double *__restrict__ nrm2, double *y, int64_t N) {
+template <typename T>
+__global__ void k_normalize(const T *x, const double *__restrict__ nrm2, T *y, int64_t N) {
     const double n2 = *nrm2;
     const double s = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
     for (int64_t K = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; K < N; K += (int64_t)gridDim.x * blockDim.x)
-        y[K] = s * x[K];
+        y[K] = (T)(s * (double)x[K]);
 }
 
 // V[r][idx[j]] = M[r][j] for r < nroots, j < ncol (guess vectors on a few determinants)
-__global__ void k_set_guess(double *V, int64_t N, const int64_t *idx, const double *M, int nroots, int ncol) {
+template <typename T>
+__global__ void k_set_guess(T *V, int64_t N, const int64_t *idx, const double *M, int nroots, int ncol) {
     const int t = threadIdx.x;
     if (t >= nroots * ncol) return;
     const int r = t / ncol, j = t - r * ncol;
-    V[(size_t)r * N + idx[j]] = M[t];
+    V[(size_t)r * N + idx[j]] = (T)M[t];
 }
 
 // r = wy - theta x; t = r / clamp(theta - diag); partial norms of r
@@ -316,6 +323,50 @@ void jacobi_eigh(std::vector<double> a, int m, std::vector<double> &w, std::vect
     v.swap(vs);
 }
 
+// Rayleigh-Ritz on a basis that is orthonormal only to rounding: G y = theta S y
+// with S = V^T V positive definite. Cholesky S = L L^T, eigenpairs z of
+// L^-1 G L^-T by Jacobi, y = L^-T z (S-orthonormal). Same output convention as
+// jacobi_eigh. False when S is not positive definite.
+bool gen_eigh(const std::vector<double> &G, const std::vector<double> &S, int m, std::vector<double> &w,
+              std::vector<double> &y) {
+    std::vector<double> L((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        double d = S[(size_t)j * m + j];
+        for (int k = 0; k < j; ++k) d -= L[(size_t)j * m + k] * L[(size_t)j * m + k];
+        if (!(d > 0.0)) return false;
+        L[(size_t)j * m + j] = std::sqrt(d);
+        for (int i = j + 1; i < m; ++i) {
+            double x = S[(size_t)i * m + j];
+            for (int k = 0; k < j; ++k) x -= L[(size_t)i * m + k] * L[(size_t)j * m + k];
+            L[(size_t)i * m + j] = x / L[(size_t)j * m + j];
+        }
+    }
+    std::vector<double> A(G), B((size_t)m * m), Gh((size_t)m * m), z;
+    for (int c = 0; c < m; ++c)  // A = L^-1 G
+        for (int i = 0; i < m; ++i) {
+            double x = A[(size_t)i * m + c];
+            for (int k = 0; k < i; ++k) x -= L[(size_t)i * m + k] * A[(size_t)k * m + c];
+            A[(size_t)i * m + c] = x / L[(size_t)i * m + i];
+        }
+    for (int c = 0; c < m; ++c)  // B = L^-1 A^T = (L^-1 G L^-T)^T
+        for (int i = 0; i < m; ++i) {
+            double x = A[(size_t)c * m + i];
+            for (int k = 0; k < i; ++k) x -= L[(size_t)i * m + k] * B[(size_t)k * m + c];
+            B[(size_t)i * m + c] = x / L[(size_t)i * m + i];
+        }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) Gh[(size_t)i * m + j] = 0.5 * (B[(size_t)i * m + j] + B[(size_t)j * m + i]);
+    jacobi_eigh(Gh, m, w, z);
+    y.assign((size_t)m * m, 0.0);
+    for (int c = 0; c < m; ++c)  // y = L^-T z
+        for (int i = m - 1; i >= 0; --i) {
+            double x = z[(size_t)i * m + c];
+            for (int k = i + 1; k < m; ++k) x -= L[(size_t)k * m + i] * y[(size_t)k * m + c];
+            y[(size_t)i * m + c] = x / L[(size_t)i * m + i];
+        }
+    return true;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -342,6 +393,12 @@ struct DavEngine {
     int nblocks = 0;
     DevBuf<double> V, W, X, WY, T, diag, R, partial, red, dY, dY2, dtheta, scal, coef;
     DevBuf<float> v32, w32;
+    // FP32-stored basis and images (basis_f32, low-precision phase only); the
+    // Rayleigh problem is then solved against the overlap Sm = V^T V
+    DevBuf<float> V32, W32, R32;
+    bool b32 = false;
+    int m_ref = 0, keep_ref = 0;  // basis size and restart of the FP64 refinement
+    std::vector<double> Sm;
     double *hG = nullptr, *hY = nullptr, *hY2 = nullptr, *hR = nullptr, *hN = nullptr;  // pinned
     enum class St { NeedSigma, WaitG, WaitR, WaitGS, Done } state = St::NeedSigma;
     int m = 0, sig_lo = 0, sig_hi = 0, g_lo = 0;
@@ -365,18 +422,48 @@ struct DavEngine {
         if (own_stream && st) cudaStreamDestroy(st);
     }
 
-    tbsci_status dots(const double *A, int ma, const double *B, int mb, double *out) {
+    // basis slot k of V / W in the current storage type
+    size_t es() const { return b32 ? sizeof(float) : sizeof(double); }
+    void *vs(int k) { return b32 ? (void *)(V32.p + (size_t)k * N) : (void *)(V.p + (size_t)k * N); }
+    void *ws(int k) { return b32 ? (void *)(W32.p + (size_t)k * N) : (void *)(W.p + (size_t)k * N); }
+
+    // out[i][j] = A_i . B_j over basis-typed rows, FP64 accumulation
+    tbsci_status dots(const void *A, int ma, const void *B, int mb, double *out) {
         dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + kMB - 1) / kMB);
         const int ldp = ma * mb;
-        k_dots<<<grid, kDotThreads, 0, st>>>(A, ma, B, mb, N, partial.p, ldp);
+        if (b32)
+            k_dots<float><<<grid, kDotThreads, 0, st>>>((const float *)A, ma, (const float *)B, mb, N, partial.p, ldp);
+        else
+            k_dots<double><<<grid, kDotThreads, 0, st>>>((const double *)A, ma, (const double *)B, mb, N, partial.p,
+                                                         ldp);
         TB_CUDA(ctx, cudaGetLastError());
         k_reduce_partials<<<(ldp + 127) / 128, 128, 0, st>>>(partial.p, nblocks, ldp, ldp, out);
         TB_CUDA(ctx, cudaGetLastError());
         return TBSCI_OK;
     }
-    tbsci_status lincomb(const double *A, int mm, double *out, int kout, double beta, const double *Ydev,
-                         double yscale) {
-        k_lincomb<<<nblocks, 256, 0, st>>>(A, mm, out, kout, N, beta, Ydev, yscale);
+    // basis-typed out = beta * out + yscale * sum_i Y[i][k] A_i
+    tbsci_status lincomb(const void *A, int mm, void *out, int kout, double beta, const double *Ydev, double yscale) {
+        if (b32)
+            k_lincomb<float, float><<<nblocks, 256, 0, st>>>((const float *)A, mm, (float *)out, kout, N, beta, Ydev,
+                                                             yscale);
+        else
+            k_lincomb<double, double><<<nblocks, 256, 0, st>>>((const double *)A, mm, (double *)out, kout, N, beta,
+                                                               Ydev, yscale);
+        TB_CUDA(ctx, cudaGetLastError());
+        return TBSCI_OK;
+    }
+    // FP64 out = sum_i Y[i][k] A_i over basis-typed rows (Ritz vectors and images)
+    tbsci_status ritz(const void *A, int mm, double *out, int kout, const double *Ydev) {
+        if (b32)
+            k_lincomb<float, double><<<nblocks, 256, 0, st>>>((const float *)A, mm, out, kout, N, 0.0, Ydev, 1.0);
+        else
+            k_lincomb<double, double><<<nblocks, 256, 0, st>>>((const double *)A, mm, out, kout, N, 0.0, Ydev, 1.0);
+        TB_CUDA(ctx, cudaGetLastError());
+        return TBSCI_OK;
+    }
+    tbsci_status normalize(void *x, const double *nrm2) {
+        if (b32) k_normalize<float><<<nblocks, 256, 0, st>>>((const float *)x, nrm2, (float *)x, N);
+        else k_normalize<double><<<nblocks, 256, 0, st>>>((const double *)x, nrm2, (double *)x, N);
         TB_CUDA(ctx, cudaGetLastError());
         return TBSCI_OK;
     }
@@ -413,32 +500,44 @@ struct DavEngine {
         TB_CUDA(ctx, cudaEventCreateWithFlags(&evt, cudaEventDisableTiming));
         // small problems use fewer reduction blocks (fixed per problem size: deterministic)
         nblocks = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, (N + 4095) / 4096));
+        f32 = opt.mixed != 0;
+        TB_CHECK(ctx, opt.mixed >= 0 && opt.mixed <= 3, TBSCI_EINVAL, "mixed must be 0..3");
+        lowp = opt.mixed == 2 ? TBSCI_F32_TC_TF32 : opt.mixed == 3 ? TBSCI_F32_TC_BF16 : TBSCI_F32;
+        b32 = opt.basis_f32 != 0;
+        TB_CHECK(ctx, !b32 || f32, TBSCI_EINVAL, "basis_f32 needs a low-precision phase (mixed != 0)");
+        m_ref = b32 ? (opt.max_subspace_refine > 0 ? opt.max_subspace_refine : std::max(nroots + 1, m_max / 2)) : m_max;
+        TB_CHECK(ctx, m_ref >= nroots + 1 && m_ref <= m_max, TBSCI_EINVAL,
+                 "max_subspace_refine must be in nroots+1..max_subspace");
+        keep_ref = b32 ? std::max(nroots, m_ref / 2) : keep;
         TB_CUDA(ctx, partial.alloc((size_t)nblocks * std::max(m_max * m_max, kMaxOut)));
-        TB_CUDA(ctx, red.alloc((size_t)m_max * m_max));
+        TB_CUDA(ctx, red.alloc((size_t)2 * m_max * m_max));
         TB_CUDA(ctx, dY.alloc((size_t)m_max * m_max));
         TB_CUDA(ctx, dY2.alloc((size_t)m_max * m_max));
         TB_CUDA(ctx, dtheta.alloc(kMaxOut));
         TB_CUDA(ctx, scal.alloc(2 * kMaxOut));
         TB_CUDA(ctx, coef.alloc((size_t)m_max * kMaxOut));
-        TB_CUDA(ctx, cudaMallocHost(&hG, (size_t)m_max * m_max * sizeof(double)));
+        TB_CUDA(ctx, cudaMallocHost(&hG, (size_t)2 * m_max * m_max * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hY, (size_t)m_max * m_max * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hY2, (size_t)m_max * m_max * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hR, kMaxOut * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hN, 2 * kMaxOut * sizeof(double)));
-        TB_CUDA(ctx, V.alloc((size_t)m_max * N));
-        TB_CUDA(ctx, W.alloc((size_t)m_max * N));
+        if (b32) {
+            TB_CUDA(ctx, V32.alloc((size_t)m_max * N));
+            TB_CUDA(ctx, W32.alloc((size_t)m_max * N));
+        } else {
+            TB_CUDA(ctx, V.alloc((size_t)m_max * N));
+            TB_CUDA(ctx, W.alloc((size_t)m_max * N));
+        }
         TB_CUDA(ctx, X.alloc((size_t)nroots * N));
         TB_CUDA(ctx, WY.alloc((size_t)nroots * N));
         TB_CUDA(ctx, T.alloc((size_t)nroots * N));
         TB_CUDA(ctx, diag.alloc(N));
-        f32 = opt.mixed != 0;
-        TB_CHECK(ctx, opt.mixed >= 0 && opt.mixed <= 3, TBSCI_EINVAL, "mixed must be 0..3");
-        lowp = opt.mixed == 2 ? TBSCI_F32_TC_TF32 : opt.mixed == 3 ? TBSCI_F32_TC_BF16 : TBSCI_F32;
-        if (f32) {
+        if (f32 && !b32) {
             TB_CUDA(ctx, v32.alloc((size_t)nroots * N));
             TB_CUDA(ctx, w32.alloc((size_t)nroots * N));
         }
         G.assign((size_t)m_max * m_max, 0.0);
+        Sm.assign((size_t)m_max * m_max, 0.0);
         theta.assign(nroots, 0.0);
         theta_prev.assign(nroots, INFINITY);
         rnorm.assign(nroots, INFINITY);
@@ -492,11 +591,12 @@ struct DavEngine {
             nn = std::sqrt(nn);
             for (int j = 0; j < ncol; ++j) M[(size_t)k * ncol + j] /= nn;
         }
-        TB_CUDA(ctx, cudaMemsetAsync(V.p, 0, (size_t)nroots * N * sizeof(double), st));
+        TB_CUDA(ctx, cudaMemsetAsync(vs(0), 0, (size_t)nroots * N * es(), st));
         TB_CUDA(ctx, cudaMemcpyAsync(dskip.p, chosen.data(), chosen.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                                      st));
         TB_CUDA(ctx, cudaMemcpyAsync(dM.p, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        k_set_guess<<<1, kMaxOut * (kMaxOut + 4), 0, st>>>(V.p, N, dskip.p, dM.p, nroots, ncol);
+        if (b32) k_set_guess<float><<<1, kMaxOut * (kMaxOut + 4), 0, st>>>(V32.p, N, dskip.p, dM.p, nroots, ncol);
+        else k_set_guess<double><<<1, kMaxOut * (kMaxOut + 4), 0, st>>>(V.p, N, dskip.p, dM.p, nroots, ncol);
         TB_CUDA(ctx, cudaGetLastError());
         TB_CUDA(ctx, cudaStreamSynchronize(st));  // bv/bi/dskip are freed on return
         m = 0;
@@ -511,19 +611,18 @@ struct DavEngine {
     bool wants_sigma(const void **c, void **s, int *k, tbsci_dtype *dt) {
         if (state != St::NeedSigma) return false;
         const int kk = sig_hi - sig_lo;
-        if (f32) {
+        if (f32 && !b32) {
             if (!sig_prepared) {
                 k_to_f32<<<nblocks, 256, 0, st>>>(V.p + (size_t)sig_lo * N, v32.p, (int64_t)kk * N);
                 sig_prepared = true;
             }
             *c = v32.p;
             *s = w32.p;
-            *dt = lowp;
-        } else {
-            *c = V.p + (size_t)sig_lo * N;
-            *s = W.p + (size_t)sig_lo * N;
-            *dt = TBSCI_F64;
+        } else {  // FP64 basis with FP64 sigma, or FP32 basis with low-precision sigma in place
+            *c = vs(sig_lo);
+            *s = ws(sig_lo);
         }
+        *dt = f32 ? lowp : TBSCI_F64;
         *k = kk;
         return true;
     }
@@ -531,18 +630,23 @@ struct DavEngine {
     // Called once the sigma of wants_sigma() is enqueued on (or ordered before) the engine stream.
     tbsci_status sigma_done() {
         const int kk = sig_hi - sig_lo;
-        if (f32) {
+        if (f32 && !b32) {
             k_to_f64<<<nblocks, 256, 0, st>>>(w32.p, W.p + (size_t)sig_lo * N, (int64_t)kk * N);
             TB_CUDA(ctx, cudaGetLastError());
-            nsig32 += kk;
         }
+        if (f32) nsig32 += kk;
         nsig += kk;
         sig_prepared = false;
         m = sig_hi;
-        // Rayleigh-matrix columns g_lo..m against rows 0..m
-        TB_TRY(dots(V.p, m, W.p + (size_t)g_lo * N, m - g_lo, red.p));
+        // Rayleigh-matrix columns g_lo..m against rows 0..m (and overlap columns for an FP32 basis)
+        return fetch_G();
+    }
+
+    tbsci_status fetch_G() {
+        TB_TRY(dots(vs(0), m, ws(g_lo), m - g_lo, red.p));
         const int ld = m * (m - g_lo);
-        TB_CUDA(ctx, cudaMemcpyAsync(hG, red.p, (size_t)ld * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (b32) TB_TRY(dots(vs(0), m, vs(g_lo), m - g_lo, red.p + ld));
+        TB_CUDA(ctx, cudaMemcpyAsync(hG, red.p, (size_t)(b32 ? 2 : 1) * ld * sizeof(double), cudaMemcpyDeviceToHost, st));
         return finish_phase(St::WaitG);
     }
 
@@ -553,15 +657,23 @@ struct DavEngine {
         std::vector<double> Gm((size_t)m * m), w;
         for (int i = 0; i < m; ++i)
             for (int j = 0; j < m; ++j) Gm[(size_t)i * m + j] = G[(size_t)i * m_max + j];
-        jacobi_eigh(Gm, m, w, Yv);
+        if (b32) {
+            std::vector<double> Sg((size_t)m * m);
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < m; ++j) Sg[(size_t)i * m + j] = Sm[(size_t)i * m_max + j];
+            TB_CHECK(ctx, gen_eigh(Gm, Sg, m, w, Yv), TBSCI_ENOCONV,
+                     "Davidson: the FP32 basis lost linear independence (overlap not positive definite)");
+        } else {
+            jacobi_eigh(Gm, m, w, Yv);
+        }
         for (int k = 0; k < nroots; ++k) theta[k] = w[k];
         for (int i = 0; i < m; ++i)
             for (int k = 0; k < nroots; ++k) hY[(size_t)i * nroots + k] = Yv[(size_t)i * m + k];
         TB_CUDA(ctx, cudaMemcpyAsync(dY.p, hY, (size_t)m * nroots * sizeof(double), cudaMemcpyHostToDevice, st));
         for (int k = 0; k < nroots; ++k) hR[k] = theta[k];
         TB_CUDA(ctx, cudaMemcpyAsync(dtheta.p, hR, nroots * sizeof(double), cudaMemcpyHostToDevice, st));
-        TB_TRY(lincomb(V.p, m, X.p, nroots, 0.0, dY.p, 1.0));
-        TB_TRY(lincomb(W.p, m, WY.p, nroots, 0.0, dY.p, 1.0));
+        TB_TRY(ritz(vs(0), m, X.p, nroots, dY.p));
+        TB_TRY(ritz(ws(0), m, WY.p, nroots, dY.p));
         k_residual<<<nblocks, kDotThreads, 0, st>>>(X.p, WY.p, diag.p, dtheta.p, nroots, N, T.p, partial.p);
         TB_CUDA(ctx, cudaGetLastError());
         k_reduce_partials<<<1, 32, 0, st>>>(partial.p, nblocks, kMaxOut, nroots, red.p);
@@ -571,19 +683,50 @@ struct DavEngine {
         return finish_phase(St::WaitR);
     }
 
+    // End of the low-precision phase with an FP32-stored basis: release it, then
+    // continue on an FP64 basis of m_ref vectors that starts from the Ritz vectors
+    // (in X, FP64), orthonormalised in FP64 because the FP32 basis was orthonormal
+    // only to FP32 rounding. Peak memory is the larger phase, not the sum.
+    tbsci_status leave_basis32() {
+        TB_CUDA(ctx, cudaStreamSynchronize(st));
+        V32.release();
+        W32.release();
+        R32.release();
+        b32 = false;
+        m_max = m_ref;
+        keep = keep_ref;
+        TB_CUDA(ctx, V.alloc((size_t)m_max * N));
+        TB_CUDA(ctx, W.alloc((size_t)m_max * N));
+        TB_CUDA(ctx, cudaMemcpyAsync(V.p, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        for (int j = 0; j < nroots; ++j) {
+            double *t = V.p + (size_t)j * N;
+            for (int pass = 0; pass < 2 && j > 0; ++pass) {
+                TB_TRY(dots(V.p, j, t, 1, coef.p));
+                TB_TRY(lincomb(V.p, j, t, 1, 1.0, coef.p, -1.0));
+            }
+            TB_TRY(dots(t, 1, t, 1, scal.p));
+            TB_TRY(normalize(t, scal.p));
+        }
+        return TBSCI_OK;
+    }
+
     tbsci_status after_G() {
         const int cols = m - g_lo;
-        for (int i = 0; i < m; ++i)
-            for (int j = g_lo; j < m; ++j) {
-                const double g = hG[(size_t)i * cols + (j - g_lo)];
-                G[(size_t)i * m_max + j] = g;
-                if (i < g_lo) G[(size_t)j * m_max + i] = g;
-            }
-        for (int i = g_lo; i < m; ++i)
-            for (int j = i + 1; j < m; ++j) {
-                const double g = 0.5 * (G[(size_t)i * m_max + j] + G[(size_t)j * m_max + i]);
-                G[(size_t)i * m_max + j] = G[(size_t)j * m_max + i] = g;
-            }
+        for (int half = 0; half < (b32 ? 2 : 1); ++half) {
+            std::vector<double> &M = half == 0 ? G : Sm;
+            const double *src = hG + (size_t)half * m * cols;
+            for (int i = 0; i < m; ++i)
+                for (int j = g_lo; j < m; ++j) {
+                    const double g = src[(size_t)i * cols + (j - g_lo)];
+                    M[(size_t)i * m_max + j] = g;
+                    if (i < g_lo) M[(size_t)j * m_max + i] = g;
+                }
+            for (int i = g_lo; i < m; ++i)
+                for (int j = i + 1; j < m; ++j) {
+                    const double g = 0.5 * (M[(size_t)i * m_max + j] + M[(size_t)j * m_max + i]);
+                    M[(size_t)i * m_max + j] = M[(size_t)j * m_max + i] = g;
+                }
+        }
         return head();
     }
 
@@ -611,7 +754,8 @@ struct DavEngine {
             // end of the FP32 phase: restart from the roots' Ritz vectors with FP64 sigma
             e32 = theta;
             f32 = false;
-            TB_CUDA(ctx, cudaMemcpyAsync(V.p, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            if (b32) TB_TRY(leave_basis32());
+            else TB_CUDA(ctx, cudaMemcpyAsync(V.p, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
             m = 0;
             sig_lo = 0;
             sig_hi = nroots;
@@ -636,46 +780,60 @@ struct DavEngine {
         if (m + (int)todo.size() > m_max) {
             // thick restart: keep the lowest `kk` Ritz vectors and their images
             const int kk = std::min(keep, m);
-            if (!R.p) TB_CUDA(ctx, R.alloc((size_t)keep * N));
+            if (b32 && !R32.p) TB_CUDA(ctx, R32.alloc((size_t)keep * N));
+            if (!b32 && !R.p) TB_CUDA(ctx, R.alloc((size_t)keep * N));
             for (int i = 0; i < m; ++i)
                 for (int k = 0; k < kk; ++k) hY2[(size_t)k * m + i] = Yv[(size_t)i * m + k];  // column-major by k
             TB_CUDA(ctx, cudaMemcpyAsync(dY2.p, hY2, (size_t)m * kk * sizeof(double), cudaMemcpyHostToDevice, st));
             for (int half = 0; half < 2; ++half) {
-                double *src = half == 0 ? V.p : W.p;
+                void *src = half == 0 ? vs(0) : ws(0);
                 for (int k0 = 0; k0 < kk; k0 += kMaxOut) {
                     const int kc = std::min(kMaxOut, kk - k0);
-                    k_lincomb_cols<<<nblocks, 256, 0, st>>>(src, m, R.p + (size_t)k0 * N, kc, N, dY2.p + (size_t)k0 * m);
+                    if (b32)
+                        k_lincomb_cols<float><<<nblocks, 256, 0, st>>>((const float *)src, m, R32.p + (size_t)k0 * N,
+                                                                        kc, N, dY2.p + (size_t)k0 * m);
+                    else
+                        k_lincomb_cols<double><<<nblocks, 256, 0, st>>>((const double *)src, m, R.p + (size_t)k0 * N,
+                                                                         kc, N, dY2.p + (size_t)k0 * m);
                     TB_CUDA(ctx, cudaGetLastError());
                 }
-                TB_CUDA(ctx, cudaMemcpyAsync(src, R.p, (size_t)kk * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                TB_CUDA(ctx, cudaMemcpyAsync(src, b32 ? (void *)R32.p : (void *)R.p, (size_t)kk * N * es(),
+                                             cudaMemcpyDeviceToDevice, st));
             }
             m = kk;
             restarted = true;
         }
+        // restart_keep + nroots may exceed the basis: the lowest roots' corrections
+        // take the free slots (keep < max_subspace leaves at least one)
+        if (m + (int)todo.size() > m_max) todo.resize(m_max - m);
         if (todo.empty()) return head();
         // Corrections into the free basis slots, then block Gram-Schmidt on the
         // device: two passes of S = V^T T, T -= V S against the basis (reads the
         // basis 4 times per iteration), then two in-block passes per vector.
         const int nb = (int)todo.size();
-        double *Tb = V.p + (size_t)m * N;
+        void *Tb = vs(m);
         for (int j = 0; j < nb; ++j) {
-            TB_CUDA(ctx, cudaMemcpyAsync(Tb + (size_t)j * N, T.p + (size_t)todo[j] * N, N * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, st));
-            TB_TRY(dots(Tb + (size_t)j * N, 1, Tb + (size_t)j * N, 1, scal.p + 2 * j));
+            if (b32) {
+                k_to_f32<<<nblocks, 256, 0, st>>>(T.p + (size_t)todo[j] * N, V32.p + (size_t)(m + j) * N, N);
+                TB_CUDA(ctx, cudaGetLastError());
+            } else {
+                TB_CUDA(ctx, cudaMemcpyAsync(vs(m + j), T.p + (size_t)todo[j] * N, N * sizeof(double),
+                                             cudaMemcpyDeviceToDevice, st));
+            }
+            TB_TRY(dots(vs(m + j), 1, vs(m + j), 1, scal.p + 2 * j));
         }
         for (int pass = 0; pass < 2; ++pass) {
-            TB_TRY(dots(V.p, m, Tb, nb, coef.p));
-            TB_TRY(lincomb(V.p, m, Tb, nb, 1.0, coef.p, -1.0));
+            TB_TRY(dots(vs(0), m, Tb, nb, coef.p));
+            TB_TRY(lincomb(vs(0), m, Tb, nb, 1.0, coef.p, -1.0));
         }
         for (int j = 0; j < nb; ++j) {
-            double *t = Tb + (size_t)j * N;
+            void *t = vs(m + j);
             for (int pass = 0; pass < 2 && j > 0; ++pass) {
                 TB_TRY(dots(Tb, j, t, 1, coef.p));
                 TB_TRY(lincomb(Tb, j, t, 1, 1.0, coef.p, -1.0));
             }
             TB_TRY(dots(t, 1, t, 1, scal.p + 2 * j + 1));
-            k_normalize<<<nblocks, 256, 0, st>>>(t, scal.p + 2 * j + 1, t, N);
-            TB_CUDA(ctx, cudaGetLastError());
+            TB_TRY(normalize(t, scal.p + 2 * j + 1));
         }
         TB_CUDA(ctx, cudaMemcpyAsync(hN, scal.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
         g_lo = restarted ? 0 : m;
@@ -684,22 +842,18 @@ struct DavEngine {
 
     tbsci_status after_GS() {
         const int nb = (int)todo.size();
+        // a direction that Gram-Schmidt reduced to rounding level carries nothing new
+        // (FP32 storage rounds at 6e-8 of the vector's norm before projection)
+        const double drop = b32 ? 1e-4 : 1e-10;
         int acc = 0;
         for (int j = 0; j < nb; ++j) {
             const double t0 = std::sqrt(std::max(hN[2 * j], 0.0)), nt = std::sqrt(std::max(hN[2 * j + 1], 0.0));
-            if (!(nt > 1e-10 * t0)) continue;  // dropped: nothing new in this direction
-            if (acc != j)
-                TB_CUDA(ctx, cudaMemcpyAsync(V.p + (size_t)(m + acc) * N, V.p + (size_t)(m + j) * N, N * sizeof(double),
-                                             cudaMemcpyDeviceToDevice, st));
+            if (!(nt > drop * t0)) continue;
+            if (acc != j) TB_CUDA(ctx, cudaMemcpyAsync(vs(m + acc), vs(m + j), N * es(), cudaMemcpyDeviceToDevice, st));
             ++acc;
         }
         if (acc == 0) {
-            if (g_lo == 0 && m > 0) {
-                // a restart happened and nothing was added: refresh the Rayleigh matrix
-                TB_TRY(dots(V.p, m, W.p, m, red.p));
-                TB_CUDA(ctx, cudaMemcpyAsync(hG, red.p, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToHost, st));
-                return finish_phase(St::WaitG);
-            }
+            if (g_lo == 0 && m > 0) return fetch_G();  // restarted, nothing added: refresh the Rayleigh matrix
             return head();
         }
         sig_lo = m;
@@ -783,7 +937,15 @@ size_t engine_device_bytes(int64_t N, int nroots, const tbsci_davidson_opts *o) 
     const int m_max = (o && o->max_subspace > 0) ? o->max_subspace : std::max(8 * nroots, nroots + 2);
     const int keep = (o && o->restart_keep > 0) ? o->restart_keep : std::max(nroots, m_max / 2);
     size_t vec = (size_t)(2 * m_max + keep + 3 * nroots + 1) * N * sizeof(double);
-    if (o && o->mixed) vec += (size_t)2 * nroots * N * sizeof(float);
+    if (o && o->mixed && o->basis_f32) {
+        const int m_ref = o->max_subspace_refine > 0 ? o->max_subspace_refine : std::max(nroots + 1, m_max / 2);
+        const int keep_ref = std::max(nroots, m_ref / 2);
+        const size_t phase32 = (size_t)(2 * m_max + keep) * N * sizeof(float);
+        const size_t phase64 = (size_t)(2 * m_ref + keep_ref) * N * sizeof(double);
+        vec = std::max(phase32, phase64) + (size_t)(3 * nroots + 1) * N * sizeof(double);
+    } else if (o && o->mixed) {
+        vec += (size_t)2 * nroots * N * sizeof(float);
+    }
     return vec + (size_t)2 * 152 * m_max * m_max * sizeof(double);
 }
 

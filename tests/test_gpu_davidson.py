@@ -107,3 +107,83 @@ def test_transpose_antisymmetric_ground_state(tb, ctx, mixed):
         assert info["converged"]
         assert np.max(np.abs(e - w[:nroots])) < 1e-8, (nroots, e, w[:nroots])
     sp.close()
+
+
+@pytest.mark.parametrize("mixed", [1, 2])
+def test_fp32_basis_vs_dense(tb, ctx, mixed):
+    """FP32-stored basis in the low-precision phase (Rayleigh problem solved against
+    the measured overlap of the stored basis), then FP64 refinement on a smaller
+    FP64 basis: the dense eigenvalues to 1e-8 Eh, H x = E x and unit norm for
+    every returned vector. The low-precision phase runs for over a hundred
+    iterations with 4 corrections each, so the FP32 basis is thick-restarted
+    many times."""
+    n, na, nb = 8, 4, 3
+    h, eri, _ = synth_hamiltonian(n, seed=41)
+    asel = selected_strings(n, na, 50, 42)
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.1, alpha=asel)
+    osp = oracle.make_space(n, na, nb, asel, None)
+    H = oracle.hamiltonian_dense(osp, h, eri, 0.1)
+    w = np.linalg.eigvalsh(H)
+    e, info, X = sp.davidson(4, want_vectors=True, mixed=mixed, basis_f32=True, max_subspace=16)
+    assert info["converged"], info
+    assert info["nsigma_f32"] > 0 and info["nsigma"] > info["nsigma_f32"]
+    assert np.max(np.abs(e - w[:4])) < 1e-8, (e, w[:4])
+    X = X.cpu().numpy().reshape(4, -1)
+    for k in range(4):
+        assert np.linalg.norm(H @ X[k] - e[k] * X[k]) < 2e-5
+        assert abs(np.linalg.norm(X[k]) - 1.0) < 1e-10
+    sp.close()
+
+
+def test_fp32_basis_fci8_golden(tb, ctx):
+    wl = WORKLOADS["fci8"]
+    h, eri, ecore = wl.hamiltonian()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore)
+    ref = np.loadtxt(os.path.join(GOLDEN, "fci8_energies.txt"))
+    e, info = sp.davidson(3, mixed=1, basis_f32=True)
+    assert info["converged"]
+    assert np.max(np.abs(e - ref[:3])) < 1e-8, (e, ref[:3])
+    sp.close()
+
+
+def test_fp32_basis_sel16_matches_fp64(tb, ctx):
+    """norb=16, 3,000 x 3,000 (9.0M determinants), 3 roots: the FP32 basis with
+    FP64 refinement reaches the FP64-basis energies to 1e-8 Eh."""
+    wl = WORKLOADS["sel16"]
+    h, eri, ecore = wl.hamiltonian()
+    asel, bsel = wl.alpha_selection(), wl.beta_selection()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=asel, beta=bsel)
+    e64, i64 = sp.davidson(3)
+    e32, i32 = sp.davidson(3, mixed=1, basis_f32=True)
+    assert i64["converged"] and i32["converged"]
+    assert np.max(np.abs(e64 - e32)) < 1e-8, (e64, e32)
+    sp.close()
+
+
+def test_fp32_basis_argument_checks(tb, ctx):
+    n, na, nb = 6, 3, 3
+    h, eri, _ = synth_hamiltonian(n, seed=5)
+    sp = tb.Space(ctx, n, na, nb, h, eri)
+    for kw in ({"basis_f32": True},  # needs a low-precision phase
+               {"basis_f32": True, "mixed": 1, "max_subspace": 8, "max_subspace_refine": 9},
+               {"basis_f32": True, "mixed": 1, "max_subspace": 8, "max_subspace_refine": 2}):
+        with pytest.raises(tb.B.TbsciError) as err:
+            sp.davidson(2, **kw)
+        assert err.value.status == tb.TBSCI_EINVAL, kw
+    sp.close()
+
+
+def test_restart_with_fewer_free_slots_than_roots(tb, ctx):
+    """max_subspace 12 with 4 roots keeps 10 Ritz vectors at each restart, leaving
+    two free slots for four corrections: the lowest unconverged roots' take them,
+    and all four dense eigenvalues are still reached."""
+    n, na, nb = 8, 4, 3
+    h, eri, _ = synth_hamiltonian(n, seed=41)
+    asel = selected_strings(n, na, 50, 42)
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.1, alpha=asel)
+    osp = oracle.make_space(n, na, nb, asel, None)
+    w = np.linalg.eigvalsh(oracle.hamiltonian_dense(osp, h, eri, 0.1))
+    e, info = sp.davidson(4, max_subspace=12, restart_keep=10)
+    assert info["converged"], info
+    assert np.max(np.abs(e - w[:4])) < 1e-8, (e, w[:4])
+    sp.close()

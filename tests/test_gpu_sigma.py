@@ -4,6 +4,8 @@ Full element-by-element comparison on spaces the oracle finishes in seconds
 (several CTAs, ragged column counts, nvec that splits across launches), and at
 the full norb=16, 3,000 x 3,000 size on sampled rows in the launch
 configuration the bench times (FP64, 3 vectors)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -170,6 +172,33 @@ def test_invalid_arguments(tb, ctx):
         tb.tbsci_prepare(ctx.handle, sp.ham, t, t)
     tb.tbsci_tables_destroy(t)
     tb.tbsci_strings_destroy(s)
+    sp.close()
+
+
+@pytest.mark.parametrize("n,dtype", [(18, "f64"), (18, "f32"), (19, "f64"), (19, "f32")])
+def test_sigma_rows_longer_than_shared_memory(tb, ctx, n, dtype):
+    """Full beta string spaces of norb 18 and 19 with 9 beta electrons (48,620 and
+    92,378 strings: 389 KB and 739 KB per FP64 row) and 4 selected alpha strings:
+    c rows and sigma accumulators that do not fit in shared memory are read and
+    accumulated in global memory. 500 sampled rows against the oracle."""
+    import torch
+    na = nb = 9
+    h, eri, _ = synth_hamiltonian(n, seed=300 + n)
+    asel = selected_strings(n, na, 4, 301 + n)
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.5, alpha=asel)
+    osp = oracle.make_space(n, na, nb, asel, None)
+    assert sp.lb == math.comb(n, nb)
+    C = random_vectors(2, sp.la, sp.lb, seed=n)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    Ct = torch.from_numpy(C).to(tdt).cuda()
+    s = sp.sigma(Ct).double().cpu().numpy().reshape(2, -1)
+    rows = np.sort(np.random.default_rng(n).choice(sp.ndet, 500, replace=False))
+    Cref = Ct.double().cpu().numpy().reshape(2, -1)  # the oracle sees the vector the kernel saw
+    ref, bound = oracle.sigma(osp, h, eri, 0.5, Cref, rows=rows, with_bound=True)
+    if dtype == "f64":
+        assert_sigma_close(s[:, rows], ref, bound)
+    else:
+        assert_sigma_close(s[:, rows], ref, bound, rel=64 * 2.0 ** -24, norm_rel=1e-5)
     sp.close()
 
 

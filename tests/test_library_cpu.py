@@ -60,3 +60,36 @@ def test_product_path_never_touches_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert "tbsci_oracle" not in src and "liboracle" not in src, f
+
+
+def test_binding_struct_layout_matches_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that
+    the C compiler gives the struct of the same name in include/tbsci.h (field
+    names must match the header's member names, or the probe does not compile)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2503_10335_gb300 import _binding as B
+    pairs = [("tbsci_single_link", B.SingleLink), ("tbsci_double_link", B.DoubleLink),
+             ("tbsci_sigma_counts", B.SigmaCounts), ("tbsci_davidson_opts", B.DavidsonOpts),
+             ("tbsci_davidson_info", B.DavidsonInfo), ("tbsci_server_opts", B.ServerOpts),
+             ("tbsci_request", B.Request), ("tbsci_result", B.Result)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tbsci.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        for f in cls._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = []
+    for _, cls in pairs:
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f[0]).offset for f in cls._fields_]
+    assert got == want
