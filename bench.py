@@ -307,10 +307,22 @@ def run_precision_study(args):
     ctx = tb.Context(0)
     sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=wl.alpha_selection(),
                   beta=wl.beta_selection())
-    out = {"metric": METRIC, "mode": "precision_study", "workload": wl.notes, "ndet": sp.ndet,
-           "nroots": wl.nroots, "runs": []}
     names = {0: "f64", 1: "f32", 2: "f32+tf32x3 tensor", 3: "f32+bf16 tensor"}
     modes = [int(x) for x in args.modes.split(",")]
+    tuned = {}
+    if not args.no_autotune:
+        # set-up, untimed: launch shapes of the SIMT sigma kernels the solves use
+        g = torch.Generator(device="cuda").manual_seed(wl.seed_vec)
+        for dt, tdt, name in ((tb.TBSCI_F32, torch.float32, "f32"), (tb.TBSCI_F64, torch.float64, "f64")):
+            if dt == tb.TBSCI_F32 and not any(m > 0 for m in modes):
+                continue
+            C = torch.randn((1, sp.la, sp.lb), generator=g, device="cuda", dtype=torch.float32).to(tdt)
+            S = torch.empty_like(C)
+            tuned[name + "_sigma_ms"] = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, 1, dt)
+            del C, S
+        torch.cuda.empty_cache()
+    out = {"metric": METRIC, "mode": "precision_study", "workload": wl.notes, "ndet": sp.ndet,
+           "nroots": wl.nroots, "counts": sp.counts(), "autotuned_sigma_ms": tuned, "runs": []}
     for m in modes:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -324,6 +336,8 @@ def run_precision_study(args):
                             "iterations_lowp": info["iterations_f32"], "nsigma": info["nsigma"],
                             "nsigma_lowp": info["nsigma_f32"], "energies": [float(x) for x in e],
                             "converged": info["converged"], "status": info["status"],
+                            "seconds_sigma": info["seconds_sigma"],
+                            "seconds_sigma_lowp": info["seconds_sigma_f32"],
                             "energy_lowp_phase": e_low,
                             "lowp_phase_error_Eh": (max(abs(a - b) for a, b in zip(e_low, e)) if m else 0.0)})
     ref = out["runs"][0]["energies"]

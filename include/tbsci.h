@@ -167,12 +167,16 @@ tbsci_status tbsci_prepare(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a
 tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
                          const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream);
 
-/* Autotuner of the SIMT sigma kernel (F64 or F32): times every launch shape
- * (4, 8 or 16 warps per CTA x 1..4 vectors per CTA) on the caller's c and
+/* Autotuner of the SIMT sigma kernel (F64 or F32): times launch shapes (4, 8
+ * or 16 warps per CTA x 1..4 vectors per CTA x shared-memory use: c row and
+ * sigma row in shared memory, sigma row only, or neither) on the caller's c and
  * sigma, keeps the fastest for this space and type (later tbsci_sigma calls use
- * it) and leaves sigma = H c computed. Each column is summed in the same order
- * in every shape, so tuning never changes results. *best_ms: the chosen shape's
- * time (may be NULL). Synchronises `stream`. Errors as tbsci_sigma. */
+ * it) and leaves sigma = H c computed. When one sigma takes 100 ms or more, the
+ * shapes are timed on a strided sample of 16 alpha rows per SM (staging and CTA
+ * size at one vector per CTA, then the vectors per CTA), else every shape on the
+ * whole space. Each column is summed in the same order in every shape, so
+ * tuning never changes results. *best_ms: the chosen shape's time on the whole
+ * space (may be NULL). Synchronises `stream`. Errors as tbsci_sigma. */
 tbsci_status tbsci_sigma_autotune(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
                                   const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream,
                                   double *best_ms);
@@ -198,6 +202,9 @@ typedef struct tbsci_sigma_counts {
     int64_t bytes_tables;
     int32_t tuned_threads[2]; /* autotuned CTA size for F64 / F32 (0 = not tuned) */
     int32_t tuned_nv[2];      /* autotuned vectors per CTA for F64 / F32 */
+    int32_t tuned_stage[2];   /* autotuned shared-memory use for F64 / F32: 0 c row
+                                 staged and sigma row accumulated in shared memory
+                                 where they fit, 1 sigma row only, 2 neither */
 } tbsci_sigma_counts;
 tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                                     const tbsci_tables *b, tbsci_sigma_counts *out);
@@ -212,8 +219,9 @@ typedef struct tbsci_davidson_opts {
     double tol_residual; /* ||r||_2 per root; 0 -> 1e-5 */
     int mixed;           /* 0: FP64 sigma throughout. 1 (F32), 2 (F32_TC_TF32) or
                             3 (F32_TC_BF16): that low-precision sigma until every
-                            residual is below tol_mixed_residual (or stops falling
-                            for 8 iterations), then restart from the roots' Ritz
+                            residual is below tol_mixed_residual (or the largest
+                            has not set a new best 10% below the previous one for
+                            30 iterations), then restart from the roots' Ritz
                             vectors with FP64 sigma and converge to the FP64
                             tolerances; everything else in FP64 */
     double tol_mixed_residual; /* residual target of the FP32 phase; 0 -> 5e-5 */
@@ -242,7 +250,8 @@ typedef struct tbsci_davidson_info {
     double residual[8];  /* final ||r|| per root (first 8) */
     double energy_f32[8];/* energies at the end of the FP32 phase (mixed mode) */
     double seconds_total;
-    double seconds_sigma;
+    double seconds_sigma;     /* device time of all sigma evaluations (blocking call) */
+    double seconds_sigma_f32; /* of which the low-precision phase's */
 } tbsci_davidson_info;
 
 /* Lowest nroots (1..8) eigenpairs of H on a x b by standard Davidson (Sec. III.A)

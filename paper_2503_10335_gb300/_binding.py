@@ -52,7 +52,8 @@ assert SINGLE_DTYPE.itemsize == 8 and DOUBLE_DTYPE.itemsize == 12
 class SigmaCounts(ctypes.Structure):
     _fields_ = [("ndet", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_aa", ctypes.c_int64),
                 ("nnz_bb", ctypes.c_int64), ("nnz_ab", ctypes.c_int64), ("bytes_tables", ctypes.c_int64),
-                ("tuned_threads", ctypes.c_int32 * 2), ("tuned_nv", ctypes.c_int32 * 2)]
+                ("tuned_threads", ctypes.c_int32 * 2), ("tuned_nv", ctypes.c_int32 * 2),
+                ("tuned_stage", ctypes.c_int32 * 2)]
 
 
 class DavidsonOpts(ctypes.Structure):
@@ -67,13 +68,15 @@ class DavidsonInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("nsigma", ctypes.c_int),
                 ("nsigma_f32", ctypes.c_int), ("iterations_f32", ctypes.c_int),
                 ("residual", ctypes.c_double * 8), ("energy_f32", ctypes.c_double * 8),
-                ("seconds_total", ctypes.c_double), ("seconds_sigma", ctypes.c_double)]
+                ("seconds_total", ctypes.c_double), ("seconds_sigma", ctypes.c_double),
+                ("seconds_sigma_f32", ctypes.c_double)]
 
     def as_dict(self):
         return dict(iterations=self.iterations, converged=bool(self.converged), nsigma=self.nsigma,
                     nsigma_f32=self.nsigma_f32, iterations_f32=self.iterations_f32,
                     residual=list(self.residual), energy_f32=list(self.energy_f32),
-                    seconds_total=self.seconds_total, seconds_sigma=self.seconds_sigma)
+                    seconds_total=self.seconds_total, seconds_sigma=self.seconds_sigma,
+                    seconds_sigma_f32=self.seconds_sigma_f32)
 
 
 class ServerOpts(ctypes.Structure):
@@ -309,6 +312,7 @@ def tbsci_sigma_counts_get(ctx, ham, ta, tb) -> dict:
     d = {k: getattr(c, k) for k, _ in SigmaCounts._fields_}
     d["tuned_threads"] = list(c.tuned_threads)
     d["tuned_nv"] = list(c.tuned_nv)
+    d["tuned_stage"] = list(c.tuned_stage)
     return d
 
 

@@ -302,6 +302,7 @@ tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_
     for (int i = 0; i < 2; ++i) {
         out->tuned_threads[i] = p->tune_threads[i];
         out->tuned_nv[i] = p->tune_nv[i];
+        out->tuned_stage[i] = p->tune_stage[i];
     }
     return TBSCI_OK;
 }

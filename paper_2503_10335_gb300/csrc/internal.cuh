@@ -145,7 +145,7 @@ struct Plan {
     DevBuf<int32_t> d_lbp, d_offpair;
     DevBuf<int> d_tc_err;
     // autotuned launch shape per sigma type (index = tbsci_dtype F64 / F32): threads per CTA, vectors per CTA
-    int tune_threads[2] = {0, 0}, tune_nv[2] = {0, 0};
+    int tune_threads[2] = {0, 0}, tune_nv[2] = {0, 0}, tune_stage[2] = {0, 0};
     tbsci_sigma_counts counts{};
 };
 

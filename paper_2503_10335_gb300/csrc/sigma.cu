@@ -424,41 +424,61 @@ tbsci_status launch_one(tbsci_ctx *ctx, SigArgs<T> A, size_t smem, cudaStream_t 
     return launch_th<T, NV, STAGE, ACCS, 128>(ctx, A, smem, st);
 }
 
-template <typename T, int NV>
-tbsci_status launch_nv(tbsci_ctx *ctx, SigArgs<T> A, cudaStream_t st, int threads) {
-    const size_t limit = ctx->smem_optin;
-    size_t sm;
-    if ((sm = smem_bytes<T>(A.npair, A.lb, NV, true, true)) <= limit)
-        return launch_one<T, NV, true, true>(ctx, A, sm, st, threads);
-    if ((sm = smem_bytes<T>(A.npair, A.lb, NV, false, true)) <= limit)
-        return launch_one<T, NV, false, true>(ctx, A, sm, st, threads);
-    sm = smem_bytes<T>(A.npair, A.lb, NV, false, false);
-    return launch_one<T, NV, false, false>(ctx, A, sm, st, threads);
+// Shared-memory use of a launch: stage = 0 stages the c row and accumulates the
+// sigma row in shared memory when both fit, else accumulates only, else neither;
+// stage = 1 at most accumulates; stage = 2 keeps both in global memory (full
+// occupancy on long rows). Returns 0 / 1 / 2 for the variant that runs.
+template <typename T>
+int stage_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int nv, int stage) {
+    if (stage == 0 && smem_bytes<T>(npair, lb, nv, true, true) <= ctx->smem_optin) return 0;
+    if (stage <= 1 && smem_bytes<T>(npair, lb, nv, false, true) <= ctx->smem_optin) return 1;
+    return 2;
 }
 
-// nv_max / threads: 0 = defaults (as many vectors per CTA as fit with staging, up to 4)
+template <typename T, int NV>
+tbsci_status launch_nv(tbsci_ctx *ctx, SigArgs<T> A, cudaStream_t st, int threads, int stage) {
+    switch (stage_variant<T>(ctx, A.npair, A.lb, NV, stage)) {
+        case 0: return launch_one<T, NV, true, true>(ctx, A, smem_bytes<T>(A.npair, A.lb, NV, true, true), st, threads);
+        case 1:
+            return launch_one<T, NV, false, true>(ctx, A, smem_bytes<T>(A.npair, A.lb, NV, false, true), st, threads);
+        default:
+            return launch_one<T, NV, false, false>(ctx, A, smem_bytes<T>(A.npair, A.lb, NV, false, false), st,
+                                                   threads);
+    }
+}
+
+// nv_max / threads: 0 = defaults (as many vectors per CTA as fit with staging, up
+// to 4); stage: -1 = the plan's tuned mode, else 0 (see stage_variant). rows /
+// nrows: launch only these alpha rows (autotuning on a sample), NULL = all.
 template <typename T>
 tbsci_status launch_typed(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, const T *c, T *s, int nvec,
-                          cudaStream_t st, int nv_max = 0, int threads = 0) {
+                          cudaStream_t st, int nv_max = 0, int threads = 0, int stage = -1,
+                          const int32_t *rows = nullptr, int64_t nrows = 0) {
     SigArgs<T> A = make_args<T>(ham, P);
     if (A.la == 0 || A.lb == 0) return TBSCI_OK;
     const int ti = sizeof(T) == 8 ? 0 : 1;
     if (nv_max == 0 && P->tune_nv[ti] > 0) {
         nv_max = P->tune_nv[ti];
         threads = P->tune_threads[ti];
+        if (stage < 0) stage = P->tune_stage[ti];
+    }
+    if (stage < 0) stage = 0;
+    if (rows) {  // grid over the sample; vstride keeps the full row count
+        A.rowsa = rows;
+        A.la = nrows;
     }
     int v = 0;
     while (v < nvec) {
         int rem = nvec - v;
         int nv = std::min(rem, nv_max > 0 ? nv_max : 4);
-        while (nv > 1 && smem_bytes<T>(A.npair, A.lb, nv, true, true) > ctx->smem_optin) --nv;
+        while (stage == 0 && nv > 1 && smem_bytes<T>(A.npair, A.lb, nv, true, true) > ctx->smem_optin) --nv;
         A.C = c + (size_t)v * A.vstride;
         A.S = s + (size_t)v * A.vstride;
         switch (nv) {
-            case 4: TB_TRY((launch_nv<T, 4>(ctx, A, st, threads))); break;
-            case 3: TB_TRY((launch_nv<T, 3>(ctx, A, st, threads))); break;
-            case 2: TB_TRY((launch_nv<T, 2>(ctx, A, st, threads))); break;
-            default: TB_TRY((launch_nv<T, 1>(ctx, A, st, threads))); break;
+            case 4: TB_TRY((launch_nv<T, 4>(ctx, A, st, threads, stage))); break;
+            case 3: TB_TRY((launch_nv<T, 3>(ctx, A, st, threads, stage))); break;
+            case 2: TB_TRY((launch_nv<T, 2>(ctx, A, st, threads, stage))); break;
+            default: TB_TRY((launch_nv<T, 1>(ctx, A, st, threads, stage))); break;
         }
         v += nv;
     }
@@ -548,45 +568,111 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
                             tbsci_dtype dt, cudaStream_t st, double *best_ms) {
     TB_CHECK(ctx, dt == TBSCI_F64 || dt == TBSCI_F32, TBSCI_EINVAL, "autotune: F64 or F32 only");
     const int ti = dt == TBSCI_F64 ? 0 : 1;
+    const int64_t la = plan->A.l, lb = plan->B.l;
+    if (la == 0 || lb == 0 || nvec <= 0) return TBSCI_OK;
+    const int npair = ham->norb * (ham->norb + 1) / 2;
     cudaEvent_t e0, e1;
     TB_CUDA(ctx, cudaEventCreate(&e0));
     TB_CUDA(ctx, cudaEventCreate(&e1));
-    float best = 1e30f;
-    int bt = 0, bn = 0;
+    // runs one candidate `reps` times after one warm-up run; mean ms of the timed runs
+    auto trial = [&](int nv, int th, int stage, const int32_t *rows, int64_t nrows, int reps, float *ms_out) {
+        float tot = 0.f;
+        for (int rep = 0; rep <= reps; ++rep) {
+            TB_CUDA(ctx, cudaEventRecord(e0, st));
+            TB_TRY(dt == TBSCI_F64 ? launch_typed<double>(ctx, ham, plan, static_cast<const double *>(c),
+                                                          static_cast<double *>(s), nvec, st, nv, th, stage, rows,
+                                                          nrows)
+                                   : launch_typed<float>(ctx, ham, plan, static_cast<const float *>(c),
+                                                         static_cast<float *>(s), nvec, st, nv, th, stage, rows,
+                                                         nrows));
+            TB_CUDA(ctx, cudaEventRecord(e1, st));
+            TB_CUDA(ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            TB_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tot += ms;
+        }
+        *ms_out = tot / reps;
+        return TBSCI_OK;
+    };
+    auto variant = [&](int nv, int stage) {
+        return dt == TBSCI_F64 ? stage_variant<double>(ctx, npair, lb, nv, stage)
+                               : stage_variant<float>(ctx, npair, lb, nv, stage);
+    };
     const int threads[3] = {128, 256, 512};
-    tbsci_status st_ret = TBSCI_OK;
-    for (int nv = 1; nv <= std::min(nvec, 4) && st_ret == TBSCI_OK; ++nv) {
-        for (int ti2 = 0; ti2 < 3 && st_ret == TBSCI_OK; ++ti2) {
-            float tot = 0.f;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, st);
-                st_ret = dt == TBSCI_F64
-                             ? launch_typed<double>(ctx, ham, plan, static_cast<const double *>(c),
-                                                    static_cast<double *>(s), nvec, st, nv, threads[ti2])
-                             : launch_typed<float>(ctx, ham, plan, static_cast<const float *>(c),
-                                                   static_cast<float *>(s), nvec, st, nv, threads[ti2]);
-                if (st_ret != TBSCI_OK) break;
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) tot += ms;  // the first run warms the caches
+    const int nvmax = std::min(nvec, 4);
+    auto cu = [&](cudaError_t e) { return e == cudaSuccess ? TBSCI_OK : fail(ctx, TBSCI_ECUDA, std::string("autotune: ") + cudaGetErrorString(e)); };
+    float best = 1e30f, probe = 0.f;
+    int bt = 0, bn = 0, bs = 0;
+    tbsci_status ret = trial(1, 0, 0, nullptr, 0, 1, &probe);
+    if (ret == TBSCI_OK && probe < 100.f) {
+        // small space: every shape on the whole space
+        for (int nv = 1; nv <= nvmax && ret == TBSCI_OK; ++nv) {
+            bool seen[3] = {false, false, false};
+            for (int stage = 0; stage < 3 && ret == TBSCI_OK; ++stage) {
+                const int var = variant(nv, stage);
+                if (seen[var]) continue;
+                seen[var] = true;
+                for (int t = 0; t < 3 && ret == TBSCI_OK; ++t) {
+                    float ms = 0.f;
+                    ret = trial(nv, threads[t], stage, nullptr, 0, 2, &ms);
+                    if (ret == TBSCI_OK && ms < best) {
+                        best = ms;
+                        bt = threads[t];
+                        bn = nv;
+                        bs = stage;
+                    }
+                }
             }
-            if (st_ret == TBSCI_OK && tot / 2 < best) {
-                best = tot / 2;
-                bt = threads[ti2];
+        }
+    } else if (ret == TBSCI_OK) {
+        // large space: time a strided sample of the work-ordered alpha rows (about
+        // 16 CTAs per SM), staging mode and CTA size at one vector per CTA first,
+        // then the vectors per CTA at that choice
+        const int64_t nrows = std::min<int64_t>(la, 16 * (int64_t)ctx->num_sms);
+        std::vector<int32_t> all(la), sample(nrows);
+        DevBuf<int32_t> dsample;
+        ret = cu(cudaMemcpy(all.data(), plan->d_rowsa.p, la * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int64_t j = 0; j < nrows; ++j) sample[j] = all[(j * la) / nrows];
+        if (ret == TBSCI_OK) ret = cu(dsample.alloc(nrows));
+        if (ret == TBSCI_OK)
+            ret = cu(cudaMemcpy(dsample.p, sample.data(), nrows * sizeof(int32_t), cudaMemcpyHostToDevice));
+        bool seen[3] = {false, false, false};
+        for (int stage = 0; stage < 3 && ret == TBSCI_OK; ++stage) {
+            const int var = variant(1, stage);
+            if (seen[var]) continue;
+            seen[var] = true;
+            for (int t = 0; t < 3 && ret == TBSCI_OK; ++t) {
+                float ms = 0.f;
+                ret = trial(1, threads[t], stage, dsample.p, nrows, 1, &ms);
+                if (ret == TBSCI_OK && ms < best) {
+                    best = ms;
+                    bt = threads[t];
+                    bn = 1;
+                    bs = stage;
+                }
+            }
+        }
+        for (int nv = 2; nv <= nvmax && ret == TBSCI_OK; ++nv) {
+            float ms = 0.f;
+            ret = trial(nv, bt, bs, dsample.p, nrows, 1, &ms);
+            if (ret == TBSCI_OK && ms < best) {
+                best = ms;
                 bn = nv;
             }
         }
     }
+    if (ret == TBSCI_OK) {
+        plan->tune_threads[ti] = bt;
+        plan->tune_nv[ti] = bn;
+        plan->tune_stage[ti] = bs;
+        // the chosen shape on the whole space: leaves sigma computed, and its time
+        float ms = 0.f;
+        ret = trial(0, 0, -1, nullptr, 0, 1, &ms);
+        if (ret == TBSCI_OK && best_ms) *best_ms = ms;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    TB_TRY(st_ret);
-    plan->tune_threads[ti] = bt;
-    plan->tune_nv[ti] = bn;
-    if (best_ms) *best_ms = best;
-    // leave sigma computed with the chosen shape
-    return sigma_launch(ctx, ham, plan, c, s, nvec, dt, st);
+    return ret;
 }
 
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,

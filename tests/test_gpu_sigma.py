@@ -264,3 +264,27 @@ def test_autotune_keeps_results_bitwise(tb, ctx):
         assert np.array_equal(out.cpu().numpy(), before)
         assert np.array_equal(sp.sigma(C).cpu().numpy(), before)
     sp.close()
+
+
+def test_autotune_on_row_sample_keeps_results_bitwise(tb, ctx):
+    """norb 16 full space in FP32 (one sigma takes well over 100 ms): the tuner
+    times shapes on a sample of alpha rows, including the shared-memory use, and
+    sigma stays bit-identical before tuning, after it, and with the chosen shape."""
+    import torch
+    wl = WORKLOADS["fci16"]
+    h, eri, ecore = wl.hamiltonian()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    C = torch.randn((1, sp.la, sp.lb), generator=g, device="cuda", dtype=torch.float32)
+    before = sp.sigma(C)
+    out = torch.empty_like(C)
+    ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, out, 1, tb.TBSCI_F32)
+    assert ms > 0
+    assert torch.equal(out, before)
+    assert torch.equal(sp.sigma(C), before)
+    cnt = sp.counts()
+    assert cnt["tuned_threads"][1] in (128, 256, 512) and cnt["tuned_nv"][1] == 1
+    assert cnt["tuned_stage"][1] in (0, 1, 2)
+    del C, out, before
+    sp.close()
+    torch.cuda.empty_cache()
