@@ -313,9 +313,12 @@ def run_precision_study(args):
     if not args.no_autotune:
         # set-up, untimed: launch shapes of the SIMT sigma kernels the solves use
         g = torch.Generator(device="cuda").manual_seed(wl.seed_vec)
-        for dt, tdt, name in ((tb.TBSCI_F32, torch.float32, "f32"), (tb.TBSCI_F64, torch.float64, "f64")):
-            if dt == tb.TBSCI_F32 and not any(m > 0 for m in modes):
+        for dt, tdt, name in ((tb.TBSCI_F32, torch.float32, "f32"), (tb.TBSCI_F32_TC_TF32, torch.float32, "tc"),
+                              (tb.TBSCI_F64, torch.float64, "f64")):
+            if dt == tb.TBSCI_F32 and 1 not in modes:
                 continue
+            if dt == tb.TBSCI_F32_TC_TF32 and not any(m in (2, 3) for m in modes):
+                continue  # one tuning serves both tensor-core types (same SIMT pass)
             C = torch.randn((1, sp.la, sp.lb), generator=g, device="cuda", dtype=torch.float32).to(tdt)
             S = torch.empty_like(C)
             tuned[name + "_sigma_ms"] = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, 1, dt)
@@ -411,7 +414,7 @@ def main():
     launches_per_step = (nvec + 3) // 4 if sdt in (tb.TBSCI_F64, tb.TBSCI_F32) else 2 * nvec
 
     tuned_ms = None
-    if sdt in (tb.TBSCI_F64, tb.TBSCI_F32) and not args.no_autotune:
+    if not args.no_autotune:
         # set-up, untimed: pick the launch shape of the SIMT kernel for this space
         tuned_ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, nvec, sdt, stream)
     for _ in range(args.warmup):

@@ -175,8 +175,11 @@ tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, 
  * shapes are timed on a strided sample of 16 alpha rows per SM (staging and CTA
  * size at one vector per CTA, then the vectors per CTA), else every shape on the
  * whole space. Each column is summed in the same order in every shape, so
- * tuning never changes results. *best_ms: the chosen shape's time on the whole
- * space (may be NULL). Synchronises `stream`. Errors as tbsci_sigma. */
+ * tuning never changes results. For F32_TC_TF32 / F32_TC_BF16 the tensor-core
+ * kernel has one shape; the SIMT pass for the classes it leaves out is tuned
+ * (shared-memory mode x CTA size) and the whole sigma is then run once.
+ * *best_ms: the chosen shape's time on the whole space (may be NULL).
+ * Synchronises `stream`. Errors as tbsci_sigma. */
 tbsci_status tbsci_sigma_autotune(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
                                   const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream,
                                   double *best_ms);
@@ -205,6 +208,9 @@ typedef struct tbsci_sigma_counts {
     int32_t tuned_stage[2];   /* autotuned shared-memory use for F64 / F32: 0 c row
                                  staged and sigma row accumulated in shared memory
                                  where they fit, 1 sigma row only, 2 neither */
+    int32_t tuned_rest[2];    /* tensor-core types: autotuned shared-memory mode and
+                                 CTA size of the SIMT pass for the classes the
+                                 tensor cores leave out (0, 0 = defaults) */
 } tbsci_sigma_counts;
 tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                                     const tbsci_tables *b, tbsci_sigma_counts *out);

@@ -53,7 +53,7 @@ class SigmaCounts(ctypes.Structure):
     _fields_ = [("ndet", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_aa", ctypes.c_int64),
                 ("nnz_bb", ctypes.c_int64), ("nnz_ab", ctypes.c_int64), ("bytes_tables", ctypes.c_int64),
                 ("tuned_threads", ctypes.c_int32 * 2), ("tuned_nv", ctypes.c_int32 * 2),
-                ("tuned_stage", ctypes.c_int32 * 2)]
+                ("tuned_stage", ctypes.c_int32 * 2), ("tuned_rest", ctypes.c_int32 * 2)]
 
 
 class DavidsonOpts(ctypes.Structure):
@@ -313,6 +313,7 @@ def tbsci_sigma_counts_get(ctx, ham, ta, tb) -> dict:
     d["tuned_threads"] = list(c.tuned_threads)
     d["tuned_nv"] = list(c.tuned_nv)
     d["tuned_stage"] = list(c.tuned_stage)
+    d["tuned_rest"] = list(c.tuned_rest)
     return d
 
 

@@ -304,6 +304,8 @@ tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_
         out->tuned_nv[i] = p->tune_nv[i];
         out->tuned_stage[i] = p->tune_stage[i];
     }
+    out->tuned_rest[0] = p->tune_rest_mode;
+    out->tuned_rest[1] = p->tune_rest_threads;
     return TBSCI_OK;
 }
 

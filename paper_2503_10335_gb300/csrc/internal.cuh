@@ -146,6 +146,8 @@ struct Plan {
     DevBuf<int> d_tc_err;
     // autotuned launch shape per sigma type (index = tbsci_dtype F64 / F32): threads per CTA, vectors per CTA
     int tune_threads[2] = {0, 0}, tune_nv[2] = {0, 0}, tune_stage[2] = {0, 0};
+    // autotuned SIMT pass of the tensor-core sigma types (shared-memory mode, threads; 0 = default)
+    int tune_rest_mode = 0, tune_rest_threads = 0;
     tbsci_sigma_counts counts{};
 };
 
@@ -206,7 +208,8 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
 tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const void *c, void *s, int nvec,
                             tbsci_dtype dt, cudaStream_t st, double *best_ms);
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
-                               int nvec, cudaStream_t st);
+                               int nvec, cudaStream_t st, int mode = -1, int threads = 0,
+                               const int32_t *rows = nullptr, int64_t nrows = 0);
 // sigma_tc.cu: the diagonal, alpha singles and all alpha-beta classes on the
 // tensor cores (3xTF32 or BF16 products, FP32 accumulation), added into s.
 tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s, int nvec,

@@ -564,12 +564,96 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
     return TBSCI_OK;
 }
 
+namespace {
+
+int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode);
+
+// Tensor-core sigma types: the tensor-core kernel has one shape; this times the
+// SIMT pass for the other classes over its shared-memory modes and CTA sizes (on
+// a sample of 16 alpha rows per SM when one pass takes 100 ms or more), keeps the
+// fastest, then runs the whole sigma once and reports its time.
+tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const float *c, float *s, int nvec,
+                           tbsci_dtype dt, cudaStream_t st, double *best_ms) {
+    const int64_t la = plan->A.l, lb = plan->B.l;
+    const int npair = ham->norb * (ham->norb + 1) / 2;
+    cudaEvent_t e0, e1;
+    TB_CUDA(ctx, cudaEventCreate(&e0));
+    TB_CUDA(ctx, cudaEventCreate(&e1));
+    auto timed = [&](auto &&launch, int reps, float *ms_out) -> tbsci_status {
+        float tot = 0.f;
+        for (int rep = 0; rep <= reps; ++rep) {
+            TB_CUDA(ctx, cudaEventRecord(e0, st));
+            TB_TRY(launch());
+            TB_CUDA(ctx, cudaEventRecord(e1, st));
+            TB_CUDA(ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            TB_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tot += ms;
+        }
+        *ms_out = tot / reps;
+        return TBSCI_OK;
+    };
+    float probe = 0.f;
+    tbsci_status ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, 0, 0); }, 1, &probe);
+    DevBuf<int32_t> dsample;
+    const int32_t *rows = nullptr;
+    int64_t nrows = 0;
+    if (ret == TBSCI_OK && probe >= 100.f) {
+        nrows = std::min<int64_t>(la, 16 * (int64_t)ctx->num_sms);
+        std::vector<int32_t> all(la), sample(nrows);
+        cudaError_t e = cudaMemcpy(all.data(), plan->d_rowsa.p, la * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        for (int64_t j = 0; j < nrows; ++j) sample[j] = all[(j * la) / nrows];
+        if (e == cudaSuccess) e = dsample.alloc(nrows);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(dsample.p, sample.data(), nrows * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) ret = fail(ctx, TBSCI_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        rows = dsample.p;
+    }
+    const int threads[3] = {128, 256, 512};
+    float best = 1e30f;
+    int bm = 0, bt = 0;
+    bool seen[4] = {false, false, false, false};
+    for (int mode = 0; mode < 3 && ret == TBSCI_OK; ++mode) {
+        const int var = rest_variant(ctx, npair, lb, mode);
+        if (seen[var]) continue;
+        seen[var] = true;
+        for (int t = 0; t < 3 && ret == TBSCI_OK; ++t) {
+            float ms = 0.f;
+            ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, mode, threads[t], rows, nrows); },
+                        rows ? 1 : 2, &ms);
+            if (ret == TBSCI_OK && ms < best) {
+                best = ms;
+                bm = mode;
+                bt = threads[t];
+            }
+        }
+    }
+    if (ret == TBSCI_OK) {
+        plan->tune_rest_mode = bm;
+        plan->tune_rest_threads = bt;
+        float ms = 0.f;
+        ret = timed([&] { return sigma_launch(ctx, ham, plan, c, s, nvec, dt, st); }, 1, &ms);
+        if (ret == TBSCI_OK && best_ms) *best_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ret;
+}
+
+}  // namespace
+
 tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const void *c, void *s, int nvec,
                             tbsci_dtype dt, cudaStream_t st, double *best_ms) {
-    TB_CHECK(ctx, dt == TBSCI_F64 || dt == TBSCI_F32, TBSCI_EINVAL, "autotune: F64 or F32 only");
-    const int ti = dt == TBSCI_F64 ? 0 : 1;
+    TB_CHECK(ctx, dt == TBSCI_F64 || dt == TBSCI_F32 || dt == TBSCI_F32_TC_TF32 || dt == TBSCI_F32_TC_BF16,
+             TBSCI_EINVAL, "autotune: unknown dtype");
     const int64_t la = plan->A.l, lb = plan->B.l;
     if (la == 0 || lb == 0 || nvec <= 0) return TBSCI_OK;
+    if (dt == TBSCI_F32_TC_TF32 || dt == TBSCI_F32_TC_BF16) {
+        if (plan->npoff > 128 || !plan->d_lbp.p) dt = TBSCI_F32;  // these run on the SIMT path
+        else return autotune_rest(ctx, ham, plan, static_cast<const float *>(c), static_cast<float *>(s), nvec, dt,
+                                  st, best_ms);
+    }
+    const int ti = dt == TBSCI_F64 ? 0 : 1;
     const int npair = ham->norb * (ham->norb + 1) / 2;
     cudaEvent_t e0, e1;
     TB_CUDA(ctx, cudaEventCreate(&e0));
@@ -675,36 +759,70 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
     return ret;
 }
 
+namespace {
+
+template <bool STAGE, bool ACCS, int TH>
+tbsci_status launch_rest_th(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t st) {
+    const size_t sm = smem_bytes<float>(A.npair, A.lb, 1, STAGE, ACCS);
+    auto k = k_sigma<float, 1, STAGE, ACCS, TH, true>;
+    TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k<<<(unsigned)A.la, TH, sm, st>>>(A);
+    TB_CUDA(ctx, cudaGetLastError());
+    return TBSCI_OK;
+}
+
+template <bool STAGE, bool ACCS>
+tbsci_status launch_rest_v(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t st, int threads) {
+    if (threads == 512) return launch_rest_th<STAGE, ACCS, 512>(ctx, A, st);
+    if (threads == 256) return launch_rest_th<STAGE, ACCS, 256>(ctx, A, st);
+    return launch_rest_th<STAGE, ACCS, 128>(ctx, A, st);
+}
+
+// Variant of the SIMT pass for a shared-memory mode: 0 = c row staged and sigma
+// row accumulated in shared memory where both fit (else the sigma row only, else
+// neither); 1 = c row only (the pass writes each sigma element once and reads it
+// once, so a global accumulator costs little and frees shared memory); 2 = neither.
+// Returns 0 (c + sigma), 1 (sigma only), 2 (c only) or 3 (neither).
+int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode) {
+    const size_t lim = ctx->smem_optin;
+    if (mode == 0) {
+        if (smem_bytes<float>(npair, lb, 1, true, true) <= lim) return 0;
+        if (smem_bytes<float>(npair, lb, 1, false, true) <= lim) return 1;
+        return 3;
+    }
+    if (mode == 1 && smem_bytes<float>(npair, lb, 1, true, false) <= lim) return 2;
+    return 3;
+}
+
+}  // namespace
+
+// The classes the tensor-core kernel leaves out (same-spin beta singles and
+// doubles, alpha doubles), FP32, one launch per vector. mode / threads: -1 / 0 =
+// the plan's tuned choice (default: mode 0, 512 threads on rows of >= 1024
+// columns, else 128); rows / nrows: launch only these alpha rows (tuning sample).
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
-                               int nvec, cudaStream_t st) {
+                               int nvec, cudaStream_t st, int mode, int threads, const int32_t *rows, int64_t nrows) {
     SigArgs<float> A = make_args<float>(ham, plan);
     if (A.la == 0 || A.lb == 0) return TBSCI_OK;
-    const size_t sm_stage = smem_bytes<float>(A.npair, A.lb, 1, true, true);
-    const size_t sm_acc = smem_bytes<float>(A.npair, A.lb, 1, false, true);
-    const size_t sm_none = smem_bytes<float>(A.npair, A.lb, 1, false, false);
+    if (mode < 0) {
+        mode = plan->tune_rest_mode;
+        threads = plan->tune_rest_threads;
+    }
+    if (threads == 0) threads = A.lb >= 1024 ? 512 : 128;
+    if (rows) {
+        A.rowsa = rows;
+        A.la = nrows;
+    }
+    const int var = rest_variant(ctx, A.npair, A.lb, mode);
     for (int v = 0; v < nvec; ++v) {
         A.C = c + (size_t)v * A.vstride;
         A.S = s + (size_t)v * A.vstride;
-        if (sm_stage <= ctx->smem_optin) {
-            if (A.lb >= 1024) {
-                auto k = k_sigma<float, 1, true, true, 512, true>;
-                TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
-                k<<<(unsigned)A.la, 512, sm_stage, st>>>(A);
-            } else {
-                auto k = k_sigma<float, 1, true, true, 128, true>;
-                TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
-                k<<<(unsigned)A.la, 128, sm_stage, st>>>(A);
-            }
-        } else if (sm_acc <= ctx->smem_optin) {
-            auto k = k_sigma<float, 1, false, true, 512, true>;
-            TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_acc));
-            k<<<(unsigned)A.la, 512, sm_acc, st>>>(A);
-        } else {
-            auto k = k_sigma<float, 1, false, false, 512, true>;
-            TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_none));
-            k<<<(unsigned)A.la, 512, sm_none, st>>>(A);
+        switch (var) {
+            case 0: TB_TRY((launch_rest_v<true, true>(ctx, A, st, threads))); break;
+            case 1: TB_TRY((launch_rest_v<false, true>(ctx, A, st, threads))); break;
+            case 2: TB_TRY((launch_rest_v<true, false>(ctx, A, st, threads))); break;
+            default: TB_TRY((launch_rest_v<false, false>(ctx, A, st, threads))); break;
         }
-        TB_CUDA(ctx, cudaGetLastError());
     }
     return TBSCI_OK;
 }

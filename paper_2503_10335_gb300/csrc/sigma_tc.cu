@@ -33,7 +33,11 @@ namespace tbsci {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+// CTA size: the first half of the warps drains the accumulator, the second
+// stages F. Split TF32 writes two planes per staged element and gains from 32
+// warps; BF16 staging is lighter and runs best with 16.
+template <bool BF16>
+__host__ __device__ constexpr int tc_threads() { return BF16 ? 512 : 1024; }
 constexpr int kTileN = 64;    // beta columns per MMA tile
 constexpr int kTileM = 128;   // off-diagonal pair rows (norb <= 16: <= 120 used)
 constexpr int kKStep = 16;    // K padding granule (a BF16 MMA step; two TF32 steps)
@@ -93,7 +97,11 @@ __device__ __forceinline__ void put(unsigned char *hi, unsigned char *lo, uint32
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
+__global__ void __launch_bounds__(tc_threads<BF16>()) k_sigma_ab_tc(TcArgs A) {
+    constexpr int kTcThreads = tc_threads<BF16>();
+    constexpr int kEpiThreads = kTcThreads / 2;
+    constexpr int kEpiParts = kEpiThreads / 128;  // warps per TMEM lane quarter
+    static_assert(kTileN % (16 * kEpiParts) == 0, "each draining warp reads whole 16-column TMEM chunks");
     constexpr int ES = BF16 ? 2 : 4;  // element bytes
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar[2];
@@ -251,9 +259,9 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
         return done;
     };
 
-    // Pipeline: while the tensor cores run tile t, warps 4-7 stage tile t+1 into
-    // the other F buffer and warps 0-3 drain tile t-1... here tile t, from its
-    // TMEM buffer, as soon as its MMAs complete; one barrier per tile.
+    // Pipeline: while the tensor cores run tile t, the staging warps fill the other
+    // F buffer with tile t+1 and the draining warps read tile t from its TMEM
+    // buffer as soon as its MMAs complete; one barrier per tile.
     if (ntiles > 0) {
         stage(0, 0, 0, kTcThreads);
         __syncthreads();
@@ -261,8 +269,8 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
         if (tid == 0) issue(0);
     }
     for (int t = 0; t < ntiles; ++t) {
-        if (warp >= 4) {
-            if (t + 1 < ntiles) stage(t + 1, (t + 1) & 1, 128, kTcThreads - 128);
+        if (tid >= kEpiThreads) {
+            if (t + 1 < ntiles) stage(t + 1, (t + 1) & 1, kEpiThreads, kTcThreads - kEpiThreads);
         } else {
             uint32_t done = __all_sync(0xffffffffu, wait_tile(t));  // warp-uniform: tcgen05.ld is collective
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -272,13 +280,17 @@ __global__ void __launch_bounds__(kTcThreads) k_sigma_ab_tc(TcArgs A) {
                     sAbortTile = t;
                 }
             } else {
-                const int rs = warp * 32 + lane;
+                // a warp reads the TMEM lanes of its quarter (warp % 4); the warps of
+                // one quarter split the tile's columns
+                const int quarter = warp & 3, part = warp >> 2;
+                const int rs = quarter * 32 + lane;
                 const int64_t Jb0 = (int64_t)t * kTileN;
                 const uint32_t dcol = (uint32_t)((t & 1) * kTileN);
+                constexpr int kCols = kTileN / kEpiParts;
 #pragma unroll
-                for (int c0 = 0; c0 < kTileN; c0 += 16) {
+                for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += 16) {
                     uint32_t r[16];
-                    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + dcol + (uint32_t)c0;
+                    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + dcol + (uint32_t)c0;
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                         "[%16];"
@@ -364,7 +376,7 @@ tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, c
     for (int v = 0; v < nvec; ++v) {
         A.C = c + (size_t)v * la * lb;
         A.S = s + (size_t)v * la * lb;
-        kern<<<(unsigned)la, kTcThreads, smem, st>>>(A);
+        kern<<<(unsigned)la, bf16 ? tc_threads<true>() : tc_threads<false>(), smem, st>>>(A);
         TB_CUDA(ctx, cudaGetLastError());
     }
     return TBSCI_OK;

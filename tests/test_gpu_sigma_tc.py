@@ -84,3 +84,29 @@ def test_tc_mixed_davidson_golden(tb, ctx, mixed):
     assert info["converged"] and info["nsigma_f32"] > 0
     assert np.max(np.abs(e - ref[:3])) < 1e-8
     sp.close()
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("n,na,nb,acnt,bcnt", [(10, 5, 5, 120, 257), (16, 8, 8, 700, 650)])
+def test_tc_sigma_parity_after_autotune(tb, ctx, mode, n, na, nb, acnt, bcnt):
+    """Tuning a tensor-core sigma type picks the shared-memory mode and CTA size of
+    the SIMT pass for the other classes; sigma still matches the oracle."""
+    import torch
+    h, eri, _ = synth_hamiltonian(n, seed=300 + n)
+    asel = selected_strings(n, na, acnt, 31 + n)
+    bsel = selected_strings(n, nb, bcnt, 37 + n)
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.2, alpha=asel, beta=bsel)
+    osp = oracle.make_space(n, na, nb, asel, bsel)
+    C = random_vectors(1, sp.la, sp.lb, seed=n).astype(np.float32)
+    dt = tb.TBSCI_F32_TC_TF32 if mode == "tf32" else tb.TBSCI_F32_TC_BF16
+    Ct = torch.from_numpy(C).cuda()
+    out = torch.empty_like(Ct)
+    ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, Ct, out, 1, dt)
+    assert ms > 0
+    cnt = sp.counts()
+    assert cnt["tuned_rest"][0] in (0, 1, 2) and cnt["tuned_rest"][1] in (128, 256, 512)
+    ref, bound = oracle.sigma(osp, h, eri, 0.2, C.astype(np.float64), with_bound=True)
+    rel, norm_rel = TOL[mode]
+    for s in (out, sp.sigma(Ct, dtype=dt)):
+        assert_sigma_close(s.double().cpu().numpy().reshape(1, -1), ref, bound, rel=rel, norm_rel=norm_rel)
+    sp.close()

@@ -49,7 +49,7 @@ def test_entry_layouts():
     from paper_2503_10335_gb300 import _binding as B
     assert ctypes.sizeof(B.SingleLink) == 8
     assert ctypes.sizeof(B.DoubleLink) == 12
-    assert ctypes.sizeof(B.SigmaCounts) == 72
+    assert ctypes.sizeof(B.SigmaCounts) == 80
 
 
 def test_product_path_never_touches_the_oracle():
