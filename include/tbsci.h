@@ -172,7 +172,7 @@ tbsci_status tbsci_sigma(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, 
  * sigma row in shared memory, sigma row only, or neither) on the caller's c and
  * sigma, keeps the fastest for this space and type (later tbsci_sigma calls use
  * it) and leaves sigma = H c computed. When one sigma takes 100 ms or more, the
- * shapes are timed on a strided sample of 16 alpha rows per SM (staging and CTA
+ * shapes are timed on a strided sample of 64 alpha rows per SM (staging and CTA
  * size at one vector per CTA, then the vectors per CTA), else every shape on the
  * whole space. Each column is summed in the same order in every shape, so
  * tuning never changes results. For F32_TC_TF32 / F32_TC_BF16 the tensor-core

@@ -178,10 +178,11 @@ __global__ void __launch_bounds__(kDotThreads) k_residual(const double *__restri
     double acc[NR];
 #pragma unroll
     for (int k = 0; k < NR; ++k) acc[k] = 0.0;
-    const int64_t step = (int64_t)gridDim.x * kDotThreads * 2;
-    for (int64_t K0 = blockIdx.x * (int64_t)kDotThreads * 2 + threadIdx.x; K0 < N; K0 += step) {
+    // four elements per thread per step: 4 (2 NR + 1) loads in flight
+    const int64_t step = (int64_t)gridDim.x * kDotThreads * 4;
+    for (int64_t K0 = blockIdx.x * (int64_t)kDotThreads * 4 + threadIdx.x; K0 < N; K0 += step) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const int64_t K = K0 + (int64_t)u * kDotThreads;
             if (K >= N) break;
             const double d = diag[K];
@@ -380,6 +381,7 @@ struct DavEngine {
     int64_t N = 0;
     int nblocks = 0;  // blocks of the reduction kernels (fixed per problem size: deterministic sums)
     int lgrid = 0;    // blocks of the linear combinations (no reduction: sized for occupancy)
+    int rgrid = 0;    // blocks of the residual kernel (fixed per problem size, like nblocks)
     DevBuf<double> V, W, X, WY, T, diag, R, partial, red, dY, dY2, dtheta, scal, coef;
     DevBuf<float> v32, w32;
     // FP32-stored basis and images (basis_f32, low-precision phase only); the
@@ -495,6 +497,7 @@ struct DavEngine {
         // small problems use fewer reduction blocks (fixed per problem size: deterministic)
         nblocks = (int)std::min<int64_t>(2 * ctx->num_sms, std::max<int64_t>(1, (N + 4095) / 4096));
         lgrid = (int)std::min<int64_t>(8 * ctx->num_sms, std::max<int64_t>(1, (N + 1023) / 1024));
+        rgrid = (int)std::min<int64_t>(6 * ctx->num_sms, std::max<int64_t>(1, (N + 1023) / 1024));
         f32 = opt.mixed != 0;
         TB_CHECK(ctx, opt.mixed >= 0 && opt.mixed <= 3, TBSCI_EINVAL, "mixed must be 0..3");
         lowp = opt.mixed == 2 ? TBSCI_F32_TC_TF32 : opt.mixed == 3 ? TBSCI_F32_TC_BF16 : TBSCI_F32;
@@ -504,7 +507,8 @@ struct DavEngine {
         TB_CHECK(ctx, m_ref >= nroots + 1 && m_ref <= m_max, TBSCI_EINVAL,
                  "max_subspace_refine must be in nroots+1..max_subspace");
         keep_ref = b32 ? std::max(nroots, m_ref / 2) : keep;
-        TB_CUDA(ctx, partial.alloc((size_t)nblocks * std::max(m_max * m_max, kMaxOut)));
+        TB_CUDA(ctx, partial.alloc(
+                         std::max((size_t)nblocks * m_max * m_max, (size_t)std::max(nblocks, rgrid) * kMaxOut)));
         TB_CUDA(ctx, red.alloc((size_t)2 * m_max * m_max));
         TB_CUDA(ctx, dY.alloc((size_t)m_max * m_max));
         TB_CUDA(ctx, dY2.alloc((size_t)m_max * m_max));
@@ -671,9 +675,9 @@ struct DavEngine {
         TB_TRY(ritz(ws(0), m, WY.p, nroots, dY.p));
         auto resid = nroots <= 1 ? k_residual<1> : nroots <= 2 ? k_residual<2> : nroots <= 4 ? k_residual<4>
                                                                                               : k_residual<8>;
-        resid<<<nblocks, kDotThreads, 0, st>>>(X.p, WY.p, diag.p, dtheta.p, nroots, N, T.p, partial.p);
+        resid<<<rgrid, kDotThreads, 0, st>>>(X.p, WY.p, diag.p, dtheta.p, nroots, N, T.p, partial.p);
         TB_CUDA(ctx, cudaGetLastError());
-        k_reduce_partials<<<1, 32, 0, st>>>(partial.p, nblocks, kMaxOut, nroots, red.p);
+        k_reduce_partials<<<1, 32, 0, st>>>(partial.p, rgrid, kMaxOut, nroots, red.p);
         TB_CUDA(ctx, cudaGetLastError());
         // hR is reused: the copy below is ordered after the upload above on the same stream
         TB_CUDA(ctx, cudaMemcpyAsync(hR, red.p, nroots * sizeof(double), cudaMemcpyDeviceToHost, st));

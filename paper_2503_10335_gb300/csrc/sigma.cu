@@ -566,11 +566,15 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
 
 namespace {
 
+// alpha rows per SM in the autotuner's sample of a large space: several waves of
+// CTAs at every CTA size, so tail and occupancy effects match a full launch
+constexpr int kTuneRowsPerSm = 64;
+
 int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode);
 
 // Tensor-core sigma types: the tensor-core kernel has one shape; this times the
 // SIMT pass for the other classes over its shared-memory modes and CTA sizes (on
-// a sample of 16 alpha rows per SM when one pass takes 100 ms or more), keeps the
+// a sample of 64 alpha rows per SM when one pass takes 100 ms or more), keeps the
 // fastest, then runs the whole sigma once and reports its time.
 tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const float *c, float *s, int nvec,
                            tbsci_dtype dt, cudaStream_t st, double *best_ms) {
@@ -599,7 +603,7 @@ tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, con
     const int32_t *rows = nullptr;
     int64_t nrows = 0;
     if (ret == TBSCI_OK && probe >= 100.f) {
-        nrows = std::min<int64_t>(la, 16 * (int64_t)ctx->num_sms);
+        nrows = std::min<int64_t>(la, kTuneRowsPerSm * (int64_t)ctx->num_sms);
         std::vector<int32_t> all(la), sample(nrows);
         cudaError_t e = cudaMemcpy(all.data(), plan->d_rowsa.p, la * sizeof(int32_t), cudaMemcpyDeviceToHost);
         for (int64_t j = 0; j < nrows; ++j) sample[j] = all[(j * la) / nrows];
@@ -709,10 +713,11 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
             }
         }
     } else if (ret == TBSCI_OK) {
-        // large space: time a strided sample of the work-ordered alpha rows (about
-        // 16 CTAs per SM), staging mode and CTA size at one vector per CTA first,
+        // large space: time a strided sample of the work-ordered alpha rows
+        // (several waves of CTAs, so tails and occupancy show as in a full launch),
+        // staging mode and CTA size at one vector per CTA first,
         // then the vectors per CTA at that choice
-        const int64_t nrows = std::min<int64_t>(la, 16 * (int64_t)ctx->num_sms);
+        const int64_t nrows = std::min<int64_t>(la, kTuneRowsPerSm * (int64_t)ctx->num_sms);
         std::vector<int32_t> all(la), sample(nrows);
         DevBuf<int32_t> dsample;
         ret = cu(cudaMemcpy(all.data(), plan->d_rowsa.p, la * sizeof(int32_t), cudaMemcpyDeviceToHost));
