@@ -184,8 +184,12 @@ tbsci_status tbsci_sigma_autotune(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_ta
                                   const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream,
                                   double *best_ms);
 
-/* Same product with HOST vectors: copies c in, evaluates in FP64, copies sigma
- * out and returns when done (uses a device buffer owned by the context). */
+/* Same product with HOST vectors (pinned memory lets the copies overlap): copies
+ * c in, evaluates in FP64, copies sigma out and returns when done. The vectors go
+ * through in the kernel's launch groups, each group's copies overlapping the
+ * evaluation of its neighbours (two copy streams of the context); the result is
+ * the same as one evaluation of all vectors. Uses device buffers owned by the
+ * context. */
 tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                               const tbsci_tables *b, const double *c, double *sigma, int nvec);
 

@@ -1,7 +1,9 @@
 // extern "C" entry points of libtbsci (declared in include/tbsci.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -75,10 +77,13 @@ void tbsci_destroy(tbsci_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_out) cudaStreamSynchronize(ctx->copy_out);
     ctx->host_c.release();
     ctx->host_s.release();
     ctx->d_binom.release();
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+    if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     delete ctx;
 }
 
@@ -274,11 +279,48 @@ tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables
         TB_CUDA(ctx, ctx->host_c.alloc(n));
         TB_CUDA(ctx, ctx->host_s.alloc(n));
     }
+    if (!ctx->copy_in) TB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
+    if (!ctx->copy_out) TB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
+    // Vectors go through in the launch groups of the (tuned) kernel: group i is
+    // evaluated while group i+1 is copied in and group i-1 copied out, on two copy
+    // streams ordered by events. Vectors are independent and every launch shape
+    // sums a column in the same order, so the result equals one launch over all.
+    const int64_t N = p->A.l * p->B.l;
+    const int g = p->tune_nv[0] > 0 ? p->tune_nv[0] : std::min(nvec, 4);
+    const int ngroups = (nvec + g - 1) / g;
+    std::vector<cudaEvent_t> evs((size_t)2 * ngroups, nullptr);
+    auto cleanup = [&] {
+        for (cudaEvent_t e : evs)
+            if (e) cudaEventDestroy(e);
+    };
+    tbsci_status ret = TBSCI_OK;
+    cudaError_t ce = cudaSuccess;
+    for (size_t i = 0; i < evs.size() && ce == cudaSuccess; ++i)
+        ce = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
     cudaStream_t st = ctx->stream;
-    if (n > 0) TB_CUDA(ctx, cudaMemcpyAsync(ctx->host_c.p, c, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    TB_TRY(sigma_launch(ctx, ham, p, ctx->host_c.p, ctx->host_s.p, nvec, TBSCI_F64, st));
-    if (n > 0) TB_CUDA(ctx, cudaMemcpyAsync(sigma, ctx->host_s.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
-    TB_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int gi = 0; gi < ngroups && ce == cudaSuccess && ret == TBSCI_OK; ++gi) {
+        const int v0 = gi * g, k = std::min(g, nvec - v0);
+        const size_t off = (size_t)v0 * N, cnt = (size_t)k * N;
+        ce = cudaMemcpyAsync(ctx->host_c.p + off, c + off, cnt * sizeof(double), cudaMemcpyHostToDevice,
+                             ctx->copy_in);
+        if (ce == cudaSuccess) ce = cudaEventRecord(evs[2 * gi], ctx->copy_in);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, evs[2 * gi], 0);
+        if (ce != cudaSuccess) break;
+        ret = sigma_launch(ctx, ham, p, ctx->host_c.p + off, ctx->host_s.p + off, k, TBSCI_F64, st);
+        if (ret != TBSCI_OK) break;
+        ce = cudaEventRecord(evs[2 * gi + 1], st);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ctx->copy_out, evs[2 * gi + 1], 0);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(sigma + off, ctx->host_s.p + off, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->copy_out);
+    }
+    // drain every stream this call used before its events are destroyed
+    const cudaError_t s1 = cudaStreamSynchronize(ctx->copy_in), s2 = cudaStreamSynchronize(st),
+                      s3 = cudaStreamSynchronize(ctx->copy_out);
+    cleanup();
+    if (ret != TBSCI_OK) return ret;
+    for (cudaError_t e : {ce, s1, s2, s3})
+        if (e != cudaSuccess) return fail(ctx, TBSCI_ECUDA, std::string("tbsci_sigma_host: ") + cudaGetErrorString(e));
     return TBSCI_OK;
 }
 

@@ -71,8 +71,9 @@ struct tbsci_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
     uint64_t next_id = 1;
-    // device buffers of tbsci_sigma_host
+    // device buffers and copy streams of tbsci_sigma_host (streams created on first use)
     tbsci::DevBuf<double> host_c, host_s;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
     // binomial table C(m, k) for m, k in 0..64, row-major [65][65]
     tbsci::DevBuf<int64_t> d_binom;
 };

@@ -96,6 +96,26 @@ def test_sigma_host_equals_device_and_deterministic(tb, ctx):
     sp.close()
 
 
+def test_sigma_host_pipelined_groups(tb, ctx):
+    """After tuning (at most 4 vectors per launch group), 5 host vectors pass
+    through in several groups with overlapped copies, the last one ragged: the
+    result equals the device evaluation bit for bit, pinned or pageable."""
+    import torch
+    sp, osp, h, eri = _case(tb, ctx, 12, 6, 6, 300, 280, seed=12)
+    C = random_vectors(5, sp.la, sp.lb, seed=13)
+    Cd = torch.from_numpy(C).cuda()
+    out = torch.empty_like(Cd)
+    tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, Cd[:4], out[:4], 4, tb.TBSCI_F64)
+    assert 1 <= sp.counts()["tuned_nv"][0] <= 4
+    want = sp.sigma(Cd).cpu().numpy()
+    assert np.array_equal(sp.sigma_host(C), want)
+    pinned = torch.from_numpy(C).pin_memory()
+    pinned_out = torch.empty_like(pinned).pin_memory()
+    tb.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, pinned.numpy(), pinned_out.numpy(), 5)
+    assert np.array_equal(pinned_out.numpy(), want)
+    sp.close()
+
+
 def test_fci8_sigma(tb, ctx):
     import torch
     wl = WORKLOADS["fci8"]
