@@ -8,7 +8,8 @@ excitation class, a wrong table order) fails at least one of them:
   on tiny spaces (independent of the Slater-Condon rules the oracle uses);
 * closed forms: one-electron systems, N_alpha = N_beta = 1 FCI Hamiltonian
   h x 1 + 1 x h + (ij|kl), one-electron eigenvalue sums;
-* invariants: symmetry, particle-number shift, spin flip, variational order;
+* invariants: symmetry, particle-number shift, spin flip, total spin ([H, S^2] = 0
+  with S^2 built from spin-orbital operators), variational order;
 * paper-printed numbers: Table VI single-link entry counts (Sec. III.C).
 """
 import itertools
@@ -184,6 +185,55 @@ def test_spin_flip_transpose():
     s = oracle.sigma(sp, h, eri, 0.0, C[None]).reshape(sp.la, sp.lb)
     st = oracle.sigma(sp, h, eri, 0.0, C.T.copy()[None]).reshape(sp.la, sp.lb)
     assert np.max(np.abs(st - s.T)) < 1e-12
+
+
+def _s_plus(n, na, nb):
+    """S+ = sum_p a+_{p alpha} a_{p beta} from the full (na, nb) space to the full
+    (na + 1, nb - 1) space, spin orbitals ordered alpha block first, ascending
+    inside each block (the determinant phase convention), determinants indexed
+    alpha-major over ascending integer strings; written from the operator
+    definition, independent of the oracle's Slater-Condon code."""
+    def strings(N):
+        return sorted(sum(1 << i for i in c) for c in itertools.combinations(range(n), N))
+    sa, sb = strings(na), strings(nb)
+    ta, tb = strings(na + 1), strings(nb - 1)
+    ia, ib = {s: i for i, s in enumerate(ta)}, {s: i for i, s in enumerate(tb)}
+    S = np.zeros((len(ta) * len(tb), len(sa) * len(sb)))
+    for w, a in enumerate(sa):
+        for u, b in enumerate(sb):
+            for p in range(n):
+                if not (b >> p) & 1 or (a >> p) & 1:
+                    continue
+                # a_{p beta}: passes all na alpha electrons and the betas below p
+                sign = (-1) ** (na + bin(b & ((1 << p) - 1)).count("1"))
+                # a+_{p alpha}: passes the alphas below p
+                sign *= (-1) ** bin(a & ((1 << p) - 1)).count("1")
+                a2, b2 = a | (1 << p), b & ~(1 << p)
+                S[ia[a2] * len(tb) + ib[b2], w * len(sb) + u] += sign
+    return S
+
+
+@pytest.mark.parametrize("n,na,nb", [(6, 3, 3), (6, 3, 2), (7, 3, 3)])
+def test_hamiltonian_commutes_with_total_spin(n, na, nb):
+    """[H, S^2] = 0 for the oracle's H on full string spaces, and every eigenvector
+    has <S^2> = s(s + 1): an exchange sign, a dropped exchange term or a phase
+    convention that disagrees between the classes breaks spin symmetry."""
+    h, eri, _ = synth_hamiltonian(n, seed=50 + n)
+    sp = oracle.make_space(n, na, nb)
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.0)
+    Sp = _s_plus(n, na, nb)
+    sz = (na - nb) / 2.0
+    S2 = Sp.T @ Sp + (sz * sz + sz) * np.eye(H.shape[0])
+    assert np.max(np.abs(H @ S2 - S2 @ H)) < 1e-11 * np.max(np.abs(H))
+    w, U = np.linalg.eigh(H)
+    gaps = np.diff(w)
+    for k in range(min(12, len(w))):
+        if (k > 0 and gaps[k - 1] < 1e-8) or (k + 1 < len(w) and gaps[k] < 1e-8):
+            continue  # degenerate: any mix of the multiplets is an eigenvector
+        s2 = U[:, k] @ S2 @ U[:, k]
+        s = (-1 + math.sqrt(1 + 4 * s2)) / 2
+        assert abs(s2 - round(2 * s) / 2 * (round(2 * s) / 2 + 1)) < 1e-8, (k, s2)
+        assert round(2 * s) % 2 == (na - nb) % 2 and round(2 * s) >= abs(na - nb)
 
 
 def test_variational_nested_selections():
