@@ -184,6 +184,23 @@ tbsci_status tbsci_sigma_autotune(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_ta
                                   const void *c, void *sigma, int nvec, tbsci_dtype dtype, tbsci_stream stream,
                                   double *best_ms);
 
+/* Autotune cache of the context: launch shapes keyed by the space's shape
+ * (norb, l_alpha, l_beta). tbsci_sigma_autotune records the shape it chooses
+ * (F64 / F32 SIMT shape, or the SIMT pass of the tensor-core types); a space
+ * prepared afterwards on this context with the same shape starts with it, so
+ * same-shaped spaces (another geometry, another Hamiltonian) need no tuning.
+ * save writes the cache as text ("tbsci-tune 1", then one line per shape:
+ * norb l_alpha l_beta, threads / vectors per CTA / shared-memory mode for F64
+ * and for F32, then mode / threads of the tensor-core types' SIMT pass; 0 = not
+ * tuned); load merges such a file into the cache, replacing equal keys, and
+ * applies to spaces prepared after it. Errors: EINVAL (null path, unreadable or
+ * unwritable file, missing header, a malformed or out-of-range line, with its
+ * number in tbsci_last_error; nothing is merged then). Not part of the paper:
+ * tile shapes for this GPU. */
+tbsci_status tbsci_tune_cache_save(tbsci_ctx *ctx, const char *path);
+tbsci_status tbsci_tune_cache_load(tbsci_ctx *ctx, const char *path);
+tbsci_status tbsci_tune_cache_size(tbsci_ctx *ctx, int64_t *entries);
+
 /* Same product with HOST vectors (pinned memory lets the copies overlap): copies
  * c in, evaluates in FP64, copies sigma out and returns when done. The vectors go
  * through in the kernel's launch groups, each group's copies overlapping the
@@ -306,6 +323,9 @@ typedef struct tbsci_server_opts {
     int fuse_sigma;    /* 0 or 1: one batched sigma launch per precision per
                           scheduler round; -1: one launch per solve */
     int fail_admission_at; /* test hook: the n-th admission (1-based) fails with ENOMEM; 0 = off */
+    const char *tune_cache; /* NULL, or a file of tbsci_tune_cache_save loaded into
+                               the server's context: solves of a cached shape that
+                               are launched on their own use its tuned shape */
 } tbsci_server_opts;
 
 typedef struct tbsci_request {

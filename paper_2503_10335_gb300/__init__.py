@@ -124,9 +124,10 @@ class Space:
 class Server:
     """Serving loop (tbsci_server_*): submit solves from any thread, poll results."""
 
-    def __init__(self, device=0, hbm_budget=0, max_active=0, max_queue=0, fuse_sigma=0, fail_admission_at=0):
+    def __init__(self, device=0, hbm_budget=0, max_active=0, max_queue=0, fuse_sigma=0, fail_admission_at=0,
+                 tune_cache=None):
         self.handle = B.tbsci_server_create(device, hbm_budget, max_active, max_queue, fuse_sigma,
-                                            fail_admission_at)
+                                            fail_admission_at, tune_cache)
 
     def submit(self, norb, nalpha, nbeta, h, eri, ecore=0.0, alpha=None, beta=None, nroots=1, mixed=False, **kw):
         st, ticket = B.tbsci_submit(self.handle, norb, nalpha, nbeta, h, eri, ecore, alpha, beta, nroots, mixed, **kw)

@@ -28,7 +28,8 @@ EXPORTS = [
     "tbsci_hamiltonian_create", "tbsci_hamiltonian_destroy", "tbsci_prepare", "tbsci_sigma",
     "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson", "tbsci_overlap",
     "tbsci_overlap_noalloc", "tbsci_server_create", "tbsci_submit", "tbsci_poll", "tbsci_server_load",
-    "tbsci_server_destroy", "tbsci_sigma_autotune",
+    "tbsci_server_destroy", "tbsci_sigma_autotune", "tbsci_tune_cache_save", "tbsci_tune_cache_load",
+    "tbsci_tune_cache_size",
 ]
 
 
@@ -81,7 +82,8 @@ class DavidsonInfo(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int),
-                ("max_queue", ctypes.c_int), ("fuse_sigma", ctypes.c_int), ("fail_admission_at", ctypes.c_int)]
+                ("max_queue", ctypes.c_int), ("fuse_sigma", ctypes.c_int), ("fail_admission_at", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class Request(ctypes.Structure):
@@ -156,6 +158,9 @@ def load(path: str | None = None):
         "tbsci_server_load": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "tbsci_server_destroy": ([P], None),
         "tbsci_sigma_autotune": ([P, P, P, P, P, P, I, I, P, ctypes.POINTER(D)], I),
+        "tbsci_tune_cache_save": ([P, ctypes.c_char_p], I),
+        "tbsci_tune_cache_load": ([P, ctypes.c_char_p], I),
+        "tbsci_tune_cache_size": ([P, ctypes.POINTER(I64)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -295,6 +300,22 @@ def tbsci_sigma_autotune(ctx, ham, ta, tb, c, sigma, nvec: int, dtype: int = TBS
     return ms.value
 
 
+def tbsci_tune_cache_save(ctx, path):
+    """Writes the context's autotune cache (shapes keyed by norb, l_alpha, l_beta) to ``path``."""
+    _check(ctx, load().tbsci_tune_cache_save(ctx, os.fsencode(path)))
+
+
+def tbsci_tune_cache_load(ctx, path):
+    """Merges an autotune cache file into the context; applies to spaces prepared afterwards."""
+    _check(ctx, load().tbsci_tune_cache_load(ctx, os.fsencode(path)))
+
+
+def tbsci_tune_cache_size(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, load().tbsci_tune_cache_size(ctx, ctypes.byref(n)))
+    return n.value
+
+
 def tbsci_sigma_host(ctx, ham, ta, tb, c: np.ndarray, sigma: np.ndarray, nvec: int):
     """sigma <- H c with host FP64 arrays (copies inside the call)."""
     assert c.dtype == np.float64 and sigma.dtype == np.float64
@@ -350,8 +371,10 @@ def tbsci_overlap(ctx, A, B, stream=None) -> np.ndarray:
 
 # ---------------------------------------------------------------- serving
 
-def tbsci_server_create(device=0, hbm_budget=0, max_active=0, max_queue=0, fuse_sigma=0, fail_admission_at=0):
-    o = ServerOpts(device, hbm_budget, max_active, max_queue, fuse_sigma, fail_admission_at)
+def tbsci_server_create(device=0, hbm_budget=0, max_active=0, max_queue=0, fuse_sigma=0, fail_admission_at=0,
+                        tune_cache=None):
+    o = ServerOpts(device, hbm_budget, max_active, max_queue, fuse_sigma, fail_admission_at,
+                   None if tune_cache is None else os.fsencode(tune_cache))
     out = ctypes.c_void_p()
     st = load().tbsci_server_create(ctypes.byref(o), ctypes.byref(out))
     if st != TBSCI_OK:

@@ -1,6 +1,7 @@
 // extern "C" entry points of libtbsci (declared in include/tbsci.h).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -263,7 +264,83 @@ tbsci_status tbsci_sigma_autotune(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_ta
     TB_TRY(plan_get(ctx, ham, a, b, &p));
     if (p->A.l * p->B.l == 0) return TBSCI_OK;
     if (!c || !sigma || c == sigma) return fail(ctx, TBSCI_EINVAL, "bad vector pointers");
-    return sigma_autotune(ctx, ham, p, c, sigma, nvec, dtype, (cudaStream_t)stream, best_ms);
+    TB_TRY(sigma_autotune(ctx, ham, p, c, sigma, nvec, dtype, (cudaStream_t)stream, best_ms));
+    tune_cache_record(ctx, p, p->A.l, p->B.l);
+    return TBSCI_OK;
+}
+
+// Tune cache file: a header line "tbsci-tune 1", then one line per space shape:
+// norb l_alpha l_beta  f64_threads f64_nv f64_stage  f32_threads f32_nv f32_stage
+// rest_mode rest_threads  (nv or threads 0 = not tuned).
+tbsci_status tbsci_tune_cache_save(tbsci_ctx *ctx, const char *path) {
+    TB_GUARD_CTX(ctx);
+    if (!path) return fail(ctx, TBSCI_EINVAL, "null path");
+    std::string text = "tbsci-tune 1\n";
+    {
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        char line[256];
+        for (const auto &kv : ctx->tune_cache) {
+            const auto &e = kv.second;
+            std::snprintf(line, sizeof line, "%lld %lld %lld %d %d %d %d %d %d %d %d\n", (long long)kv.first[0],
+                          (long long)kv.first[1], (long long)kv.first[2], e.threads[0], e.nv[0], e.stage[0],
+                          e.threads[1], e.nv[1], e.stage[1], e.rest_mode, e.rest_threads);
+            text += line;
+        }
+    }
+    FILE *f = std::fopen(path, "w");
+    if (!f) return fail(ctx, TBSCI_EINVAL, std::string("tune cache: cannot write ") + path);
+    const bool ok = std::fwrite(text.data(), 1, text.size(), f) == text.size();
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) return fail(ctx, TBSCI_EINVAL, std::string("tune cache: write failed: ") + path);
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_tune_cache_load(tbsci_ctx *ctx, const char *path) {
+    TB_GUARD_CTX(ctx);
+    if (!path) return fail(ctx, TBSCI_EINVAL, "null path");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return fail(ctx, TBSCI_EINVAL, std::string("tune cache: cannot read ") + path);
+    std::map<std::array<int64_t, 3>, tbsci_ctx::TuneEntry> got;
+    char buf[512];
+    int lineno = 0;
+    std::string bad;
+    auto threads_ok = [](int t) { return t == 0 || t == 128 || t == 256 || t == 512; };
+    while (std::fgets(buf, sizeof buf, f)) {
+        ++lineno;
+        if (lineno == 1) {
+            if (std::strncmp(buf, "tbsci-tune 1", 12) != 0) bad = "missing header";
+            if (!bad.empty()) break;
+            continue;
+        }
+        long long k0, k1, k2;
+        tbsci_ctx::TuneEntry e;
+        const int n = std::sscanf(buf, "%lld %lld %lld %d %d %d %d %d %d %d %d", &k0, &k1, &k2, &e.threads[0],
+                                  &e.nv[0], &e.stage[0], &e.threads[1], &e.nv[1], &e.stage[1], &e.rest_mode,
+                                  &e.rest_threads);
+        bool ok = n == 11 && k0 >= 1 && k0 <= 64 && k1 >= 0 && k2 >= 0 && threads_ok(e.rest_threads) &&
+                  e.rest_mode >= 0 && e.rest_mode <= 2;
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = threads_ok(e.threads[i]) && e.nv[i] >= 0 && e.nv[i] <= 4 && e.stage[i] >= 0 && e.stage[i] <= 2;
+        if (!ok) {
+            bad = "malformed line " + std::to_string(lineno);
+            break;
+        }
+        got[{k0, k1, k2}] = e;
+    }
+    std::fclose(f);
+    if (lineno == 0) bad = "empty file";
+    if (!bad.empty()) return fail(ctx, TBSCI_EINVAL, std::string("tune cache ") + path + ": " + bad);
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    for (const auto &kv : got) ctx->tune_cache[kv.first] = kv.second;
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_tune_cache_size(tbsci_ctx *ctx, int64_t *entries) {
+    TB_GUARD_CTX(ctx);
+    if (!entries) return fail(ctx, TBSCI_EINVAL, "null out");
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    *entries = (int64_t)ctx->tune_cache.size();
+    return TBSCI_OK;
 }
 
 tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,

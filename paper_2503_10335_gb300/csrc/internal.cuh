@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -76,6 +78,14 @@ struct tbsci_ctx {
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
     // binomial table C(m, k) for m, k in 0..64, row-major [65][65]
     tbsci::DevBuf<int64_t> d_binom;
+    // autotuned launch shapes keyed by (norb, l_alpha, l_beta): filled by
+    // tbsci_sigma_autotune and tbsci_tune_cache_load, applied to plans created later
+    struct TuneEntry {
+        int threads[2] = {0, 0}, nv[2] = {0, 0}, stage[2] = {0, 0};  // F64, F32; nv 0 = not tuned
+        int rest_mode = 0, rest_threads = 0;                         // threads 0 = not tuned
+    };
+    std::mutex tune_mu;
+    std::map<std::array<int64_t, 3>, TuneEntry> tune_cache;
 };
 
 struct tbsci_strings {
@@ -206,6 +216,9 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
 // FP32 sigma without the diagonal, alpha singles and alpha-beta classes (the
 // part the tensor-core kernel does not cover); overwrites s.
 // Times every launch shape of the SIMT kernel on (c, s) and keeps the fastest in the plan.
+// copy a plan's tuned shape into the context's cache / a cached shape into a new plan
+void tune_cache_record(tbsci_ctx *ctx, const Plan *plan, int64_t la, int64_t lb);
+void tune_cache_apply(tbsci_ctx *ctx, Plan *plan, int64_t la, int64_t lb);
 tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const void *c, void *s, int nvec,
                             tbsci_dtype dt, cudaStream_t st, double *best_ms);
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,

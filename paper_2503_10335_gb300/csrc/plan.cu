@@ -381,6 +381,7 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
                                plan->A.d_dval.bytes() + plan->B.d_sci.bytes() + plan->B.d_sval.bytes() +
                                plan->B.d_dcol.bytes() + plan->B.d_dval.bytes() + plan->d_U.bytes());
     TB_CUDA(ctx, cudaStreamSynchronize(st));
+    tune_cache_apply(ctx, plan.get(), la, lb);
     *out = plan.get();
     ham->plans.push_back(std::move(plan));
     return TBSCI_OK;

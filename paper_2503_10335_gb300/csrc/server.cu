@@ -309,6 +309,14 @@ tbsci_status tbsci_server_create(const tbsci_server_opts *o, tbsci_server **out)
     if (srv->opts.max_queue <= 0) srv->opts.max_queue = 4096;
     tbsci_status st = tbsci_create(srv->opts.device, &srv->ctx);
     if (st != TBSCI_OK) return st;
+    if (srv->opts.tune_cache) {
+        st = tbsci_tune_cache_load(srv->ctx, srv->opts.tune_cache);
+        if (st != TBSCI_OK) {
+            tbsci_destroy(srv->ctx);
+            return st;
+        }
+    }
+    srv->opts.tune_cache = nullptr;  // the caller's string is not kept
     cudaDeviceGetStreamPriorityRange(&srv->prio_low, &srv->prio_high);
     if (cudaStreamCreateWithPriority(&srv->sstream, cudaStreamNonBlocking, srv->prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&srv->sig_done, cudaEventDisableTiming) != cudaSuccess) {

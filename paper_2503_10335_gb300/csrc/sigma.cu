@@ -564,6 +564,38 @@ tbsci_status sigma_launch_batch(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
     return TBSCI_OK;
 }
 
+void tune_cache_record(tbsci_ctx *ctx, const Plan *plan, int64_t la, int64_t lb) {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    tbsci_ctx::TuneEntry &e = ctx->tune_cache[{plan->norb, la, lb}];
+    for (int i = 0; i < 2; ++i)
+        if (plan->tune_nv[i] > 0) {
+            e.threads[i] = plan->tune_threads[i];
+            e.nv[i] = plan->tune_nv[i];
+            e.stage[i] = plan->tune_stage[i];
+        }
+    if (plan->tune_rest_threads > 0) {
+        e.rest_mode = plan->tune_rest_mode;
+        e.rest_threads = plan->tune_rest_threads;
+    }
+}
+
+void tune_cache_apply(tbsci_ctx *ctx, Plan *plan, int64_t la, int64_t lb) {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    auto it = ctx->tune_cache.find({plan->norb, la, lb});
+    if (it == ctx->tune_cache.end()) return;
+    const tbsci_ctx::TuneEntry &e = it->second;
+    for (int i = 0; i < 2; ++i)
+        if (e.nv[i] > 0) {
+            plan->tune_threads[i] = e.threads[i];
+            plan->tune_nv[i] = e.nv[i];
+            plan->tune_stage[i] = e.stage[i];
+        }
+    if (e.rest_threads > 0) {
+        plan->tune_rest_mode = e.rest_mode;
+        plan->tune_rest_threads = e.rest_threads;
+    }
+}
+
 namespace {
 
 // alpha rows per SM in the autotuner's sample of a large space: several waves of

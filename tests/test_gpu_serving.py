@@ -120,3 +120,23 @@ def test_poll_timeout_queue_limit_and_injected_failure(tb):
         assert st == 0 and d["status"] == 0
     finally:
         srv.close()
+
+
+def test_server_with_tune_cache(tb, tmp_path):
+    """A server created with a tune cache file serves solves as before (the file
+    only changes launch shapes); an unreadable cache file is refused at creation."""
+    with pytest.raises(tb.B.TbsciError):
+        tb.Server(0, tune_cache=str(tmp_path / "missing.txt"))
+    path = tmp_path / "tune.txt"
+    path.write_text("tbsci-tune 1\n8 40 45 128 1 0 256 1 1 0 0\n")
+    reqs = _requests(4, 4)
+    srv = tb.Server(0, tune_cache=str(path))
+    plain = tb.Server(0)
+    try:
+        ra = _solve_all(srv, reqs)
+        rb = _solve_all(plain, reqs)
+    finally:
+        srv.close()
+        plain.close()
+    for x, y in zip(ra, rb):
+        assert np.max(np.abs(np.array(x["energies"]) - np.array(y["energies"]))) < 1e-8

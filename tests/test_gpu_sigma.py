@@ -308,3 +308,49 @@ def test_autotune_on_row_sample_keeps_results_bitwise(tb, ctx):
     del C, out, before
     sp.close()
     torch.cuda.empty_cache()
+
+
+def test_tune_cache_roundtrip(tb, ctx, tmp_path):
+    """A tuned shape is recorded under (norb, l_alpha, l_beta), saved as text, and
+    a same-shaped space with another Hamiltonian on a fresh context that loads
+    the file starts with that shape; sigma there still matches the oracle.
+    Malformed files are rejected whole."""
+    import torch
+    n, na, nb = 12, 6, 6
+    asel, bsel = selected_strings(n, na, 300, 1201), selected_strings(n, nb, 280, 1202)
+    h, eri, _ = synth_hamiltonian(n, seed=1203)
+    sp = tb.Space(ctx, n, na, nb, h, eri, alpha=asel, beta=bsel)
+    C = torch.from_numpy(random_vectors(3, sp.la, sp.lb, seed=1204)).cuda()
+    tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, torch.empty_like(C), 3, tb.TBSCI_F64)
+    tuned = sp.counts()
+    assert tuned["tuned_nv"][0] >= 1 and tb.tbsci_tune_cache_size(ctx.handle) >= 1
+    path = tmp_path / "tune.txt"
+    tb.tbsci_tune_cache_save(ctx.handle, str(path))
+    lines = path.read_text().splitlines()
+    assert lines[0] == "tbsci-tune 1"
+    row = [x for x in lines[1:] if x.split()[:3] == [str(n), str(sp.la), str(sp.lb)]]
+    assert len(row) == 1
+    assert [int(v) for v in row[0].split()[3:6]] == [tuned["tuned_threads"][0], tuned["tuned_nv"][0],
+                                                     tuned["tuned_stage"][0]]
+    ctx2 = tb.Context(0)
+    for bad in ("", "tbsci-tune 1\n12 300 280 512 9 0 0 0 0 0 0\n", "other 1\n", "tbsci-tune 1\n12 300\n"):
+        p = tmp_path / "bad.txt"
+        p.write_text(bad)
+        with pytest.raises(tb.B.TbsciError) as err:
+            tb.tbsci_tune_cache_load(ctx2.handle, str(p))
+        assert err.value.status == tb.TBSCI_EINVAL
+    assert tb.tbsci_tune_cache_size(ctx2.handle) == 0
+    tb.tbsci_tune_cache_load(ctx2.handle, str(path))
+    h2, eri2, _ = synth_hamiltonian(n, seed=1205)
+    sp2 = tb.Space(ctx2, n, na, nb, h2, eri2, 0.3, alpha=asel, beta=bsel)
+    got = sp2.counts()
+    for key in ("tuned_threads", "tuned_nv", "tuned_stage"):
+        assert got[key][0] == tuned[key][0], key
+    osp = oracle.make_space(n, na, nb, asel, bsel)
+    C2 = random_vectors(3, sp2.la, sp2.lb, seed=1206)
+    s2 = sp2.sigma(torch.from_numpy(C2).cuda()).cpu().numpy().reshape(3, -1)
+    ref, bound = oracle.sigma(osp, h2, eri2, 0.3, C2, with_bound=True)
+    assert_sigma_close(s2, ref, bound)
+    sp2.close()
+    ctx2.close()
+    sp.close()
