@@ -229,9 +229,12 @@ typedef struct tbsci_sigma_counts {
     int32_t tuned_stage[2];   /* autotuned shared-memory use for F64 / F32: 0 c row
                                  staged and sigma row accumulated in shared memory
                                  where they fit, 1 sigma row only, 2 neither */
-    int32_t tuned_rest[2];    /* tensor-core types: autotuned shared-memory mode and
-                                 CTA size of the SIMT pass for the classes the
-                                 tensor cores leave out (0, 0 = defaults) */
+    int32_t tuned_rest[2];    /* tensor-core types: autotuned mode and CTA size of
+                                 the SIMT pass for the classes the tensor cores
+                                 leave out (0, 0 = defaults). Modes: 0 c row and
+                                 sigma row in shared memory where they fit, 1 c row
+                                 only, 2 neither, 3 two alpha rows per CTA sharing
+                                 the beta links (even l_alpha; else as 1) */
 } tbsci_sigma_counts;
 tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                                     const tbsci_tables *b, tbsci_sigma_counts *out);

@@ -149,6 +149,7 @@ struct Plan {
     DevBuf<double> d_U1, d_U2, d_Eb2;    // Coulomb table / beta energies with columns in permb / permb2 order
     DevBuf<float> d_U1f, d_U2f, d_Eb2f;
     DevBuf<int32_t> d_rowsa; // alpha rows ordered by work (descending)
+    DevBuf<int32_t> d_pairs; // even l_alpha only: starts 2k of row pairs, heaviest pair first
     // Tensor-core alpha-beta path (norb <= 16): beta single links indexed by
     // (source string Jb, off-diagonal orbital pair r > s): (Ib << 1 | sign<0) or -1,
     // and the map from off-diagonal pair index to the full pair index.

@@ -284,6 +284,18 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
     TB_CUDA(ctx, plan->d_rowsa.alloc(la));
     if (lb > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_permb.p, permb.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (la > 0) TB_CUDA(ctx, cudaMemcpy(plan->d_rowsa.p, rowsa.data(), la * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (la > 0 && la % 2 == 0) {
+        // even alpha row starts of row pairs (2k, 2k + 1), heaviest pair first: the
+        // SIMT pass of the tensor-core sigma types may serve two rows per CTA
+        std::vector<int64_t> pr(la / 2);
+        std::iota(pr.begin(), pr.end(), 0);
+        std::stable_sort(pr.begin(), pr.end(),
+                         [&](int64_t x, int64_t y) { return work[2 * x] + work[2 * x + 1] > work[2 * y] + work[2 * y + 1]; });
+        std::vector<int32_t> starts(la / 2);
+        for (int64_t k = 0; k < la / 2; ++k) starts[k] = (int32_t)(2 * pr[k]);
+        TB_CUDA(ctx, plan->d_pairs.alloc(la / 2));
+        TB_CUDA(ctx, cudaMemcpy(plan->d_pairs.p, starts.data(), (la / 2) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     // sliced-ELL beta links and column-permuted tables
     {
         const int64_t nsl = (lb + 31) / 32;

@@ -66,7 +66,10 @@ struct SigArgs {
 // One alpha row Ia of sigma (the whole body of a CTA). REST: only the classes
 // the tensor-core kernel leaves out (same-spin beta singles and doubles, alpha
 // doubles); the diagonal, alpha singles and every alpha-beta term are skipped.
-template <typename T, int NV, bool STAGE, bool ACCS, int kThreads, bool REST = false>
+// PAIR (with REST, NV = 2, vstride = l_beta): the CTA serves alpha rows Ia and
+// Ia + 1 of one vector; the beta sweep reads each link once for both rows, the
+// alpha-double sweep runs per row. Same summation order per row as NV = 1.
+template <typename T, int NV, bool STAGE, bool ACCS, int kThreads, bool REST = false, bool PAIR = false>
 __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia, unsigned char *smem_raw) {
     const int npair = A.npair;
     const int64_t lb = A.lb, vs = A.vstride;
@@ -228,6 +231,34 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
     }
     __syncthreads();
 
+    if (PAIR) {
+        // ---- alpha doubles of rows Ia and Ia + 1, each from its own link list
+        for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const int64_t row = Ia + v;
+                const int64_t p0 = A.a_doff[row], p1 = A.a_doff[row + 1];
+                T acc = acc_ref(v, j), acc2 = T(0);
+                int64_t t = p0;
+                for (; t + 3 < p1; t += 4) {
+                    const int64_t J0 = __ldg(A.a_dcol + t), J1 = __ldg(A.a_dcol + t + 1);
+                    const int64_t J2 = __ldg(A.a_dcol + t + 2), J3 = __ldg(A.a_dcol + t + 3);
+                    const T x0 = __ldg(A.a_dval + t), x1 = __ldg(A.a_dval + t + 1);
+                    const T x2 = __ldg(A.a_dval + t + 2), x3 = __ldg(A.a_dval + t + 3);
+                    const T c0 = __ldg(C + J0 * lb + j), c1 = __ldg(C + J1 * lb + j);
+                    const T c2 = __ldg(C + J2 * lb + j), c3 = __ldg(C + J3 * lb + j);
+                    acc += x0 * c0;
+                    acc2 += x1 * c1;
+                    acc += x2 * c2;
+                    acc2 += x3 * c3;
+                }
+                for (; t < p1; ++t) acc += __ldg(A.a_dval + t) * __ldg(C + __ldg(A.a_dcol + t) * lb + j);
+                S[row * lb + j] = acc + acc2;
+            }
+        }
+        return;
+    }
+
     // ---- Ja = alpha doubles of Ia, natural column order, c rows read coalesced
     const int64_t u0 = A.a_doff[Ia], u1 = A.a_doff[Ia + 1];
     for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
@@ -268,6 +299,14 @@ template <typename T, int NV, bool STAGE, bool ACCS, int kThreads, bool REST = f
 __global__ void __launch_bounds__(kThreads) k_sigma(SigArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     sigma_row<T, NV, STAGE, ACCS, kThreads, REST>(A, A.rowsa[blockIdx.x], smem_raw);
+}
+
+// SIMT pass of the tensor-core sigma types over row pairs: A.rowsa holds even
+// row starts, A.vstride = l_beta (see sigma_row's PAIR)
+template <bool STAGE, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_sigma_rest_pair(SigArgs<float> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sigma_row<float, 2, STAGE, false, kThreads, true, true>(A, A.rowsa[blockIdx.x], smem_raw);
 }
 
 // One launch over the alpha rows of several jobs (a job = one vector of one
@@ -602,7 +641,7 @@ namespace {
 // CTAs at every CTA size, so tail and occupancy effects match a full launch
 constexpr int kTuneRowsPerSm = 64;
 
-int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode);
+int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode, bool pairs);
 
 // Tensor-core sigma types: the tensor-core kernel has one shape; this times the
 // SIMT pass for the other classes over its shared-memory modes and CTA sizes (on
@@ -631,31 +670,43 @@ tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, con
     };
     float probe = 0.f;
     tbsci_status ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, 0, 0); }, 1, &probe);
-    DevBuf<int32_t> dsample;
-    const int32_t *rows = nullptr;
-    int64_t nrows = 0;
+    // a strided sample of the work-ordered rows (and of the row pairs, for the
+    // pair variants: the same number of rows)
+    DevBuf<int32_t> dsample, dpsample;
+    const int32_t *rows = nullptr, *prows = nullptr;
+    int64_t nrows = 0, nprows = 0;
+    const bool pairs = plan->d_pairs.p != nullptr;
+    auto sample_of = [&](const int32_t *src, int64_t n, int64_t k, DevBuf<int32_t> &dst) -> tbsci_status {
+        std::vector<int32_t> all(n), sample(k);
+        cudaError_t e = cudaMemcpy(all.data(), src, n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        for (int64_t j = 0; j < k; ++j) sample[j] = all[(j * n) / k];
+        if (e == cudaSuccess) e = dst.alloc(k);
+        if (e == cudaSuccess) e = cudaMemcpy(dst.p, sample.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? TBSCI_OK : fail(ctx, TBSCI_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    };
     if (ret == TBSCI_OK && probe >= 100.f) {
         nrows = std::min<int64_t>(la, kTuneRowsPerSm * (int64_t)ctx->num_sms);
-        std::vector<int32_t> all(la), sample(nrows);
-        cudaError_t e = cudaMemcpy(all.data(), plan->d_rowsa.p, la * sizeof(int32_t), cudaMemcpyDeviceToHost);
-        for (int64_t j = 0; j < nrows; ++j) sample[j] = all[(j * la) / nrows];
-        if (e == cudaSuccess) e = dsample.alloc(nrows);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(dsample.p, sample.data(), nrows * sizeof(int32_t), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) ret = fail(ctx, TBSCI_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        ret = sample_of(plan->d_rowsa.p, la, nrows, dsample);
         rows = dsample.p;
+        if (ret == TBSCI_OK && pairs) {
+            nprows = std::max<int64_t>(1, nrows / 2);
+            ret = sample_of(plan->d_pairs.p, la / 2, nprows, dpsample);
+            prows = dpsample.p;
+        }
     }
     const int threads[3] = {128, 256, 512};
     float best = 1e30f;
     int bm = 0, bt = 0;
-    bool seen[4] = {false, false, false, false};
-    for (int mode = 0; mode < 3 && ret == TBSCI_OK; ++mode) {
-        const int var = rest_variant(ctx, npair, lb, mode);
+    bool seen[6] = {false, false, false, false, false, false};
+    for (int mode = 0; mode < 4 && ret == TBSCI_OK; ++mode) {
+        const int var = rest_variant(ctx, npair, lb, mode, pairs);
         if (seen[var]) continue;
         seen[var] = true;
+        const int32_t *r = var >= 4 ? prows : rows;
+        const int64_t nr = var >= 4 ? nprows : nrows;
         for (int t = 0; t < 3 && ret == TBSCI_OK; ++t) {
             float ms = 0.f;
-            ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, mode, threads[t], rows, nrows); },
+            ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, mode, threads[t], r, nr); },
                         rows ? 1 : 2, &ms);
             if (ret == TBSCI_OK && ms < best) {
                 best = ms;
@@ -808,6 +859,23 @@ tbsci_status launch_rest_th(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_
     return TBSCI_OK;
 }
 
+template <bool STAGE, int TH>
+tbsci_status launch_rest_pair_th(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t st) {
+    const size_t sm = smem_bytes<float>(A.npair, A.lb, 2, STAGE, false);
+    auto k = k_sigma_rest_pair<STAGE, TH>;
+    TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k<<<(unsigned)A.la, TH, sm, st>>>(A);
+    TB_CUDA(ctx, cudaGetLastError());
+    return TBSCI_OK;
+}
+
+template <bool STAGE>
+tbsci_status launch_rest_pair(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t st, int threads) {
+    if (threads == 512) return launch_rest_pair_th<STAGE, 512>(ctx, A, st);
+    if (threads == 256) return launch_rest_pair_th<STAGE, 256>(ctx, A, st);
+    return launch_rest_pair_th<STAGE, 128>(ctx, A, st);
+}
+
 template <bool STAGE, bool ACCS>
 tbsci_status launch_rest_v(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t st, int threads) {
     if (threads == 512) return launch_rest_th<STAGE, ACCS, 512>(ctx, A, st);
@@ -818,10 +886,14 @@ tbsci_status launch_rest_v(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t
 // Variant of the SIMT pass for a shared-memory mode: 0 = c row staged and sigma
 // row accumulated in shared memory where both fit (else the sigma row only, else
 // neither); 1 = c row only (the pass writes each sigma element once and reads it
-// once, so a global accumulator costs little and frees shared memory); 2 = neither.
-// Returns 0 (c + sigma), 1 (sigma only), 2 (c only) or 3 (neither).
-int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode) {
+// once, so a global accumulator costs little and frees shared memory); 2 = neither;
+// 3 = two alpha rows per CTA sharing the beta links, their c rows staged where
+// they fit (even l_alpha only, else as mode 1). Returns 0 (c + sigma), 1 (sigma
+// only), 2 (c only), 3 (neither), 4 (row pairs, c staged) or 5 (row pairs).
+int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode, bool pairs) {
     const size_t lim = ctx->smem_optin;
+    if (mode == 3 && pairs) return smem_bytes<float>(npair, lb, 2, true, false) <= lim ? 4 : 5;
+    if (mode == 3) mode = 1;
     if (mode == 0) {
         if (smem_bytes<float>(npair, lb, 1, true, true) <= lim) return 0;
         if (smem_bytes<float>(npair, lb, 1, false, true) <= lim) return 1;
@@ -836,7 +908,8 @@ int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode) {
 // The classes the tensor-core kernel leaves out (same-spin beta singles and
 // doubles, alpha doubles), FP32, one launch per vector. mode / threads: -1 / 0 =
 // the plan's tuned choice (default: mode 0, 512 threads on rows of >= 1024
-// columns, else 128); rows / nrows: launch only these alpha rows (tuning sample).
+// columns, else 128); rows / nrows: launch only these alpha rows (tuning sample;
+// for the row-pair variants: these even pair starts).
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
                                int nvec, cudaStream_t st, int mode, int threads, const int32_t *rows, int64_t nrows) {
     SigArgs<float> A = make_args<float>(ham, plan);
@@ -846,11 +919,25 @@ tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan 
         threads = plan->tune_rest_threads;
     }
     if (threads == 0) threads = A.lb >= 1024 ? 512 : 128;
+    const int var = rest_variant(ctx, A.npair, A.lb, mode, plan->d_pairs.p != nullptr);
+    if (var >= 4) {
+        // row pairs: one vector per launch with vstride = l_beta, pair starts as rows
+        SigArgs<float> P = A;
+        P.vstride = A.lb;
+        P.rowsa = rows ? rows : plan->d_pairs.p;
+        P.la = rows ? nrows : A.la / 2;
+        for (int v = 0; v < nvec; ++v) {
+            P.C = c + (size_t)v * A.vstride;
+            P.S = s + (size_t)v * A.vstride;
+            if (var == 4) TB_TRY(launch_rest_pair<true>(ctx, P, st, threads));
+            else TB_TRY(launch_rest_pair<false>(ctx, P, st, threads));
+        }
+        return TBSCI_OK;
+    }
     if (rows) {
         A.rowsa = rows;
         A.la = nrows;
     }
-    const int var = rest_variant(ctx, A.npair, A.lb, mode);
     for (int v = 0; v < nvec; ++v) {
         A.C = c + (size_t)v * A.vstride;
         A.S = s + (size_t)v * A.vstride;

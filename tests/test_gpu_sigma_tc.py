@@ -110,3 +110,30 @@ def test_tc_sigma_parity_after_autotune(tb, ctx, mode, n, na, nb, acnt, bcnt):
     for s in (out, sp.sigma(Ct, dtype=dt)):
         assert_sigma_close(s.double().cpu().numpy().reshape(1, -1), ref, bound, rel=rel, norm_rel=norm_rel)
     sp.close()
+
+
+@pytest.mark.parametrize("rest_mode,threads", [(3, 512), (3, 128), (1, 256), (2, 512)])
+@pytest.mark.parametrize("n,na,nb,acnt,bcnt", [(10, 5, 5, 120, 257), (12, 4, 6, None, 200), (16, 8, 8, 700, 650)])
+def test_tc_sigma_rest_modes_from_tune_cache(tb, n, na, nb, acnt, bcnt, rest_mode, threads, tmp_path):
+    """Every shared-memory mode of the SIMT pass, pinned through a tune cache file
+    loaded into a fresh context: mode 3 serves two alpha rows per CTA when l_alpha
+    is even (120, 700) and falls back to mode 1 when it is odd (495); sigma
+    matches the oracle in each."""
+    import torch
+    h, eri, _ = synth_hamiltonian(n, seed=300 + n)
+    asel = None if acnt is None else selected_strings(n, na, acnt, 31 + n)
+    bsel = None if bcnt is None else selected_strings(n, nb, bcnt, 37 + n)
+    osp = oracle.make_space(n, na, nb, asel, bsel)
+    path = tmp_path / "tune.txt"
+    path.write_text("tbsci-tune 1\n%d %d %d 0 0 0 0 0 0 %d %d\n" % (n, osp.la, osp.lb, rest_mode, threads))
+    ctx = tb.Context(0)
+    tb.tbsci_tune_cache_load(ctx.handle, str(path))
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.2, alpha=asel, beta=bsel)
+    assert sp.counts()["tuned_rest"] == [rest_mode, threads]
+    C = random_vectors(2, sp.la, sp.lb, seed=n + 1).astype(np.float32)
+    s = sp.sigma(torch.from_numpy(C).cuda(), dtype=tb.TBSCI_F32_TC_TF32).double().cpu().numpy().reshape(2, -1)
+    ref, bound = oracle.sigma(osp, h, eri, 0.2, C.astype(np.float64), with_bound=True)
+    rel, norm_rel = TOL["tf32"]
+    assert_sigma_close(s, ref, bound, rel=rel, norm_rel=norm_rel)
+    sp.close()
+    ctx.close()
