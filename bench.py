@@ -54,8 +54,8 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FM
 # the kernel source it was taken on: a changed kernel reports null until
 # re-captured (profiles/k_sigma_f64_sel16.md).
 NCU_TRAFFIC = {
-    # tuned shape (512 threads, 2 + 1 vectors per CTA): 6.834 GB + 1.559 GB per 3-vector step
-    "f64": {"sha1": "ac92dfba77b64044e2c81f455e3726490d658570", "bytes": (6.834e9 + 1.559e9) / 2},
+    # tuned shape (512 threads, 2 + 1 vectors per CTA): 7.439 GB + 1.998 GB per 3-vector step
+    "f64": {"sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2", "bytes": (7.439e9 + 1.998e9) / 2},
 }
 
 
