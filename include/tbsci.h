@@ -205,8 +205,8 @@ tbsci_status tbsci_tune_cache_size(tbsci_ctx *ctx, int64_t *entries);
  * c in, evaluates in FP64, copies sigma out and returns when done. The vectors go
  * through in the kernel's launch groups, each group's copies overlapping the
  * evaluation of its neighbours (two copy streams of the context); the result is
- * the same as one evaluation of all vectors. Uses device buffers owned by the
- * context. */
+ * the same as one evaluation of all vectors. Uses device buffers and streams
+ * owned by the context, so calls on one context must not overlap. */
 tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                               const tbsci_tables *b, const double *c, double *sigma, int nvec);
 
