@@ -200,7 +200,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(wl, nvec, "f64"),
+        "config": dict(_config(wl, nvec, "f64"), parallelism="replicas" if ws > 1 else "single"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                          "sample": "%d seeded determinant rows per step of %d, %d vectors" %
                                    (rows_per_step, sp.ndet, nvec)},
