@@ -1,0 +1,47 @@
+"""Host logic of bench.py (no GPU): clock-sample summaries and throttle reasons,
+the traffic record's source-hash gate, replica throughput."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_clock_summary(bench):
+    lines = [
+        "0, 2070, 2070, 700.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1399.9, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 10, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = bench.ClockSampler.summarize(lines)
+    assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = bench.ClockSampler.summarize([
+        "0, 1500, 2070, 1400, 0x48, Active, Not Active, Active, Not Active"])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler.summarize(["garbage"]) is None
+    assert bench.ClockSampler.summarize([]) is None
+
+
+def test_traffic_only_for_the_profiled_kernel_source(bench, monkeypatch):
+    rec = bench.NCU_TRAFFIC["f64"]
+    monkeypatch.setattr(bench, "_kernel_hash", lambda: rec["sha1"])
+    assert bench._traffic("f64") == rec["bytes"]
+    monkeypatch.setattr(bench, "_kernel_hash", lambda: "0" * 40)
+    assert bench._traffic("f64") is None
+    assert bench._traffic("bf16tc") is None
+
+
+def test_replica_throughput_and_single_rank_max(bench):
+    assert bench.replica_throughput(2, 9e6, 0.5) == pytest.approx(3.6e7)
+    assert bench.max_over_ranks(1.25) == 1.25
