@@ -45,3 +45,25 @@ def test_traffic_only_for_the_profiled_kernel_source(bench, monkeypatch):
 def test_replica_throughput_and_single_rank_max(bench):
     assert bench.replica_throughput(2, 9e6, 0.5) == pytest.approx(3.6e7)
     assert bench.max_over_ranks(1.25) == 1.25
+
+
+def test_clock_sampler_start_stop_with_a_stand_in_tool(bench, tmp_path, monkeypatch):
+    """The sampler's process handling end to end: a stand-in `nvidia-smi` on PATH
+    prints three samples and waits; stop() terminates it and summarises."""
+    tool = tmp_path / "nvidia-smi"
+    tool.write_text("#!/bin/sh\n"
+                    "echo '0, 2070, 2070, 600, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2040, 2070, 900, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 2070, 2070, 950, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    tool.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    import time
+    s = bench.ClockSampler(0)
+    s.start()
+    deadline = time.time() + 10
+    while len(s.lines) < 3 and time.time() < deadline:
+        time.sleep(0.05)
+    out = s.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert s.proc.poll() is not None  # the tool was terminated
