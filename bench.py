@@ -53,9 +53,16 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FM
 # from an ncu capture of the default workload, keyed by dtype, with the sha1 of
 # the kernel source it was taken on: a changed kernel reports null until
 # re-captured (profiles/k_sigma_f64_sel16.md).
+# DRAM bytes (read + write) per launch of the sigma kernel by launch shape
+# (threads, vectors per CTA, shared-memory mode), from one ncu capture of the kernel
+# source with this sha1 (the shape-by-shape table is in the profile of k_sigma FP64 at
+# sel16); a shape or source not captured reports null
 NCU_TRAFFIC = {
-    # tuned shape (512 threads, 2 + 1 vectors per CTA): 7.439 GB + 1.998 GB per 3-vector step
-    "f64": {"sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2", "bytes": (7.439e9 + 1.998e9) / 2},
+    "f64": {"sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2",
+            "shapes": {(512, 1, 0): 1.998e9, (512, 2, 0): 7.439e9, (512, 3, 0): 12.643e9,
+                       (256, 1, 0): 1.356e9, (128, 1, 0): 0.803e9,
+                       (512, 1, 1): 1.233e9, (256, 1, 1): 0.811e9, (128, 1, 1): 1.558e9,
+                       (512, 1, 2): 2.049e9, (256, 1, 2): 1.496e9, (128, 1, 2): 3.683e9}},
 }
 
 
@@ -65,11 +72,17 @@ def _kernel_hash():
         return hashlib.sha1(f.read()).hexdigest()
 
 
-def _traffic(dtype):
+def _traffic(dtype, threads, nv, stage, nvec):
+    """Average DRAM bytes per launch of one step: nvec vectors in launch groups of
+    nv (the last one smaller) at the tuned threads and shared-memory mode."""
     rec = NCU_TRAFFIC.get(dtype)
-    if rec and rec["sha1"] == _kernel_hash():
-        return rec["bytes"]
-    return None
+    if not rec or rec["sha1"] != _kernel_hash() or nv < 1:
+        return None
+    groups = [min(nv, nvec - v) for v in range(0, nvec, nv)]
+    try:
+        return sum(rec["shapes"][(threads, g, stage)] for g in groups) / len(groups)
+    except KeyError:
+        return None
 
 
 def _dist():
@@ -457,7 +470,9 @@ def main():
     achieved = flops_step / launches_per_step / (kern_ms * 1e-3) / 1e12
     peak = FP64_NOMINAL_TFLOPS if args.dtype == "f64" else FP32_NOMINAL_TFLOPS
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic(args.dtype), "kernel": "k_sigma (fused, all classes)",
+                "traffic": (_traffic(args.dtype, counts["tuned_threads"][0], counts["tuned_nv"][0],
+                                     counts["tuned_stage"][0], nvec) if args.dtype == "f64" else None),
+                "kernel": "k_sigma (fused, all classes)",
                 "peak_source": "nominal %s ALU (152 SMs, 2070 MHz)" % ("FP64" if args.dtype == "f64" else "FP32"),
                 "algorithmic_flops_per_launch": flops_step / launches_per_step}
 
