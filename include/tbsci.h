@@ -91,9 +91,30 @@ typedef struct tbsci_double_link {
 
 /* ------------------------------------------------------------- context */
 
-/* Creates a context on CUDA device `device` (made current for the calls of this
- * context). Errors: EINVAL (bad device), ECUDA. */
+/* Options of a context (tbsci_create_ex). */
+typedef struct tbsci_options {
+    int device;             /* CUDA device (made current for the calls of this context) */
+    size_t hbm_budget;      /* device bytes the context's objects may hold: string sets,
+                               link tables, prepared spaces, Davidson vectors and the
+                               buffers of tbsci_sigma_host; a call whose objects would
+                               exceed it frees what it made and returns ENOMEM.
+                               0 = no limit */
+    int default_mixed;      /* mixed mode of tbsci_davidson when its opts is NULL
+                               (0..3, as tbsci_davidson_opts.mixed) */
+    const char *tune_cache; /* NULL, or a tune-cache file (tbsci_tune_cache_save format):
+                               loaded at creation when it exists, written back by
+                               tbsci_destroy; the path is copied */
+} tbsci_options;
+
+/* Creates a context from options (NULL = device 0, no budget, FP64 Davidson, no
+ * tune-cache file). Errors: EINVAL (bad device, default_mixed outside 0..3, an
+ * existing tune-cache file that does not parse), ENOMEM, ECUDA. The paper has no
+ * counterpart: the settings of one GPU process. */
+tbsci_status tbsci_create_ex(const tbsci_options *opts, tbsci_ctx **out);
+/* tbsci_create_ex with only the device set. Errors: EINVAL (bad device), ECUDA. */
 tbsci_status tbsci_create(int device, tbsci_ctx **out);
+/* Device bytes the context's live objects hold against its budget. */
+tbsci_status tbsci_hbm_used(const tbsci_ctx *ctx, size_t *bytes);
 void tbsci_destroy(tbsci_ctx *ctx);
 /* Last error message of this context ("" when none). Valid until the next call. */
 const char *tbsci_last_error(const tbsci_ctx *ctx);
@@ -282,6 +303,11 @@ typedef struct tbsci_davidson_info {
     double seconds_total;
     double seconds_sigma;     /* device time of all sigma evaluations (blocking call) */
     double seconds_sigma_f32; /* of which the low-precision phase's */
+    int precision;            /* sigma type of the low-precision phase (a tbsci_dtype);
+                                 TBSCI_F64 when the solve ran in FP64 throughout */
+    double refine_delta[8];   /* mixed mode: final FP64-refined energy minus the energy
+                                 at the end of the low-precision phase, per root
+                                 (the low-precision phase's energy error); 0 otherwise */
 } tbsci_davidson_info;
 
 /* Lowest nroots (1..8) eigenpairs of H on a x b by standard Davidson (Sec. III.A)
@@ -298,6 +324,7 @@ typedef struct tbsci_davidson_info {
  * (theta - H_KK)^-1 (|denominator| clamped at 1e-8), orthonormalise twice
  * against the basis (FP64 Gram-Schmidt) and add. energies: HOST array
  * [nroots]. vecs: DEVICE array [nroots][l_a][l_b] FP64 or NULL.
+ * opts == NULL: defaults, with the context's default_mixed mode.
  * Errors: EINVAL, ENOMEM, ECUDA; ENOCONV when max_iter is reached (energies
  * and vecs hold the last estimates). Blocks until done. */
 tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
@@ -341,7 +368,10 @@ typedef struct tbsci_request {
     const uint64_t *beta;  /* HOST selected beta strings or NULL (full space) */
     int64_t n_beta;
     int nroots;            /* 1..8 */
-    int mixed;             /* 1: FP32 sigma then FP64 refinement; 0: FP64 throughout */
+    int mixed;             /* 0: FP64 throughout; 1, 2, 3: FP32, FP32 + split-TF32
+                              tensor-core or FP32 + BF16 tensor-core sigma, then FP64
+                              refinement (the mixed modes of tbsci_davidson_opts);
+                              other values: EINVAL */
     double tol_energy, tol_residual; /* 0 -> the tbsci_davidson defaults */
     int max_iter;          /* 0 -> 1000 */
 } tbsci_request;
@@ -400,8 +430,10 @@ tbsci_status tbsci_overlap(tbsci_ctx *ctx, const double *A, int ma, const double
  * other host threads) race and must be serialised by the caller.
  * The first call on each device resolves the array's device address (and may
  * load the library's device code); make that first call during set-up, before
- * any stream capture. No call allocates: no cudaMalloc, cudaFree or allocating
- * library routine. Errors: EINVAL, ECUDA. */
+ * any stream capture. That address is kept for the rest of the process: after
+ * a cudaDeviceReset of the device it is stale, so a process that resets a
+ * device must not call this entry point on it again. No call allocates: no
+ * cudaMalloc, cudaFree or allocating library routine. Errors: EINVAL, ECUDA. */
 tbsci_status tbsci_overlap_noalloc(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n,
                                    double *S, tbsci_stream stream);
 

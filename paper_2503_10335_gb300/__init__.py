@@ -23,8 +23,11 @@ __all__ = ["Context", "Space", "Server", "B"] + [n for n in dir(B) if n.startswi
 class Context:
     """A libtbsci context on one CUDA device."""
 
-    def __init__(self, device: int = 0):
-        self.handle = B.tbsci_create(device)
+    def __init__(self, device: int = 0, hbm_budget: int = 0, default_mixed: int = 0, tune_cache=None):
+        if hbm_budget or default_mixed or tune_cache is not None:
+            self.handle = B.tbsci_create_ex(device, hbm_budget, default_mixed, tune_cache)
+        else:
+            self.handle = B.tbsci_create(device)
         self.device = device
 
     def close(self):
@@ -50,6 +53,13 @@ class Space:
         c = ctx.handle
         self.norb, self.nalpha, self.nbeta = int(norb), int(nalpha), int(nbeta)
         self._handles = []
+        try:
+            self._build(c, norb, nalpha, nbeta, h, eri, ecore, alpha, beta, prepare)
+        except Exception:
+            self.close()  # frees what was made before the failing call
+            raise
+
+    def _build(self, c, norb, nalpha, nbeta, h, eri, ecore, alpha, beta, prepare):
         self.sa = B.tbsci_build_strings(c, norb, nalpha, alpha)
         self._handles.append((B.tbsci_strings_destroy, self.sa))
         self.sb = B.tbsci_build_strings(c, norb, nbeta, beta)

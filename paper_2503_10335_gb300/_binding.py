@@ -29,7 +29,7 @@ EXPORTS = [
     "tbsci_sigma_host", "tbsci_diagonal", "tbsci_sigma_counts_get", "tbsci_davidson", "tbsci_overlap",
     "tbsci_overlap_noalloc", "tbsci_server_create", "tbsci_submit", "tbsci_poll", "tbsci_server_load",
     "tbsci_server_destroy", "tbsci_sigma_autotune", "tbsci_tune_cache_save", "tbsci_tune_cache_load",
-    "tbsci_tune_cache_size",
+    "tbsci_tune_cache_size", "tbsci_create_ex", "tbsci_hbm_used",
 ]
 
 
@@ -70,14 +70,21 @@ class DavidsonInfo(ctypes.Structure):
                 ("nsigma_f32", ctypes.c_int), ("iterations_f32", ctypes.c_int),
                 ("residual", ctypes.c_double * 8), ("energy_f32", ctypes.c_double * 8),
                 ("seconds_total", ctypes.c_double), ("seconds_sigma", ctypes.c_double),
-                ("seconds_sigma_f32", ctypes.c_double)]
+                ("seconds_sigma_f32", ctypes.c_double), ("precision", ctypes.c_int),
+                ("refine_delta", ctypes.c_double * 8)]
 
     def as_dict(self):
         return dict(iterations=self.iterations, converged=bool(self.converged), nsigma=self.nsigma,
                     nsigma_f32=self.nsigma_f32, iterations_f32=self.iterations_f32,
                     residual=list(self.residual), energy_f32=list(self.energy_f32),
                     seconds_total=self.seconds_total, seconds_sigma=self.seconds_sigma,
-                    seconds_sigma_f32=self.seconds_sigma_f32)
+                    seconds_sigma_f32=self.seconds_sigma_f32, precision=self.precision,
+                    refine_delta=list(self.refine_delta))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("default_mixed", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -131,6 +138,8 @@ def load(path: str | None = None):
     PP = ctypes.POINTER(ctypes.c_void_p)
     sig = {
         "tbsci_create": ([I, PP], I),
+        "tbsci_create_ex": ([ctypes.POINTER(Options), PP], I),
+        "tbsci_hbm_used": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
         "tbsci_destroy": ([P], None),
         "tbsci_last_error": ([P], ctypes.c_char_p),
         "tbsci_status_string": ([I], ctypes.c_char_p),
@@ -202,6 +211,21 @@ def tbsci_create(device: int = 0):
     if st != TBSCI_OK:
         raise TbsciError(st, "tbsci_create(%d) failed" % device)
     return h
+
+
+def tbsci_create_ex(device: int = 0, hbm_budget: int = 0, default_mixed: int = 0, tune_cache=None):
+    o = Options(device, hbm_budget, default_mixed, None if tune_cache is None else os.fsencode(tune_cache))
+    h = ctypes.c_void_p()
+    st = load().tbsci_create_ex(ctypes.byref(o), ctypes.byref(h))
+    if st != TBSCI_OK:
+        raise TbsciError(st, "tbsci_create_ex(device %d) failed" % device)
+    return h
+
+
+def tbsci_hbm_used(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, load().tbsci_hbm_used(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def tbsci_destroy(ctx):
@@ -384,7 +408,9 @@ def tbsci_server_create(device=0, hbm_budget=0, max_active=0, max_queue=0, fuse_
 
 def tbsci_submit(srv, norb, nalpha, nbeta, h, eri, ecore=0.0, alpha=None, beta=None, nroots=1, mixed=False,
                  tol_energy=0.0, tol_residual=0.0, max_iter=0):
-    """Queues one solve; returns ``(status, ticket)`` (status EAGAIN when the queue is full)."""
+    """Queues one solve; returns ``(status, ticket)`` (status EAGAIN when the queue is full).
+    ``mixed``: False / 0 FP64, True / 1 FP32 sigma, 2 split-TF32 and 3 BF16
+    tensor-core sigma, each then FP64 refinement."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     eri = np.ascontiguousarray(eri, dtype=np.float64)
     a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.uint64)
@@ -392,7 +418,7 @@ def tbsci_submit(srv, norb, nalpha, nbeta, h, eri, ecore=0.0, alpha=None, beta=N
     r = Request(norb, nalpha, nbeta, h.ctypes.data, eri.ctypes.data, float(ecore),
                 None if a is None else a.ctypes.data, 0 if a is None else len(a),
                 None if b is None else b.ctypes.data, 0 if b is None else len(b),
-                nroots, 1 if mixed else 0, tol_energy, tol_residual, max_iter)
+                nroots, int(mixed), tol_energy, tol_residual, max_iter)
     t = ctypes.c_uint64()
     st = load().tbsci_submit(srv, ctypes.byref(r), ctypes.byref(t))
     return st, t.value

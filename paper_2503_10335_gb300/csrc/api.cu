@@ -15,6 +15,22 @@ tbsci_status fail(tbsci_ctx *ctx, tbsci_status st, const std::string &msg) {
     return st;
 }
 
+tbsci_status charge(tbsci_ctx *ctx, size_t bytes, const char *what) {
+    if (!ctx || bytes == 0) return TBSCI_OK;
+    size_t cur = ctx->hbm_used.load();
+    for (;;) {
+        if (ctx->hbm_budget && cur + bytes > ctx->hbm_budget)
+            return fail(ctx, TBSCI_ENOMEM,
+                        std::string(what) + ": " + std::to_string(bytes) + " device bytes would exceed the context's "
+                        "budget (" + std::to_string(cur) + " of " + std::to_string(ctx->hbm_budget) + " in use)");
+        if (ctx->hbm_used.compare_exchange_weak(cur, cur + bytes)) return TBSCI_OK;
+    }
+}
+
+void uncharge(tbsci_ctx *ctx, size_t bytes) {
+    if (ctx && bytes) ctx->hbm_used.fetch_sub(std::min(bytes, ctx->hbm_used.load()));
+}
+
 }  // namespace tbsci
 
 using namespace tbsci;
@@ -43,14 +59,21 @@ const char *tbsci_status_string(tbsci_status st) {
     return "unknown status";
 }
 
-tbsci_status tbsci_create(int device, tbsci_ctx **out) {
+tbsci_status tbsci_create_ex(const tbsci_options *opts, tbsci_ctx **out) {
     if (!out) return TBSCI_EINVAL;
     *out = nullptr;
+    tbsci_options o{};
+    if (opts) o = *opts;
+    if (o.default_mixed < 0 || o.default_mixed > 3) return TBSCI_EINVAL;
+    const int device = o.device;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return TBSCI_EINVAL;
     tbsci_ctx *ctx = new (std::nothrow) tbsci_ctx();
     if (!ctx) return TBSCI_ENOMEM;
     ctx->device = device;
+    ctx->hbm_budget = o.hbm_budget;
+    ctx->default_mixed = o.default_mixed;
+    if (o.tune_cache) ctx->tune_path = o.tune_cache;
     auto bad = [&](cudaError_t e) {
         if (e == cudaSuccess) return false;
         delete ctx;
@@ -70,7 +93,30 @@ tbsci_status tbsci_create(int device, tbsci_ctx **out) {
     }
     if (bad(ctx->d_binom.alloc(B.size()))) return TBSCI_ENOMEM;
     if (bad(cudaMemcpy(ctx->d_binom.p, B.data(), B.size() * sizeof(int64_t), cudaMemcpyHostToDevice))) return TBSCI_ECUDA;
+    if (!ctx->tune_path.empty()) {
+        FILE *f = std::fopen(ctx->tune_path.c_str(), "r");
+        if (f) {
+            std::fclose(f);
+            if (tbsci_tune_cache_load(ctx, ctx->tune_path.c_str()) != TBSCI_OK) {
+                ctx->tune_path.clear();  // not written back on destroy
+                tbsci_destroy(ctx);
+                return TBSCI_EINVAL;
+            }
+        }
+    }
     *out = ctx;
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_create(int device, tbsci_ctx **out) {
+    tbsci_options o{};
+    o.device = device;
+    return tbsci_create_ex(&o, out);
+}
+
+tbsci_status tbsci_hbm_used(const tbsci_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return TBSCI_EINVAL;
+    *bytes = ctx->hbm_used.load();
     return TBSCI_OK;
 }
 
@@ -79,6 +125,7 @@ void tbsci_destroy(tbsci_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->copy_out) cudaStreamSynchronize(ctx->copy_out);
+    if (!ctx->tune_path.empty()) tbsci_tune_cache_save(ctx, ctx->tune_path.c_str());
     ctx->host_c.release();
     ctx->host_s.release();
     ctx->d_binom.release();
@@ -98,10 +145,12 @@ tbsci_status tbsci_build_strings(tbsci_ctx *ctx, int norb, int nelec, const uint
     tbsci_strings *s = new (std::nothrow) tbsci_strings();
     if (!s) return fail(ctx, TBSCI_ENOMEM, "host allocation failed");
     tbsci_status st = strings_build(ctx, norb, nelec, selected, nsel, s);
+    if (st == TBSCI_OK) st = charge(ctx, s->d_str.bytes(), "string set");
     if (st != TBSCI_OK) {
         delete s;
         return st;
     }
+    s->charged = s->d_str.bytes();
     *out = s;
     return TBSCI_OK;
 }
@@ -122,6 +171,7 @@ tbsci_status tbsci_strings_export(tbsci_ctx *ctx, const tbsci_strings *s, uint64
 void tbsci_strings_destroy(tbsci_strings *s) {
     if (!s) return;
     if (s->ctx) cudaSetDevice(s->ctx->device);
+    uncharge(s->ctx, s->charged);
     delete s;
 }
 
@@ -133,10 +183,14 @@ tbsci_status tbsci_build_excitation_tables(tbsci_ctx *ctx, const tbsci_strings *
     if (!t) return fail(ctx, TBSCI_ENOMEM, "host allocation failed");
     t->id = ctx->next_id++;
     tbsci_status st = tables_build(ctx, s, flags, t);
+    const size_t bytes = t->d_str.bytes() + t->d_off1.bytes() + t->d_off2.bytes() + t->d_ent1.bytes() +
+                         t->d_ent2.bytes();
+    if (st == TBSCI_OK) st = charge(ctx, bytes, "excitation tables");
     if (st != TBSCI_OK) {
         delete t;
         return st;
     }
+    t->charged = bytes;
     *out = t;
     return TBSCI_OK;
 }
@@ -169,6 +223,7 @@ tbsci_status tbsci_tables_export(tbsci_ctx *ctx, const tbsci_tables *t, int64_t 
 void tbsci_tables_destroy(tbsci_tables *t) {
     if (!t) return;
     if (t->ctx) cudaSetDevice(t->ctx->device);
+    uncharge(t->ctx, t->charged);
     delete t;
 }
 
@@ -234,6 +289,7 @@ tbsci_status tbsci_hamiltonian_create(tbsci_ctx *ctx, int norb, const double *h,
 void tbsci_hamiltonian_destroy(tbsci_ham *ham) {
     if (!ham) return;
     if (ham->ctx) cudaSetDevice(ham->ctx->device);
+    for (auto &p : ham->plans) uncharge(ham->ctx, p->charged);
     delete ham;
 }
 
@@ -352,9 +408,20 @@ tbsci_status tbsci_sigma_host(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables
     const size_t n = (size_t)nvec * p->A.l * p->B.l;
     if (n == 0) return TBSCI_OK;
     if (!c || !sigma) return fail(ctx, TBSCI_EINVAL, "null vector pointer");
-    if (ctx->host_c.n < n) {
-        TB_CUDA(ctx, ctx->host_c.alloc(n));
-        TB_CUDA(ctx, ctx->host_s.alloc(n));
+    if (ctx->host_c.n < n || ctx->host_s.n < n) {
+        // both buffers are re-made together; a failure leaves them empty
+        uncharge(ctx, ctx->host_c.bytes() + ctx->host_s.bytes());
+        ctx->host_c.release();
+        ctx->host_s.release();
+        TB_TRY(charge(ctx, 2 * n * sizeof(double), "tbsci_sigma_host buffers"));
+        cudaError_t e = ctx->host_c.alloc(n);
+        if (e == cudaSuccess) e = ctx->host_s.alloc(n);
+        if (e != cudaSuccess) {
+            ctx->host_c.release();
+            uncharge(ctx, 2 * n * sizeof(double));
+            return fail(ctx, e == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA,
+                        std::string("tbsci_sigma_host buffers: ") + cudaGetErrorString(e));
+        }
     }
     if (!ctx->copy_in) TB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking));
     if (!ctx->copy_out) TB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking));
@@ -435,7 +502,14 @@ tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *
     if (!energies) return fail(ctx, TBSCI_EINVAL, "null energies");
     Plan *p = nullptr;
     TB_TRY(plan_get(ctx, ham, a, b, &p));
-    return davidson_run(ctx, ham, p, nroots, opts, energies, vecs, info);
+    tbsci_davidson_opts o{};
+    if (opts) o = *opts;
+    else o.mixed = ctx->default_mixed;
+    const size_t bytes = engine_device_bytes(p->A.l * p->B.l, nroots, &o);
+    TB_TRY(charge(ctx, bytes, "Davidson vectors"));
+    tbsci_status st = davidson_run(ctx, ham, p, nroots, &o, energies, vecs, info);
+    uncharge(ctx, bytes);
+    return st;
 }
 
 tbsci_status tbsci_overlap(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n, double *S,

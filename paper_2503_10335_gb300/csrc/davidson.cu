@@ -394,6 +394,7 @@ struct DavEngine {
     enum class St { NeedSigma, WaitG, WaitR, WaitGS, Done } state = St::NeedSigma;
     int m = 0, sig_lo = 0, sig_hi = 0, g_lo = 0;
     bool f32 = false, sig_prepared = false;
+    bool mixed_mode = false;  // the solve has a low-precision phase
     tbsci_dtype lowp = TBSCI_F32;  // sigma type of the low-precision phase
     std::vector<double> G, theta, theta_prev, rnorm, e32, Yv;
     std::vector<int> todo;
@@ -499,6 +500,7 @@ struct DavEngine {
         lgrid = (int)std::min<int64_t>(8 * ctx->num_sms, std::max<int64_t>(1, (N + 1023) / 1024));
         rgrid = (int)std::min<int64_t>(6 * ctx->num_sms, std::max<int64_t>(1, (N + 1023) / 1024));
         f32 = opt.mixed != 0;
+        mixed_mode = f32;
         TB_CHECK(ctx, opt.mixed >= 0 && opt.mixed <= 3, TBSCI_EINVAL, "mixed must be 0..3");
         lowp = opt.mixed == 2 ? TBSCI_F32_TC_TF32 : opt.mixed == 3 ? TBSCI_F32_TC_BF16 : TBSCI_F32;
         b32 = opt.basis_f32 != 0;
@@ -903,9 +905,11 @@ struct DavEngine {
             info->nsigma = nsig;
             info->nsigma_f32 = nsig32;
             info->iterations_f32 = it32;
+            info->precision = (int)(mixed_mode ? lowp : TBSCI_F64);
             for (int k = 0; k < nroots && k < 8; ++k) {
                 info->residual[k] = rnorm[k];
                 info->energy_f32[k] = e32[k];
+                info->refine_delta[k] = (mixed_mode && !f32) ? theta[k] - e32[k] : 0.0;
             }
             info->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <array>
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -20,11 +21,19 @@ namespace tbsci {
 // Records `msg` in the context and returns `st`.
 tbsci_status fail(tbsci_ctx *ctx, tbsci_status st, const std::string &msg);
 
+// Context budget (tbsci_options.hbm_budget): charge() counts `bytes` of new
+// device memory against it (ENOMEM, nothing counted, when it would be exceeded),
+// uncharge() gives them back when the object is freed.
+tbsci_status charge(tbsci_ctx *ctx, size_t bytes, const char *what);
+void uncharge(tbsci_ctx *ctx, size_t bytes);
+
+// A failed device allocation returns ENOMEM (the context stays usable); any
+// other CUDA error returns ECUDA.
 #define TB_CUDA(ctx, call)                                                                   \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \
         if (e_ != cudaSuccess)                                                               \
-            return ::tbsci::fail((ctx), TBSCI_ECUDA,                                         \
+            return ::tbsci::fail((ctx), e_ == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA, \
                                  std::string(#call) + ": " + cudaGetErrorString(e_));        \
     } while (0)
 
@@ -53,11 +62,18 @@ struct DevBuf {
         p = nullptr;
         n = 0;
     }
+    // n is set only once the allocation succeeded: a failed alloc leaves an
+    // empty buffer (p == nullptr, n == 0), so a later size check re-allocates
     cudaError_t alloc(size_t count) {
         release();
-        n = count;
         if (count == 0) return cudaSuccess;
-        return cudaMalloc((void **)&p, count * sizeof(T));
+        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        n = count;
+        return cudaSuccess;
     }
     size_t bytes() const { return n * sizeof(T); }
 };
@@ -70,6 +86,12 @@ struct tbsci_ctx {
     int device = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
+    // tbsci_options: device-memory budget of the context's objects (0 = none),
+    // bytes they hold now, Davidson mode when no options are given, tune-cache file
+    size_t hbm_budget = 0;
+    std::atomic<size_t> hbm_used{0};
+    int default_mixed = 0;
+    std::string tune_path;
     cudaStream_t stream = nullptr;
     std::string err;
     uint64_t next_id = 1;
@@ -90,6 +112,7 @@ struct tbsci_ctx {
 
 struct tbsci_strings {
     tbsci_ctx *ctx = nullptr;
+    size_t charged = 0;  // bytes counted against the context's budget
     int norb = 0, nelec = 0;
     int64_t count = 0;
     bool full = false;  // the full C(norb, nelec) space (combinatorial rank applies)
@@ -98,6 +121,7 @@ struct tbsci_strings {
 
 struct tbsci_tables {
     tbsci_ctx *ctx = nullptr;
+    size_t charged = 0;
     uint64_t id = 0;
     int norb = 0, nelec = 0, flags = 0;
     int64_t count = 0;
@@ -161,6 +185,7 @@ struct Plan {
     // autotuned SIMT pass of the tensor-core sigma types (shared-memory mode, threads; 0 = default)
     int tune_rest_mode = 0, tune_rest_threads = 0;
     tbsci_sigma_counts counts{};
+    size_t charged = 0;  // device bytes counted against the context's budget
 };
 
 }  // namespace tbsci

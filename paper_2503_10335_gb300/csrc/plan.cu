@@ -220,6 +220,21 @@ tbsci_status build_spin(tbsci_ctx *ctx, const tbsci_ham *ham, const tbsci_tables
     return TBSCI_OK;
 }
 
+// device bytes a prepared space holds
+size_t plan_device_bytes(const Plan &P) {
+    size_t b = 0;
+    for (const SpinPlan *sp : {&P.A, &P.B})
+        b += sp->d_sci.bytes() + sp->d_sval.bytes() + sp->d_svalf.bytes() + sp->d_dcol.bytes() + sp->d_dval.bytes() +
+             sp->d_dvalf.bytes() + sp->d_E.bytes() + sp->d_Ef.bytes();
+    b += P.d_U.bytes() + P.d_Uf.bytes() + P.d_permb.bytes() + P.d_permb2.bytes();
+    b += P.d_s1_off.bytes() + P.d_s2_off.bytes() + P.d_d2_off.bytes() + P.d_s1_w.bytes() + P.d_s2_w.bytes() +
+         P.d_d2_w.bytes() + P.d_s1_ci.bytes() + P.d_s2_ci.bytes() + P.d_s2_val.bytes() + P.d_d2_val.bytes() +
+         P.d_s2_valf.bytes() + P.d_d2_valf.bytes() + P.d_d2_col.bytes();
+    b += P.d_U1.bytes() + P.d_U2.bytes() + P.d_Eb2.bytes() + P.d_U1f.bytes() + P.d_U2f.bytes() + P.d_Eb2f.bytes();
+    b += P.d_rowsa.bytes() + P.d_pairs.bytes() + P.d_lbp.bytes() + P.d_offpair.bytes() + P.d_tc_err.bytes();
+    return b;
+}
+
 }  // namespace
 
 tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b, Plan **out) {
@@ -393,6 +408,9 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
                                plan->A.d_dval.bytes() + plan->B.d_sci.bytes() + plan->B.d_sval.bytes() +
                                plan->B.d_dcol.bytes() + plan->B.d_dval.bytes() + plan->d_U.bytes());
     TB_CUDA(ctx, cudaStreamSynchronize(st));
+    const size_t bytes = plan_device_bytes(*plan);
+    TB_TRY(charge(ctx, bytes, "prepared space"));  // on failure the plan is freed on return
+    plan->charged = bytes;
     tune_cache_apply(ctx, plan.get(), la, lb);
     *out = plan.get();
     ham->plans.push_back(std::move(plan));

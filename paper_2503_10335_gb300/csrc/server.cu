@@ -216,8 +216,8 @@ struct tbsci_server {
                 --i;
             }
         }
-        // batched sigma for every solve waiting on one
-        std::vector<tbsci::SigmaJob> jobs[2];
+        // batched sigma for every solve waiting on one, grouped by sigma type
+        std::vector<tbsci::SigmaJob> jobs[4];
         std::vector<Req *> waiting;
         for (auto &q : active) {
             const void *c;
@@ -238,15 +238,15 @@ struct tbsci_server {
             }
             cudaEventRecord(q->ready, tbsci::engine_stream(q->eng));
             cudaStreamWaitEvent(sstream, q->ready, 0);
-            jobs[dt == TBSCI_F32 ? 1 : 0].push_back({q->ham, q->plan, c, s, k});
+            jobs[(int)dt].push_back({q->ham, q->plan, c, s, k});
             waiting.push_back(q.get());
         }
         if (!waiting.empty()) {
             tbsci_status bst = TBSCI_OK;
-            for (int d = 0; d < 2 && bst == TBSCI_OK; ++d)
+            for (int d = 0; d < 4 && bst == TBSCI_OK; ++d)
                 if (!jobs[d].empty())
-                    bst = tbsci::sigma_launch_batch(ctx, jobs[d].data(), (int)jobs[d].size(),
-                                                    d ? TBSCI_F32 : TBSCI_F64, sstream, &scratch);
+                    bst = tbsci::sigma_launch_batch(ctx, jobs[d].data(), (int)jobs[d].size(), (tbsci_dtype)d,
+                                                    sstream, &scratch);
             cudaEventRecord(sig_done, sstream);
             const double t = now();
             for (Req *q : waiting) {
@@ -334,7 +334,8 @@ tbsci_status tbsci_submit(tbsci_server *srv, const tbsci_request *req, uint64_t 
     if (!srv || !req || !ticket) return TBSCI_EINVAL;
     const tbsci_request &r = *req;
     if (r.norb < 1 || r.norb > 64 || r.nalpha < 0 || r.nalpha > r.norb || r.nbeta < 0 || r.nbeta > r.norb ||
-        r.nroots < 1 || r.nroots > 8 || !r.h || !r.eri || (r.alpha && r.n_alpha < 0) || (r.beta && r.n_beta < 0))
+        r.nroots < 1 || r.nroots > 8 || !r.h || !r.eri || (r.alpha && r.n_alpha < 0) || (r.beta && r.n_beta < 0) ||
+        r.mixed < 0 || r.mixed > 3)
         return TBSCI_EINVAL;
     auto q = std::make_unique<Req>();
     q->r = r;

@@ -34,18 +34,19 @@ def test_clock_summary(bench):
 
 
 def test_traffic_only_for_the_profiled_kernel_source_and_shape(bench, monkeypatch):
-    rec = bench.NCU_TRAFFIC["f64"]
+    rec = bench.NCU_TRAFFIC[("sel16", "f64")]
     monkeypatch.setattr(bench, "_kernel_hash", lambda: rec["sha1"])
     shapes = rec["shapes"]
     # 3 vectors at 2 per CTA: one 2-vector launch and one 1-vector launch
-    assert bench._traffic("f64", 512, 2, 0, 3) == pytest.approx((shapes[(512, 2, 0)] + shapes[(512, 1, 0)]) / 2)
-    assert bench._traffic("f64", 512, 3, 0, 3) == pytest.approx(shapes[(512, 3, 0)])
-    assert bench._traffic("f64", 512, 1, 0, 3) == pytest.approx(shapes[(512, 1, 0)])
-    assert bench._traffic("f64", 256, 2, 0, 3) is None  # shape not captured
-    assert bench._traffic("f64", 512, 0, 0, 3) is None  # not tuned
+    assert bench._traffic("sel16", "f64", 512, 2, 0, 3) == pytest.approx((shapes[(512, 2, 0)] + shapes[(512, 1, 0)]) / 2)
+    assert bench._traffic("sel16", "f64", 512, 3, 0, 3) == pytest.approx(shapes[(512, 3, 0)])
+    assert bench._traffic("sel16", "f64", 512, 1, 0, 3) == pytest.approx(shapes[(512, 1, 0)])
+    assert bench._traffic("sel16", "f64", 256, 2, 0, 3) is None  # shape not captured
+    assert bench._traffic("sel16", "f64", 512, 0, 0, 3) is None  # not tuned
+    assert bench._traffic("fci16", "f64", 512, 1, 0, 1) is None  # workload not captured
     monkeypatch.setattr(bench, "_kernel_hash", lambda: "0" * 40)
-    assert bench._traffic("f64", 512, 2, 0, 3) is None  # kernel source changed since the capture
-    assert bench._traffic("bf16tc", 512, 2, 0, 3) is None
+    assert bench._traffic("sel16", "f64", 512, 2, 0, 3) is None  # kernel source changed since the capture
+    assert bench._traffic("sel16", "bf16tc", 512, 2, 0, 3) is None
 
 
 def test_replica_throughput_and_single_rank_max(bench):

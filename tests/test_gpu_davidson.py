@@ -187,3 +187,85 @@ def test_restart_with_fewer_free_slots_than_roots(tb, ctx):
     assert info["converged"], info
     assert np.max(np.abs(e - w[:4])) < 1e-8, (e, w[:4])
     sp.close()
+
+
+def _sel12_space(tb, ctx):
+    """norb=12, 6+6 electrons, 250 x 260 selected strings (65,000 determinants,
+    distinct alpha and beta sets): the space of tests/golden/sel12_energies.txt."""
+    h, eri, ecore = synth_hamiltonian(12, seed=4012)
+    a = selected_strings(12, 6, 250, 4013)
+    b = selected_strings(12, 6, 260, 4014)
+    return tb.Space(ctx, 12, 6, 6, h, eri, ecore, alpha=a, beta=b)
+
+
+@pytest.mark.parametrize("mixed,basis_f32", [(0, False), (1, False), (2, False), (1, True)])
+def test_sel12_golden_beyond_dense(tb, ctx, mixed, basis_f32):
+    """65,000 determinants, 3 roots: FP64, FP32-sigma mixed, split-TF32 tensor-core
+    mixed and FP32-basis solves all reach the stored oracle energies (oracle
+    Davidson, cross-checked by ARPACK Lanczos on the oracle sigma) to 1e-8 Eh."""
+    ref = np.loadtxt(os.path.join(GOLDEN, "sel12_energies.txt"))
+    sp = _sel12_space(tb, ctx)
+    assert sp.ndet == 65_000
+    e, info = sp.davidson(3, mixed=mixed, basis_f32=basis_f32)
+    assert info["converged"], info
+    assert np.max(np.abs(e - ref)) < 1e-8, (e, ref)
+    if mixed:
+        assert info["nsigma_f32"] > 0
+    sp.close()
+
+
+def test_sel16_lowest_roots_self_consistency(tb, ctx):
+    """Self-consistency check (no independent reference exists at 9.0M
+    determinants): the 3 roots of the bench's workload equal the lowest 3 of a
+    6-root solve, so the 3-root solve did not converge to higher states."""
+    wl = WORKLOADS["sel16"]
+    h, eri, ecore = wl.hamiltonian()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=wl.alpha_selection(),
+                  beta=wl.beta_selection())
+    e3, i3 = sp.davidson(3)
+    e6, i6 = sp.davidson(6)
+    assert i3["converged"] and i6["converged"]
+    assert np.all(np.diff(e6) >= -1e-10)
+    assert np.max(np.abs(e3 - e6[:3])) < 1e-8, (e3, e6)
+    sp.close()
+
+
+def test_context_options_budget_default_mode_and_tune_file(tb, tmp_path):
+    """tbsci_create_ex: objects are counted against hbm_budget (a space that does
+    not fit is refused with ENOMEM and nothing stays counted; closing a space
+    returns its bytes); tbsci_davidson without options runs in the context's
+    default mixed mode and reports the precision used and the FP64-refinement
+    delta; the tune-cache file is written back by tbsci_destroy."""
+    import ctypes
+    n, na, nb = 8, 4, 3
+    h, eri, _ = synth_hamiltonian(n, seed=41)
+    asel = selected_strings(n, na, 50, 42)
+    small = tb.Context(0, hbm_budget=64 << 10)
+    with pytest.raises(tb.B.TbsciError) as err:
+        tb.Space(small, 12, 6, 6, *synth_hamiltonian(12, seed=3)[:2])
+    assert err.value.status == tb.TBSCI_ENOMEM
+    assert tb.tbsci_hbm_used(small.handle) == 0
+    small.close()
+    path = tmp_path / "tune.txt"
+    ctx = tb.Context(0, hbm_budget=1 << 30, default_mixed=1, tune_cache=str(path))
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.1, alpha=asel)
+    used = tb.tbsci_hbm_used(ctx.handle)
+    assert used > 0
+    lib = tb.B.load()
+    e = np.zeros(2)
+    info = tb.B.DavidsonInfo()
+    st = lib.tbsci_davidson(ctx.handle, sp.ham, sp.ta, sp.tb, 2, None, tb.B._ptr(e), None, ctypes.byref(info))
+    assert st == tb.TBSCI_OK
+    d = info.as_dict()
+    assert d["precision"] == tb.TBSCI_F32 and d["nsigma_f32"] > 0
+    assert np.allclose(np.array(d["refine_delta"][:2]), e - np.array(d["energy_f32"][:2]), atol=1e-14)
+    assert max(abs(x) for x in d["refine_delta"][:2]) < 1e-3
+    w = np.linalg.eigvalsh(oracle.hamiltonian_dense(oracle.make_space(n, na, nb, asel, None), h, eri, 0.1))
+    assert np.max(np.abs(e - w[:2])) < 1e-8
+    e64, i64 = sp.davidson(2)
+    assert i64["precision"] == tb.TBSCI_F64 and i64["refine_delta"][:2] == [0.0, 0.0]
+    assert tb.tbsci_hbm_used(ctx.handle) == used  # the solves' vectors were given back
+    sp.close()
+    assert tb.tbsci_hbm_used(ctx.handle) == 0
+    ctx.close()
+    assert path.read_text().startswith("tbsci-tune 1")

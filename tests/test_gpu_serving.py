@@ -140,3 +140,58 @@ def test_server_with_tune_cache(tb, tmp_path):
         plain.close()
     for x, y in zip(ra, rb):
         assert np.max(np.abs(np.array(x["energies"]) - np.array(y["energies"]))) < 1e-8
+
+
+def test_large_job_same_alone_and_in_the_mix(tb):
+    """Two requests above the batching threshold (2^20 determinant-vectors: full
+    norb 12, 6+6 space, 853,776 determinants x 2 roots, one FP64 and one mixed)
+    launch their sigma on their own streams while small solves ride in the
+    batched launches beside them. Each result equals the same request solved
+    alone on the server and the blocking tbsci_davidson solve, to 1e-8 Eh."""
+    small = _requests(5, 8)
+    h, eri, _ = synth_hamiltonian(12, seed=5012)
+    big = [dict(norb=12, nalpha=6, nbeta=6, h=h, eri=eri, ecore=0.0, alpha=None, beta=None, nroots=2,
+                mixed=m) for m in (False, True)]
+    reqs = small[:3] + [big[0]] + small[3:6] + [big[1]] + small[6:]
+    srv = tb.Server(0)
+    try:
+        mixed_res = _solve_all(srv, reqs, stagger=0.01)
+        alone = [_solve_all(srv, [r])[0] for r in reqs]
+    finally:
+        srv.close()
+    for r, a, b in zip(reqs, mixed_res, alone):
+        assert a["status"] == 0 and b["status"] == 0
+        assert np.max(np.abs(np.array(a["energies"]) - np.array(b["energies"]))) < 1e-8
+    ctx = tb.Context(0)
+    sp = tb.Space(ctx, 12, 6, 6, h, eri, 0.0)
+    assert sp.ndet * 2 > (1 << 20)
+    e, info = sp.davidson(2)
+    assert info["converged"]
+    for k in (3, 7):
+        assert np.max(np.abs(np.array(mixed_res[k]["energies"]) - e)) < 1e-8, (k, mixed_res[k], e)
+    sp.close()
+    ctx.close()
+
+
+def test_tensor_core_mixed_requests_in_the_mix(tb):
+    """Requests whose low-precision phase uses the tensor-core sigma types (2:
+    split TF32, 3: BF16) ride beside FP64 and FP32-sigma requests in the same
+    server; each result equals the dense eigenvalues to 1e-8 Eh after the FP64
+    refinement. A mode outside 0..3 is refused at submit."""
+    reqs = _requests(6, 8)
+    for i, r in enumerate(reqs):
+        r["mixed"] = i % 4
+    srv = tb.Server(0)
+    try:
+        with pytest.raises(tb.B.TbsciError):
+            srv.submit(**dict(reqs[0], mixed=4))
+        res = _solve_all(srv, reqs, stagger=0.002)
+    finally:
+        srv.close()
+    for r, d in zip(reqs, res):
+        assert d["status"] == 0
+        osp = oracle.make_space(r["norb"], r["nalpha"], r["nbeta"], r["alpha"], r["beta"])
+        w = np.linalg.eigvalsh(oracle.hamiltonian_dense(osp, r["h"], r["eri"], r["ecore"]))[:r["nroots"]]
+        assert np.max(np.abs(np.array(d["energies"]) - w)) < 1e-8, (r["mixed"], d["energies"], w)
+        if r["mixed"]:
+            assert d["nsigma_f32"] > 0

@@ -131,9 +131,9 @@ def test_fci8_sigma(tb, ctx):
 
 def test_sel16_sigma_sampled_rows_full_size(tb, ctx):
     """norb=16, 3,000 x 3,000 selected strings (9.0M determinants), FP64, 3
-    vectors in one call: the bench's workload and launch configuration. 4,000
-    seeded rows (whole rows of the first and last alpha strings included) are
-    recomputed by the oracle."""
+    vectors in one call, autotuned first: the launch configuration the bench
+    times for this workload. 4,000 seeded rows (whole rows of the first and last
+    alpha strings included) are recomputed by the oracle."""
     import torch
     wl = WORKLOADS["sel16"]
     h, eri, ecore = wl.hamiltonian()
@@ -142,7 +142,9 @@ def test_sel16_sigma_sampled_rows_full_size(tb, ctx):
     osp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, asel, bsel)
     assert sp.ndet == 9_000_000
     C = random_vectors(3, sp.la, sp.lb, seed=wl.seed_vec)
-    s = sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy().reshape(3, -1)
+    Cd = torch.from_numpy(C).cuda()
+    tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, Cd, torch.empty_like(Cd), 3, tb.TBSCI_F64)
+    s = sp.sigma(Cd).cpu().numpy().reshape(3, -1)
     rng = np.random.default_rng(wl.seed_vec)
     rows = np.unique(np.concatenate([rng.choice(sp.ndet, 3000, replace=False), np.arange(500),
                                      np.arange(sp.ndet - 500, sp.ndet)]))
@@ -222,12 +224,14 @@ def test_sigma_rows_longer_than_shared_memory(tb, ctx, n, dtype):
     sp.close()
 
 
-@pytest.mark.parametrize("name,dtype", [("fci16", "f64"), ("fci16", "f32"), ("sel24", "f32")])
-def test_large_configs_sigma_sampled_rows(tb, ctx, name, dtype):
+@pytest.mark.parametrize("name,dtype,tune", [("fci16", "f64", False), ("fci16", "f32", False),
+                                             ("sel24", "f32", False), ("sel24", "f64", True)])
+def test_large_configs_sigma_sampled_rows(tb, ctx, name, dtype, tune):
     """norb=16 full string space (12,870^2 = 165.6M determinants) and norb=24,
     40,000 x 40,000 selected strings (1.6B determinants), one vector: 600 seeded
     rows recomputed by the oracle. FP32 runs compare against the oracle applied
-    to the FP32-rounded vector, within FP32 accumulation error."""
+    to the FP32-rounded vector, within FP32 accumulation error. The FP64 run at
+    norb 24 is the bench's headline launch: autotuned first, then timed shape."""
     import torch
     wl = WORKLOADS[name]
     h, eri, ecore = wl.hamiltonian()
@@ -240,7 +244,14 @@ def test_large_configs_sigma_sampled_rows(tb, ctx, name, dtype):
     # neighbourhoods are read back from it for the oracle
     g = torch.Generator(device="cuda").manual_seed(wl.seed_vec)
     C = torch.randn((1, sp.la, sp.lb), generator=g, device="cuda", dtype=torch.float32).to(tdt)
-    S = sp.sigma(C)
+    if tune:
+        S = torch.empty_like(C)
+        sdt = tb.TBSCI_F64 if dtype == "f64" else tb.TBSCI_F32
+        assert tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, 1, sdt) > 0
+        assert sp.counts()["tuned_nv"][0 if dtype == "f64" else 1] >= 1
+        S = sp.sigma(C, S)
+    else:
+        S = sp.sigma(C)
     rows = np.sort(rng.choice(sp.ndet, 600, replace=False))
     got = S.reshape(-1)[torch.from_numpy(rows).cuda()].double().cpu().numpy()[None]
     del S
@@ -353,4 +364,21 @@ def test_tune_cache_roundtrip(tb, ctx, tmp_path):
     assert_sigma_close(s2, ref, bound)
     sp2.close()
     ctx2.close()
+    sp.close()
+
+
+def test_sigma_host_recovers_from_a_failed_allocation(tb, ctx):
+    """tbsci_sigma_host with more vectors than the device can hold: its device
+    buffers cannot be allocated, the call returns ENOMEM without touching the host
+    arrays, and the next call of a normal size allocates again and gives the
+    device result."""
+    import torch
+    sp, osp, h, eri = _case(tb, ctx, 10, 5, 5, 120, 130, seed=19)
+    C = random_vectors(1, sp.la, sp.lb, seed=20)
+    out = np.empty_like(C)
+    lib = tb.B.load()
+    huge = (1 << 31) - 1  # ~ 2^31 vectors of 15,600 determinants: 267 TB
+    st = lib.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, tb.B._ptr(C), tb.B._ptr(out), huge)
+    assert st == tb.TBSCI_ENOMEM, st
+    assert np.array_equal(sp.sigma_host(C), sp.sigma(torch.from_numpy(C).cuda()).cpu().numpy())
     sp.close()

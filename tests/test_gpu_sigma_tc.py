@@ -137,3 +137,33 @@ def test_tc_sigma_rest_modes_from_tune_cache(tb, n, na, nb, acnt, bcnt, rest_mod
     assert_sigma_close(s, ref, bound, rel=rel, norm_rel=norm_rel)
     sp.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_tc_sigma_fci16_sampled_tuned(tb, ctx, mode):
+    """norb=16 full string space (12,870^2 = 165.6M determinants), 1 vector, in the
+    launch configuration the bench times for the tensor-core types: autotuned
+    first (SIMT pass shape), then 600 seeded rows recomputed by the oracle from
+    the FP32-rounded vector, at the tensor-core tolerances."""
+    import torch
+    wl = WORKLOADS["fci16"]
+    h, eri, ecore = wl.hamiltonian()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore)
+    osp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta)
+    assert sp.ndet == 12870 * 12870
+    dt = tb.TBSCI_F32_TC_TF32 if mode == "tf32" else tb.TBSCI_F32_TC_BF16
+    g = torch.Generator(device="cuda").manual_seed(wl.seed_vec)
+    C = torch.randn((1, sp.la, sp.lb), generator=g, device="cuda", dtype=torch.float32)
+    S = torch.empty_like(C)
+    ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, 1, dt)
+    assert ms > 0
+    S = sp.sigma(C, S, dtype=dt)
+    rows = np.sort(np.random.default_rng(wl.seed_vec + 1).choice(sp.ndet, 600, replace=False))
+    got = S.reshape(-1)[torch.from_numpy(rows).cuda()].double().cpu().numpy()[None]
+    Ch = C.reshape(1, -1).double().cpu().numpy()
+    del S, C
+    ref, bound = oracle.sigma(osp, h, eri, ecore, Ch, rows=rows, with_bound=True)
+    rel, norm_rel = TOL[mode]
+    assert_sigma_close(got, ref, bound, rel=rel, norm_rel=norm_rel)
+    sp.close()
+    torch.cuda.empty_cache()
