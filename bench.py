@@ -1,13 +1,13 @@
 """Benchmark: sigma = H.c throughput (GDet/s) on one GB300, plus Davidson time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
-                    [--workload sel16|fci8|fci16|sel24] [--dtype f64|f32]
+                    [--workload sel24|sel16|fci8|fci16] [--dtype f64|f32|tf32tc|bf16tc]
 
 A step is one sigma evaluation of ``nvec`` vectors over the whole space (all of
-its Slater-Condon classes, one fused kernel launch per group of <= 4 vectors).
-The default workload is norb=16, 8+8 electrons, 3,000 x 3,000 selected strings
-(9.0M determinants), FP64, 3 vectors -- 216 MB of input and 216 MB of output per
-step, both larger than the 129 MB L2, so no flush is needed between steps.
+its Slater-Condon classes). The default workload is the largest single-GPU one:
+norb=24, 12+12 electrons, 40,000 x 40,000 selected strings (1.6B determinants),
+FP64, 1 vector -- 12.8 GB of input and 12.8 GB of output per step, both far
+larger than the 129 MB L2, so no flush is needed between steps.
 
 value  = nvec * ndet / (device time per step) / 1e9, timed with CUDA events on
          the launching stream after W warm-up steps, max over ranks.
@@ -18,6 +18,10 @@ roofline = the fused sigma kernel against the FP64 ALU (2 flops per non-zero
          H_IJ per vector) or the FP32 ALU.
 cpu_baseline = the CPU oracle timed on a bounded row sample of the same
          workload on this host's cores (rank 0, N = 1 only).
+sel16_sigma = the same measurement on norb=16, 3,000 x 3,000 selected strings
+         (9.0M determinants), FP64, 3 vectors.
+davidson = Davidson time to 1e-9 / 1e-5 on the 9.0M-determinant space, FP64
+         and mixed precision.
 --impl reference runs the oracle alone as the reference arm.
 
 Under torchrun (N > 1) every rank runs an independent replica (the path does
@@ -41,7 +45,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from tbsci_inputs import WORKLOADS, random_vectors  # noqa: E402
+from tbsci_inputs import WORKLOADS, random_vectors, selected_strings  # noqa: E402
 
 METRIC = "σ GDet/s and Davidson time to 1e-8 Eh; serving p50/p99 vs plain FP64 on GB300"
 UNIT = "GDet/s"
@@ -49,20 +53,16 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (recipe nominal)
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FMA = 2 flops
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_sigma launch
-# from an ncu capture of the default workload, keyed by dtype, with the sha1 of
-# the kernel source it was taken on: a changed kernel reports null until
-# re-captured (profiles/k_sigma_f64_sel16.md).
-# DRAM bytes (read + write) per launch of the sigma kernel by launch shape
-# (threads, vectors per CTA, shared-memory mode), from one ncu capture of the kernel
-# source with this sha1 (the shape-by-shape table is in the profile of k_sigma FP64 at
-# sel16); a shape or source not captured reports null
+# DRAM bytes (read + write) per launch of the sigma kernel, by workload and launch
+# shape (threads, vectors per CTA, shared-memory mode), from one ncu capture of the
+# kernel source with this sha1 (the shape-by-shape tables are in the profiles of
+# k_sigma FP64); a workload, shape or source not captured reports null
 NCU_TRAFFIC = {
-    "f64": {"sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2",
-            "shapes": {(512, 1, 0): 1.998e9, (512, 2, 0): 7.439e9, (512, 3, 0): 12.643e9,
-                       (256, 1, 0): 1.356e9, (128, 1, 0): 0.803e9,
-                       (512, 1, 1): 1.233e9, (256, 1, 1): 0.811e9, (128, 1, 1): 1.558e9,
-                       (512, 1, 2): 2.049e9, (256, 1, 2): 1.496e9, (128, 1, 2): 3.683e9}},
+    ("sel16", "f64"): {"sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2",
+                       "shapes": {(512, 1, 0): 1.998e9, (512, 2, 0): 7.439e9, (512, 3, 0): 12.643e9,
+                                  (256, 1, 0): 1.356e9, (128, 1, 0): 0.803e9,
+                                  (512, 1, 1): 1.233e9, (256, 1, 1): 0.811e9, (128, 1, 1): 1.558e9,
+                                  (512, 1, 2): 2.049e9, (256, 1, 2): 1.496e9, (128, 1, 2): 3.683e9}},
 }
 
 
@@ -72,10 +72,10 @@ def _kernel_hash():
         return hashlib.sha1(f.read()).hexdigest()
 
 
-def _traffic(dtype, threads, nv, stage, nvec):
+def _traffic(workload, dtype, threads, nv, stage, nvec):
     """Average DRAM bytes per launch of one step: nvec vectors in launch groups of
     nv (the last one smaller) at the tuned threads and shared-memory mode."""
-    rec = NCU_TRAFFIC.get(dtype)
+    rec = NCU_TRAFFIC.get((workload, dtype))
     if not rec or rec["sha1"] != _kernel_hash() or nv < 1:
         return None
     groups = [min(nv, nvec - v) for v in range(0, nvec, nv)]
@@ -171,19 +171,37 @@ def replica_throughput(world_size: int, units_per_rank: float, max_seconds: floa
     return world_size * units_per_rank / max_seconds
 
 
-def cpu_baseline(wl, nvec, budget_s=15.0, impl_rows=None):
-    """Oracle sigma over a bounded, seeded row sample of the workload."""
+def _oracle_space(wl, count_alpha=None):
+    import oracle
+    asel = wl.alpha_selection()
+    if count_alpha is not None:
+        asel = selected_strings(wl.norb, wl.nalpha, count_alpha, wl.seed_sel)
+    return oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, asel, wl.beta_selection())
+
+
+def _host_vector(nvec, ndet, seed):
+    """A seeded host vector [nvec, ndet] for timing the oracle (uniform in
+    [-0.5, 0.5): drawing 1.6B normal deviates would take longer than the timing)."""
+    c = np.random.default_rng(seed).random((nvec, ndet))
+    c -= 0.5
+    return c
+
+
+def cpu_baseline(wl, nvec, budget_s=15.0, C=None, count_alpha=None):
+    """Oracle sigma over a bounded, seeded row sample of the workload; C is the
+    host copy [nvec, ndet] of the vector the GPU leg used (drawn here if None)."""
     import oracle
     h, eri, ecore = wl.hamiltonian()
-    sp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, wl.alpha_selection(), wl.beta_selection())
-    C = random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec).reshape(nvec, -1)
+    sp = _oracle_space(wl, count_alpha)
+    if C is None:
+        C = _host_vector(nvec, sp.ndet, wl.seed_vec)
     rng = np.random.default_rng(wl.seed_vec + 17)
     # calibrate on a small sample, then size the measured sample to the budget
     probe = rng.choice(sp.ndet, 500, replace=False)
     t0 = time.perf_counter()
     oracle.sigma(sp, h, eri, ecore, C, rows=probe)
     rate = 500 / max(time.perf_counter() - t0, 1e-6)
-    nrows = impl_rows or int(min(sp.ndet, max(1000, rate * budget_s)))
+    nrows = int(min(sp.ndet, max(1000, rate * budget_s)))
     rows = rng.choice(sp.ndet, nrows, replace=False)
     t0 = time.perf_counter()
     oracle.sigma(sp, h, eri, ecore, C, rows=rows)
@@ -201,10 +219,16 @@ def run_reference(args):
     wl = WORKLOADS[args.workload]
     nvec = wl.nvec
     h, eri, ecore = wl.hamiltonian()
-    sp = oracle.make_space(wl.norb, wl.nalpha, wl.nbeta, wl.alpha_selection(), wl.beta_selection())
-    C = random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec).reshape(nvec, -1)
+    sp = _oracle_space(wl, args.count_alpha)
+    C = _host_vector(nvec, sp.ndet, wl.seed_vec)
     rng = np.random.default_rng(wl.seed_vec + 29)
-    rows_per_step = min(sp.ndet, args.ref_rows)
+    rows_per_step = args.ref_rows
+    if rows_per_step <= 0:  # about 2 s of oracle work per step
+        probe = rng.choice(sp.ndet, 500, replace=False)
+        t0 = time.perf_counter()
+        oracle.sigma(sp, h, eri, ecore, C, rows=probe)
+        rows_per_step = int(max(1000, 2.0 * 500 / max(time.perf_counter() - t0, 1e-6)))
+    rows_per_step = min(sp.ndet, rows_per_step)
     for _ in range(args.warmup):
         oracle.sigma(sp, h, eri, ecore, C, rows=rng.choice(sp.ndet, rows_per_step, replace=False))
     times = []
@@ -219,7 +243,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(_config(wl, nvec, "f64"), parallelism="replicas" if ws > 1 else "single"),
+        "config": dict(_config(wl, nvec, "f64", la=sp.la, lb=sp.lb), parallelism="replicas" if ws > 1 else "single"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                          "sample": "%d seeded determinant rows per step of %d, %d vectors" %
                                    (rows_per_step, sp.ndet, nvec)},
@@ -228,13 +252,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _config(wl, nvec, dtype):
-    la = math.comb(wl.norb, wl.nalpha) if wl.count_alpha is None else min(wl.count_alpha, math.comb(wl.norb, wl.nalpha))
-    lb = math.comb(wl.norb, wl.nbeta) if wl.count_beta is None else min(wl.count_beta, math.comb(wl.norb, wl.nbeta))
-    return {"workload": wl.notes, "name": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta,
+def _config(wl, nvec, dtype, la=None, lb=None):
+    if la is None:
+        la = math.comb(wl.norb, wl.nalpha) if wl.count_alpha is None else min(wl.count_alpha,
+                                                                               math.comb(wl.norb, wl.nalpha))
+    if lb is None:
+        lb = math.comb(wl.norb, wl.nbeta) if wl.count_beta is None else min(wl.count_beta,
+                                                                             math.comb(wl.norb, wl.nbeta))
+    name = wl.notes if (la, lb) == _config_default_sizes(wl) else \
+        "norb=%d, %d+%d electrons, %d x %d selected strings (%.1fM determinants; a smaller case of %s)" % (
+            wl.norb, wl.nalpha, wl.nbeta, la, lb, la * lb / 1e6, wl.name)
+    return {"workload": name, "name": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta,
             "l_alpha": la, "l_beta": lb, "ndet": la * lb, "nvec": nvec, "sigma_dtype": dtype,
             "l2_policy": "inputs larger than L2 (no flush)" if la * lb * nvec * (8 if dtype == "f64" else 4) > 129e6
-            else "L2 flushed between steps"}
+            else "inputs smaller than L2 (not flushed; not a headline configuration)"}
+
+
+def _config_default_sizes(wl):
+    la = math.comb(wl.norb, wl.nalpha) if wl.count_alpha is None else min(wl.count_alpha,
+                                                                           math.comb(wl.norb, wl.nalpha))
+    lb = math.comb(wl.norb, wl.nbeta) if wl.count_beta is None else min(wl.count_beta,
+                                                                         math.comb(wl.norb, wl.nbeta))
+    return la, lb
 
 
 def _serving_requests(nreq, seed, max_count):
@@ -249,70 +288,76 @@ def _serving_requests(nreq, seed, max_count):
     return reqs
 
 
-def _fifo_latencies(arrivals, service):
-    """Latencies of a single FIFO server (one solve at a time)."""
-    t_free, lat = 0.0, []
-    for a, s in zip(arrivals, service):
-        start = max(a, t_free)
-        t_free = start + s
-        lat.append(t_free - a)
-    return lat, t_free
-
-
-def run_serving(args):
-    """Serving stream (Poisson arrivals, norb 8..16, 50..max strings per spin, 1-3
-    roots): FP64 one-at-a-time vs the mixed-precision continuous-batching server,
-    at arrival rates 0.5x and 2x the FP64 sequential service rate."""
-    import torch
-    import paper_2503_10335_gb300 as tb
-    reqs = _serving_requests(args.nreq, 5005, args.max_count)
-    ctx = tb.Context(0)
-    # calibration: FP64 one-at-a-time service times (set-up + solve through the C ABI)
-    service, e64 = [], []
-    for r in reqs:
-        t0 = time.perf_counter()
-        sp = tb.Space(ctx, r["norb"], r["nalpha"], r["nbeta"], r["h"], r["eri"], r["ecore"], alpha=r["alpha"],
-                      beta=r["beta"])
-        e, info = sp.davidson(r["nroots"])
-        torch.cuda.synchronize()
-        service.append(time.perf_counter() - t0)
-        e64.append(e)
-        sp.close()
-    ctx.close()
-    mu = len(reqs) / sum(service)
-    base_gaps = np.array([r["gap"] for r in reqs])  # unit-rate Poisson arrival times
-    out = {"metric": METRIC, "mode": "serving", "nreq": len(reqs), "fp64_service_rate_per_s": mu,
-           "fp64_total_service_s": sum(service), "max_strings": args.max_count, "rates": []}
-    for mult in (0.5, 2.0):
-        lam = mult * mu
-        arrivals = base_gaps / lam
-        lat64, end64 = _fifo_latencies(arrivals, service)
-        srv = tb.Server(0)
-        t0 = time.perf_counter()
-        tickets = []
+def _replay(tb, reqs, arrivals, mixed, **server_kw):
+    """Submits every request at its arrival time (seconds from the start) to a new
+    server and waits for all results. Returns (results, makespan seconds)."""
+    srv = tb.Server(0, **server_kw)
+    t0 = time.perf_counter()
+    tickets = []
+    try:
         for r, a in zip(reqs, arrivals):
             delay = a - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
             kw = {k: r[k] for k in ("norb", "nalpha", "nbeta", "h", "eri", "ecore", "alpha", "beta", "nroots")}
-            tickets.append(srv.submit(mixed=True, **kw))
+            tickets.append(srv.submit(mixed=mixed, **kw))
         res = []
         for t in tickets:
             st, d = srv.poll(t, timeout_ms=-1)
             res.append(d)
         makespan = time.perf_counter() - t0
+    finally:
         srv.close()
-        lat = [d["t_done"] - d["t_submit"] for d in res]
-        err = max(float(np.max(np.abs(np.array(d["energies"]) - e))) for d, e in zip(res, e64))
+    return res, makespan
+
+
+def _latency_summary(res, makespan):
+    lat = [d["t_done"] - d["t_submit"] for d in res]
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(np.mean(lat)), "throughput_per_s": len(res) / makespan, "makespan_s": makespan,
+            "statuses": sorted(set(int(d["status"]) for d in res))}
+
+
+def run_serving(args, print_line=True):
+    """Serving stream (Poisson arrivals, norb 8..16, 50..max strings per spin, 1-3
+    roots): plain FP64 one-at-a-time (a one-slot server, unbatched, FP64 sigma)
+    against the mixed-precision continuous-batching server, both fed the same
+    arrival timestamps live, at arrival rates that are multiples of the FP64
+    sequential service rate (calibrated on the first requests of the stream)."""
+    import torch
+    import paper_2503_10335_gb300 as tb
+    reqs = _serving_requests(args.nreq, 5005, args.max_count)
+    ncal = min(len(reqs), args.calibrate)
+    ctx = tb.Context(0)
+    # calibration: FP64 one-at-a-time service times (set-up + solve through the C ABI)
+    service = []
+    for r in reqs[:ncal]:
+        t0 = time.perf_counter()
+        sp = tb.Space(ctx, r["norb"], r["nalpha"], r["nbeta"], r["h"], r["eri"], r["ecore"], alpha=r["alpha"],
+                      beta=r["beta"])
+        sp.davidson(r["nroots"])
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+        sp.close()
+    ctx.close()
+    mu = ncal / sum(service)
+    base = np.array([r["gap"] for r in reqs])  # unit-rate Poisson arrival times
+    out = {"metric": METRIC, "mode": "serving", "nreq": len(reqs), "max_strings": args.max_count,
+           "fp64_service_rate_per_s": mu, "calibration_requests": ncal, "rates": []}
+    for mult in [float(x) for x in args.rates.split(",")]:
+        lam = mult * mu
+        arrivals = base / lam
+        r64, m64 = _replay(tb, reqs, arrivals, False, max_active=1, fuse_sigma=-1)
+        rmx, mmx = _replay(tb, reqs, arrivals, args.serving_mixed)
+        diffs = [float(np.max(np.abs(np.array(a["energies"]) - np.array(b["energies"])))) for a, b in zip(rmx, r64)]
         out["rates"].append({
             "arrival_rate_per_s": lam, "x_fp64_rate": mult,
-            "fp64_one_at_a_time": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
-                                   "throughput_per_s": len(reqs) / end64},
-            "mixed_batched": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                              "throughput_per_s": len(reqs) / makespan,
-                              "statuses": sorted(set(d["status"] for d in res))},
-            "max_energy_diff_vs_fp64_Eh": err})
-    print(json.dumps(out), flush=True)
+            "fp64_one_at_a_time": _latency_summary(r64, m64),
+            "mixed_batched": dict(_latency_summary(rmx, mmx), sigma_mode=args.serving_mixed),
+            "energy_diff_vs_fp64_Eh": {"max": max(diffs), "p50": float(np.median(diffs))}})
+    if print_line:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 def run_precision_study(args):
@@ -370,18 +415,130 @@ def run_precision_study(args):
     print(json.dumps(out), flush=True)
 
 
+def _sigma_leg(tb, ctx, wl, dtype, nvec, steps, warmup, dev, stream, autotune=True, clocks=False,
+               count_alpha=None):
+    """Times `steps` sigma evaluations of `nvec` vectors on one workload (device
+    buffers, CUDA events on the launching stream). Returns the leg's record and
+    the space with its device vectors (for the callers' e2e and baseline legs)."""
+    import torch
+    h, eri, ecore = wl.hamiltonian()
+    asel = wl.alpha_selection()
+    if count_alpha is not None:
+        asel = selected_strings(wl.norb, wl.nalpha, count_alpha, wl.seed_sel)
+    t_setup = time.perf_counter()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=asel, beta=wl.beta_selection())
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    sdt = {"f64": tb.TBSCI_F64, "f32": tb.TBSCI_F32, "tf32tc": tb.TBSCI_F32_TC_TF32,
+           "bf16tc": tb.TBSCI_F32_TC_BF16}[dtype]
+    g = torch.Generator(device=dev).manual_seed(wl.seed_vec)
+    C = torch.randn((nvec, sp.la, sp.lb), generator=g, device=dev, dtype=torch.float64).to(tdt)
+    S = torch.empty_like(C)
+    tuned_ms = None
+    if autotune:
+        # set-up, untimed: pick the launch shape of the SIMT kernel for this space
+        tuned_ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, nvec, sdt, stream)
+    for _ in range(warmup):
+        sp.sigma(C, S, stream=stream, dtype=sdt)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index) if clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(steps):
+        sp.sigma(C, S, stream=stream, dtype=sdt)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = sampler.stop() if sampler else None
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    counts = sp.counts()  # after tuning: carries the chosen launch shape
+    if sdt in (tb.TBSCI_F64, tb.TBSCI_F32):
+        nv_used = counts["tuned_nv"][0 if sdt == tb.TBSCI_F64 else 1] or min(nvec, 4)
+        launches_per_step = (nvec + nv_used - 1) // nv_used
+    else:  # SIMT pass + tensor-core kernel per vector
+        launches_per_step = 2 * nvec
+    flops_step = 2.0 * counts["nnz"] * nvec
+    kern_ms = statistics.mean(per_step) / launches_per_step
+    achieved = flops_step / launches_per_step / (kern_ms * 1e-3) / 1e12
+    peak = FP64_NOMINAL_TFLOPS if dtype == "f64" else FP32_NOMINAL_TFLOPS
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": (_traffic(wl.name, dtype, counts["tuned_threads"][0], counts["tuned_nv"][0],
+                                     counts["tuned_stage"][0], nvec) if dtype == "f64" else None),
+                "kernel": "k_sigma (fused, all classes)",
+                "peak_source": "%s ALU derived from unit counts and clocks (152 SMs x %s per clock x 2070 MHz)" %
+                               (("FP64", "2 DFMA") if dtype == "f64" else ("FP32", "128 FFMA")),
+                "algorithmic_flops_per_launch": flops_step / launches_per_step,
+                "algorithmic_flops_rule": "2 flops per non-zero H_IJ per vector"}
+    rec = {"value": nvec * sp.ndet / (total_ms / steps * 1e-3) / 1e9, "ms_per_step": total_ms / steps,
+           "step_ms_min": min(per_step), "step_ms_max": max(per_step), "roofline": roofline,
+           "launches_per_step": launches_per_step, "counts": counts, "setup_seconds": t_setup,
+           "autotune_ms": tuned_ms, "config": _config(wl, nvec, dtype, la=sp.la, lb=sp.lb), "clocks": clk}
+    return rec, sp, C, S, sdt
+
+
+def _e2e_leg(tb, ctx, sp, C, nvec, steps, world):
+    """The same metric through tbsci_sigma_host with pinned HOST buffers: the
+    host->device copy of c and the device->host copy of sigma are inside the
+    timed region of every step. Returns the record and the pinned host c."""
+    import torch
+    hc = C.cpu().pin_memory()
+    hs = torch.empty_like(hc).pin_memory()
+    hcn, hsn = hc.numpy(), hs.numpy()
+    tb.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, hcn, hsn, nvec)  # warm the device buffers
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        tb.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, hcn, hsn, nvec)
+    dt = (time.perf_counter() - t0) / steps
+    nbytes = nvec * sp.ndet * 8
+    del hs
+    return ({"value": world * nvec * sp.ndet / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+             "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3, "steps": steps, "api": "tbsci_sigma_host"},
+            hcn)
+
+
+def _davidson_leg(tb, ctx, wl):
+    """Davidson to |dE| < 1e-9, ||r|| < 1e-5 per root, FP64 and mixed precision."""
+    import torch
+    h, eri, ecore = wl.hamiltonian()
+    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=wl.alpha_selection(),
+                  beta=wl.beta_selection())
+    dav = {"workload": wl.notes, "nroots": wl.nroots}
+    for mode, mixed in (("f64", 0), ("mixed", 1)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, info = sp.davidson(wl.nroots, mixed=mixed, tol_energy=1e-9, tol_residual=1e-5)
+        dt = time.perf_counter() - t0
+        dav[mode] = {"seconds": dt, "iterations": info["iterations"], "nsigma": info["nsigma"],
+                     "nsigma_f32": info["nsigma_f32"], "energies": [float(x) for x in e],
+                     "converged": info["converged"], "seconds_sigma": info["seconds_sigma"],
+                     "seconds_outside_sigma": dt - info["seconds_sigma"]}
+    dav["mixed_minus_f64_max_abs"] = max(abs(a - b) for a, b in zip(dav["mixed"]["energies"],
+                                                                   dav["f64"]["energies"]))
+    dav["target"] = "time to |dE| < 1e-9 and ||r|| < 1e-5 per root (energies within 1e-8 Eh)"
+    sp.close()
+    return dav
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--workload", default="sel16", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sel24", choices=sorted(WORKLOADS))
+    ap.add_argument("--count-alpha", type=int, default=None,
+                    help="use this many selected alpha strings (a smaller case of the workload, for profiling)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "tf32tc", "bf16tc"])
-    ap.add_argument("--ref-rows", type=int, default=20000)
+    ap.add_argument("--ref-rows", type=int, default=0, help="reference arm: oracle rows per step (0: sized)")
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-extra", action="store_true", help="skip the norb=16 selected-space sigma leg")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--serving", action="store_true", help="serving stream instead of the sigma bench")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--precision-study", action="store_true")
@@ -390,7 +547,10 @@ def main():
     ap.add_argument("--basis-f32", action="store_true", help="--precision-study: FP32-stored Davidson basis")
     ap.add_argument("--max-subspace", type=int, default=0)
     ap.add_argument("--restart-keep", type=int, default=0)
-    ap.add_argument("--nreq", type=int, default=48)
+    ap.add_argument("--nreq", type=int, default=512)
+    ap.add_argument("--rates", default="2", help="serving: arrival rates as multiples of the FP64 service rate")
+    ap.add_argument("--calibrate", type=int, default=64, help="serving: requests timed for the FP64 rate")
+    ap.add_argument("--serving-mixed", type=int, default=1, help="serving: low-precision sigma mode (1, 2, 3)")
     ap.add_argument("--max-count", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -414,117 +574,60 @@ def main():
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
     nvec = wl.nvec
-    h, eri, ecore = wl.hamiltonian()
     ctx = tb.Context(local)
-    t_setup = time.perf_counter()
-    sp = tb.Space(ctx, wl.norb, wl.nalpha, wl.nbeta, h, eri, ecore, alpha=wl.alpha_selection(),
-                  beta=wl.beta_selection())
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t_setup
-    counts = sp.counts()
-    Cn = random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec)
-    tdt = torch.float64 if args.dtype == "f64" else torch.float32
-    sdt = {"f64": tb.TBSCI_F64, "f32": tb.TBSCI_F32, "tf32tc": tb.TBSCI_F32_TC_TF32,
-           "bf16tc": tb.TBSCI_F32_TC_BF16}[args.dtype]
-    C = torch.from_numpy(Cn).to(dev).to(tdt)
-    S = torch.empty_like(C)
     stream = torch.cuda.current_stream()
-    # fused kernel: one launch per <= 4 vectors; tensor-core modes: SIMT rest + tensor kernel per vector
-    launches_per_step = (nvec + 3) // 4 if sdt in (tb.TBSCI_F64, tb.TBSCI_F32) else 2 * nvec
-
-    tuned_ms = None
-    if not args.no_autotune:
-        # set-up, untimed: pick the launch shape of the SIMT kernel for this space
-        tuned_ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, C, S, nvec, sdt, stream)
-    for _ in range(args.warmup):
-        sp.sigma(C, S, stream=stream, dtype=sdt)
-    torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for k in range(args.steps):
-        sp.sigma(C, S, stream=stream, dtype=sdt)
-        ev[k + 1].record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
+    rec, sp, C, S, sdt = _sigma_leg(tb, ctx, wl, args.dtype, nvec, args.steps, args.warmup, dev, stream,
+                                    autotune=not args.no_autotune, clocks=True, count_alpha=args.count_alpha)
+    ms_step = rec["ms_per_step"]
     if dist:
         dist.barrier()
-        total_ms = max_over_ranks(total_ms, dist, dev)
-    ms_step = total_ms / args.steps
+        ms_step = max_over_ranks(ms_step, dist, dev)
     value = replica_throughput(ws, nvec * sp.ndet, ms_step * 1e-3) / 1e9
+    del S
 
-    # roofline of the fused sigma kernel (one launch per step for nvec <= 4)
-    counts = sp.counts()  # after tuning: carries the chosen launch shape
-    if sdt in (tb.TBSCI_F64, tb.TBSCI_F32):
-        nv_used = counts["tuned_nv"][0 if sdt == tb.TBSCI_F64 else 1] or min(nvec, 4)
-        launches_per_step = (nvec + nv_used - 1) // nv_used
-    flops_step = 2.0 * counts["nnz"] * nvec
-    kern_ms = statistics.mean(per_step) / launches_per_step
-    achieved = flops_step / launches_per_step / (kern_ms * 1e-3) / 1e12
-    peak = FP64_NOMINAL_TFLOPS if args.dtype == "f64" else FP32_NOMINAL_TFLOPS
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": (_traffic(args.dtype, counts["tuned_threads"][0], counts["tuned_nv"][0],
-                                     counts["tuned_stage"][0], nvec) if args.dtype == "f64" else None),
-                "kernel": "k_sigma (fused, all classes)",
-                "peak_source": "nominal %s ALU (152 SMs, 2070 MHz)" % ("FP64" if args.dtype == "f64" else "FP32"),
-                "algorithmic_flops_per_launch": flops_step / launches_per_step}
+    e2e, hc = None, None
+    if args.dtype == "f64" and args.e2e_steps > 0:
+        e2e, hc = _e2e_leg(tb, ctx, sp, C, nvec, args.e2e_steps, ws)
+    del C
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        if hc is None:
+            hc = np.ascontiguousarray(random_vectors(nvec, sp.la, sp.lb, seed=wl.seed_vec))
+        cpu = cpu_baseline(wl, nvec, C=hc.reshape(nvec, -1), count_alpha=args.count_alpha)
+    del hc
+    sp.close()
+    torch.cuda.empty_cache()
 
-    # end to end through the C ABI with pinned host buffers (FP64)
-    e2e = None
-    if args.dtype == "f64":
-        hc = torch.from_numpy(Cn).pin_memory()
-        hs = torch.empty_like(hc).pin_memory()
-        hcn, hsn = hc.numpy(), hs.numpy()
-        sp.sigma_host(hcn)  # warm the device buffers
-        tb.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, hcn, hsn, nvec)
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            tb.tbsci_sigma_host(ctx.handle, sp.ham, sp.ta, sp.tb, hcn, hsn, nvec)
-        dt = (time.perf_counter() - t0) / args.e2e_steps
-        nbytes = nvec * sp.ndet * 8
-        e2e = {"value": ws * nvec * sp.ndet / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3, "steps": args.e2e_steps,
-               "api": "tbsci_sigma_host"}
+    extra = None
+    if rank == 0 and not args.no_extra and args.workload != "sel16":
+        # the norb=16, 3,000 x 3,000 selected space (9.0M determinants, 3 vectors), FP64
+        r16, sp16, C16, S16, _ = _sigma_leg(tb, ctx, WORKLOADS["sel16"], "f64", 3, max(5, args.steps // 2),
+                                           args.warmup, dev, stream, autotune=not args.no_autotune)
+        extra = {k: r16[k] for k in ("value", "ms_per_step", "roofline", "config", "launches_per_step")}
+        extra["unit"] = UNIT
+        sp16.close()
+        del C16, S16
+        torch.cuda.empty_cache()
 
     dav = None
     if not args.no_davidson and rank == 0:
-        dav = {}
-        for mode in ("f64", "mixed"):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e, info = sp.davidson(wl.nroots, mixed=(mode == "mixed"), tol_energy=1e-9, tol_residual=1e-5)
-            dt = time.perf_counter() - t0
-            dav[mode] = {"seconds": dt, "iterations": info["iterations"], "nsigma": info["nsigma"],
-                         "nsigma_f32": info["nsigma_f32"], "energies": [float(x) for x in e],
-                         "converged": info["converged"], "seconds_sigma": info["seconds_sigma"]}
-        dav["mixed_minus_f64_max_abs"] = max(abs(a - b) for a, b in zip(dav["mixed"]["energies"],
-                                                                       dav["f64"]["energies"]))
-        dav["target"] = "time to |dE| < 1e-9 and ||r|| < 1e-5 per root (energies within 1e-8 Eh)"
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, nvec)
+        dav = _davidson_leg(tb, ctx, WORKLOADS["sel16"])
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": dict(_config(wl, nvec, args.dtype), parallelism="replicas" if ws > 1 else "single"),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "clocks": clocks, "davidson": dav,
-            "counts": counts, "setup_seconds": t_setup, "autotune_ms": tuned_ms,
-            "step_ms_min": min(per_step), "step_ms_max": max(per_step),
+            "config": dict(rec["config"], parallelism="replicas" if ws > 1 else "single"),
+            "roofline": rec["roofline"], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": rec["launches_per_step"] * args.steps,
+            "clocks": rec["clocks"], "sel16_sigma": extra, "davidson": dav,
+            "counts": rec["counts"], "setup_seconds": rec["setup_seconds"], "autotune_ms": rec["autotune_ms"],
+            "step_ms_min": rec["step_ms_min"], "step_ms_max": rec["step_ms_max"],
         }
         print(json.dumps(line), flush=True)
-    sp.close()
     ctx.close()
     if dist:
         dist.destroy_process_group()
