@@ -17,6 +17,9 @@ What it computes (each function cites the passage it follows):
   space by the spin-orbital Slater-Condon rules (Sec. II.C, Eq. 8), sigma = H.c.
 * ``davidson`` -- standard Davidson (Sec. III.A) with restart to the Ritz
   vectors when the subspace is full (Sec. III.C), in numpy FP64.
+* ``PrunedSpace`` / ``sigma_pruned`` / ``diagonal_pruned`` -- the general TBSCI
+  space D_TBSCI of Sec. II.A, Eq. 6: per alpha string w a set I_w of allowed beta
+  strings; H on it is the principal submatrix of H on the member determinants.
 
 Parity status: every function above is pinned by ``tests/test_oracle_pins.py``
 (brute-force second quantisation, closed forms, library special cases,
@@ -76,6 +79,11 @@ def _load():
             lib.orc_sigma_rows.restype = None
             lib.orc_diagonal.argtypes = [i32, P, i64, P, i64, P, P, ctypes.c_double, P, i64, P]
             lib.orc_diagonal.restype = None
+            lib.orc_sigma_pruned.argtypes = [i32, i32, i32, P, i64, P, i64, P, P, P, P, ctypes.c_double,
+                                             P, i32, P, i64, P, P, i32]
+            lib.orc_sigma_pruned.restype = None
+            lib.orc_diagonal_pruned.argtypes = [i32, P, i64, P, P, P, P, P, ctypes.c_double, P, i64, P]
+            lib.orc_diagonal_pruned.restype = None
             lib.orc_max_threads.argtypes = []
             lib.orc_max_threads.restype = i32
             _lib = lib
@@ -244,6 +252,83 @@ def hamiltonian_dense(space: Space, h, eri, ecore) -> np.ndarray:
         cols, vals = row(space, h, eri, ecore, K)
         H[K, cols] = vals
     return H
+
+
+# ---------------------------------------------------- pruned spaces (D_TBSCI)
+
+class PrunedSpace:
+    """The general TBSCI space (Sec. II.A, Eq. 6): the determinants (w, u) of a
+    TPB space with u in I_w, given as CSR ``off[la + 1]`` and ascending beta
+    indices ``cols``. Determinant (w, u) has the compressed index
+    ``off[w] + position of u in I_w``."""
+
+    def __init__(self, space: Space, off, cols):
+        self.space = space
+        self.off = np.ascontiguousarray(off, dtype=np.int64)
+        self.cols = np.ascontiguousarray(cols, dtype=np.int32)
+        if len(self.off) != space.la + 1 or self.off[0] != 0 or np.any(np.diff(self.off) < 0):
+            raise ValueError("off must be a CSR offset array of length la + 1")
+        if self.off[-1] != len(self.cols):
+            raise ValueError("off[la] must equal len(cols)")
+        for w in range(space.la):
+            row = self.cols[self.off[w]:self.off[w + 1]]
+            if len(row) and (row.min() < 0 or row.max() >= space.lb or np.any(np.diff(row) <= 0)):
+                raise ValueError("I_w must hold ascending beta indices inside the beta set")
+        self.ndet = int(self.off[-1])
+
+    def members(self) -> np.ndarray:
+        """TPB indices w * lb + u of the member determinants, in compressed order."""
+        w = np.repeat(np.arange(self.space.la, dtype=np.int64), np.diff(self.off))
+        return w * self.space.lb + self.cols
+
+
+def sigma_pruned(ps: PrunedSpace, h, eri, ecore, C, rows=None, nthreads: int = 0, with_bound: bool = False):
+    """sigma = H.c over a pruned space (Sec. II.A, Eq. 6; Sec. II.C, the membership
+    test of Algorithm 1 written as a lookup in I_w). ``C``: ``[nvec, ndet]``
+    compressed; returns ``[nvec, nrows]`` (and ``sum_J |H_KJ||c_J|``)."""
+    lib = _load()
+    h, eri = _ham_arrays(h, eri)
+    sp = ps.space
+    C = np.ascontiguousarray(np.asarray(C, dtype=np.float64).reshape(-1, ps.ndet))
+    nvec = C.shape[0]
+    rows_arr = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nrows = ps.ndet if rows is None else len(rows_arr)
+    out = np.zeros((nvec, nrows))
+    bound = np.zeros((nvec, nrows)) if with_bound else None
+    lib.orc_sigma_pruned(sp.norb, sp.na, sp.nb, _ptr(sp.sa), sp.la, _ptr(sp.sb), sp.lb, _ptr(ps.off),
+                         _ptr(ps.cols), _ptr(h), _ptr(eri), float(ecore), _ptr(C), nvec, _ptr(rows_arr), nrows,
+                         _ptr(out), _ptr(bound), int(nthreads))
+    return (out, bound) if with_bound else out
+
+
+def diagonal_pruned(ps: PrunedSpace, h, eri, ecore, rows=None) -> np.ndarray:
+    """H_KK of the member determinants (compressed order)."""
+    lib = _load()
+    h, eri = _ham_arrays(h, eri)
+    sp = ps.space
+    rows_arr = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nrows = ps.ndet if rows is None else len(rows_arr)
+    out = np.zeros(nrows)
+    lib.orc_diagonal_pruned(sp.norb, _ptr(sp.sa), sp.la, _ptr(sp.sb), _ptr(ps.off), _ptr(ps.cols), _ptr(h),
+                            _ptr(eri), float(ecore), _ptr(rows_arr), nrows, _ptr(out))
+    return out
+
+
+def hamiltonian_dense_pruned(ps: PrunedSpace, h, eri, ecore) -> np.ndarray:
+    """Dense H over a pruned space (small spaces only), column by column from
+    sigma of unit vectors."""
+    E = np.eye(ps.ndet)
+    return sigma_pruned(ps, h, eri, ecore, E).T.copy()
+
+
+def solve_pruned(ps: PrunedSpace, h, eri, ecore, nroots, nthreads=0, **kw):
+    """Lowest eigenpairs of H on a pruned space: oracle sigma + oracle Davidson."""
+    d = diagonal_pruned(ps, h, eri, ecore)
+
+    def apply_h(V):
+        return sigma_pruned(ps, h, eri, ecore, V, nthreads=nthreads)
+
+    return davidson(apply_h, d, nroots, **kw)
 
 
 # --------------------------------------------------------------- Davidson

@@ -430,6 +430,102 @@ void orc_sigma_rows(int n, int na, int nb, const uint64_t *sa, int64_t la,
     }
 }
 
+/* ----------------------------------------------- pruned spaces (D_TBSCI) */
+
+/* A pruned space (Sec. II.A, Eq. 6): for each alpha string w the ascending list
+ * of allowed beta indices I_w = cols[off[w] .. off[w+1]). Determinant (w, u)
+ * with u in I_w has the compressed index off[w] + (position of u in I_w). */
+typedef struct {
+    const int64_t *off; /* [la + 1] */
+    const int32_t *cols;
+    int64_t la, nd;
+} pruned_t;
+
+/* compressed index of (w, u); -1 when u is not in I_w (binary search) */
+static int64_t pruned_index(const pruned_t *pr, int64_t w, int64_t u)
+{
+    int64_t lo = pr->off[w], hi = pr->off[w + 1] - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (pr->cols[mid] == u) return mid;
+        if (pr->cols[mid] < u) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* alpha string of compressed index K: the last w with off[w] <= K */
+static int64_t pruned_row_of(const pruned_t *pr, int64_t K)
+{
+    int64_t lo = 0, hi = pr->la - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo + 1) / 2;
+        if (pr->off[mid] <= K) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* sigma over a pruned space: for every listed compressed row K (all when rows
+ * is NULL, nrows = nd), sigma_K = sum_{J in D} H_KJ c_J. The elements are the
+ * full TPB row of the Slater-Condon rules, kept when the coupled determinant is
+ * a member (H restricted to D is the principal submatrix of H on D's
+ * determinants). C is [nvec][nd], out / bound [nvec][nrows]. */
+void orc_sigma_pruned(int n, int na, int nb, const uint64_t *sa, int64_t la, const uint64_t *sb, int64_t lb,
+                      const int64_t *off, const int32_t *pcols, const double *h, const double *eri, double ecore,
+                      const double *C, int nvec, const int64_t *rows, int64_t nrows, double *out, double *bound,
+                      int nthreads)
+{
+    ham_t H = {n, h, eri, ecore};
+    space_t sp = {sa, sb, la, lb};
+    pruned_t pr = {off, pcols, la, off[la]};
+    int64_t cap = orc_row_capacity(n, na, nb);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        int64_t *cols = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+        double *vals = (double *)malloc((size_t)cap * sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < nrows; r++) {
+            int64_t Kp = rows ? rows[r] : r;
+            int64_t w = pruned_row_of(&pr, Kp);
+            int64_t K = w * lb + pcols[Kp];
+            int64_t m = row_elements(&H, &sp, K, cols, vals);
+            for (int v = 0; v < nvec; v++) {
+                const double *c = C + (size_t)v * pr.nd;
+                double acc = 0.0, ab = 0.0;
+                for (int64_t t = 0; t < m; t++) {
+                    int64_t Jp = pruned_index(&pr, cols[t] / lb, cols[t] % lb);
+                    if (Jp < 0) continue;
+                    acc += vals[t] * c[Jp];
+                    ab += (vals[t] < 0 ? -vals[t] : vals[t]) * (c[Jp] < 0 ? -c[Jp] : c[Jp]);
+                }
+                out[(size_t)v * nrows + r] = acc;
+                if (bound) bound[(size_t)v * nrows + r] = ab;
+            }
+        }
+        free(cols);
+        free(vals);
+    }
+}
+
+/* Diagonal of a pruned space for the listed compressed rows (all when rows is NULL). */
+void orc_diagonal_pruned(int n, const uint64_t *sa, int64_t la, const uint64_t *sb, const int64_t *off,
+                         const int32_t *pcols, const double *h, const double *eri, double ecore,
+                         const int64_t *rows, int64_t nrows, double *out)
+{
+    ham_t H = {n, h, eri, ecore};
+    pruned_t pr = {off, pcols, la, off[la]};
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nrows; r++) {
+        int64_t Kp = rows ? rows[r] : r;
+        det_t d = {sa[pruned_row_of(&pr, Kp)], sb[pcols[Kp]]};
+        out[r] = diag_element(&H, &d);
+    }
+}
+
 /* Diagonal H_KK for the listed rows (all when rows is NULL). */
 void orc_diagonal(int n, const uint64_t *sa, int64_t la, const uint64_t *sb, int64_t lb,
                   const double *h, const double *eri, double ecore, const int64_t *rows,

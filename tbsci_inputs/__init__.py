@@ -38,6 +38,8 @@ __all__ = [
     "Workload",
     "WORKLOADS",
     "serving_stream",
+    "excitation_level",
+    "prune_by_total_level",
 ]
 
 
@@ -132,6 +134,31 @@ def selected_strings(norb: int, nelec: int, count: int, seed: int, shuffle: bool
     if shuffle:
         arr = arr[rng.permutation(len(arr))]
     return arr
+
+
+def excitation_level(strings, nelec: int) -> np.ndarray:
+    """Number of electrons of each string outside the aufbau orbitals 0..nelec-1."""
+    ref = np.uint64(reference_string(nelec))
+    s = np.asarray(strings, dtype=np.uint64) & ~ref
+    out = np.zeros(len(s), dtype=np.int64)
+    for b in range(64):
+        out += ((s >> np.uint64(b)) & np.uint64(1)).astype(np.int64)
+    return out
+
+
+def prune_by_total_level(alpha_sorted, beta_sorted, nalpha: int, nbeta: int, max_level: int):
+    """A determinant-level selection inside a TPB space (the general space of
+    Sec. II.A, Eq. 6): keep (w, u) when the alpha and beta excitation levels sum to
+    at most ``max_level``. Inputs are the SORTED string sets; returns the CSR
+    ``(off[la + 1], cols)`` of allowed beta indices per alpha string."""
+    la_lev = excitation_level(alpha_sorted, nalpha)
+    lb_lev = excitation_level(beta_sorted, nbeta)
+    cols, off = [], [0]
+    for w in range(len(la_lev)):
+        keep = np.nonzero(lb_lev + la_lev[w] <= max_level)[0].astype(np.int32)
+        cols.append(keep)
+        off.append(off[-1] + len(keep))
+    return np.array(off, dtype=np.int64), (np.concatenate(cols) if cols else np.zeros(0, dtype=np.int32))
 
 
 def random_vectors(nvec: int, la: int, lb: int, seed: int, dtype=np.float64) -> np.ndarray:

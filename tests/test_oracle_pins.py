@@ -418,3 +418,97 @@ def test_davidson_finds_a_transpose_antisymmetric_ground_state():
         e, X, info = oracle.davidson(lambda V: V @ H.T, d, nroots)
         assert info["converged"]
         assert np.max(np.abs(e - w[:nroots])) < 1e-8
+
+
+# ------------------------------------------------- pruned spaces (D_TBSCI)
+
+def _pruned_case(n, na, nb, acnt, bcnt, max_level, seed):
+    from tbsci_inputs import prune_by_total_level
+    h, eri, _ = synth_hamiltonian(n, seed=seed)
+    asel = None if acnt is None else selected_strings(n, na, acnt, seed + 1)
+    bsel = None if bcnt is None else selected_strings(n, nb, bcnt, seed + 2)
+    sp = oracle.make_space(n, na, nb, asel, bsel)
+    off, cols = prune_by_total_level(sp.sa, sp.sb, na, nb, max_level)
+    return sp, oracle.PrunedSpace(sp, off, cols), h, eri
+
+
+def test_pruned_h_is_the_brute_force_h_on_the_members():
+    """Second quantisation (independent of the Slater-Condon rules) on the
+    member determinants only: the pruned oracle's dense H equals it."""
+    n, na, nb = 5, 2, 2
+    sp, ps, h, eri = _pruned_case(n, na, nb, None, None, 2, seed=71)
+    assert 0 < ps.ndet < sp.ndet
+    H = oracle.hamiltonian_dense_pruned(ps, h, eri, 0.4)
+    Hb = brute_force_h(n, sp.sa, sp.sb, h, eri, 0.4)
+    m = ps.members()
+    assert np.max(np.abs(H - Hb[np.ix_(m, m)])) < 1e-12
+
+
+@pytest.mark.parametrize("n,na,nb,acnt,bcnt,lev", [(8, 4, 4, None, None, 3), (8, 4, 3, 40, None, 2),
+                                                   (10, 5, 5, 120, 130, 4)])
+def test_pruned_sigma_is_the_principal_submatrix_product(n, na, nb, acnt, bcnt, lev):
+    """H restricted to D_TBSCI is the principal submatrix of H on its
+    determinants: sigma_pruned(c) equals H_TPB applied to c zero-padded outside
+    the space, read back at the members."""
+    sp, ps, h, eri = _pruned_case(n, na, nb, acnt, bcnt, lev, seed=81 + n)
+    assert 0 < ps.ndet < sp.ndet
+    rng = np.random.default_rng(3)
+    c = rng.standard_normal((2, ps.ndet))
+    full = np.zeros((2, sp.ndet))
+    full[:, ps.members()] = c
+    want = oracle.sigma(sp, h, eri, 0.1, full)[:, ps.members()]
+    got, bound = oracle.sigma_pruned(ps, h, eri, 0.1, c, with_bound=True)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(bound)
+    assert np.allclose(oracle.diagonal_pruned(ps, h, eri, 0.1), oracle.diagonal(sp, h, eri, 0.1)[ps.members()],
+                       atol=0, rtol=0)
+
+
+def test_pruning_nothing_is_the_tpb_space():
+    """I_w = every beta string: the pruned sigma is the TPB sigma bit for bit."""
+    n, na, nb = 8, 4, 4
+    h, eri, _ = synth_hamiltonian(n, seed=91)
+    sp = oracle.make_space(n, na, nb, selected_strings(n, na, 50, 92), None)
+    off = np.arange(sp.la + 1, dtype=np.int64) * sp.lb
+    cols = np.tile(np.arange(sp.lb, dtype=np.int32), sp.la)
+    ps = oracle.PrunedSpace(sp, off, cols)
+    c = np.random.default_rng(4).standard_normal((1, sp.ndet))
+    assert np.array_equal(oracle.sigma_pruned(ps, h, eri, 0.0, c), oracle.sigma(sp, h, eri, 0.0, c))
+
+
+def test_pruned_spectrum_interlaces_and_is_variational():
+    """Cauchy interlacing for a principal submatrix of size m of an N x N
+    symmetric H: lambda_k(H) <= lambda_k(H_D) <= lambda_{k+N-m}(H); nested
+    prunings give non-increasing ground-state energies (variational, Sec. II.A)."""
+    n, na, nb = 8, 4, 4
+    h, eri, _ = synth_hamiltonian(n, seed=93)
+    sp = oracle.make_space(n, na, nb)
+    w = np.linalg.eigvalsh(oracle.hamiltonian_dense(sp, h, eri, 0.0))
+    from tbsci_inputs import prune_by_total_level
+    e0 = []
+    for lev in (2, 4, 6, 8):
+        off, cols = prune_by_total_level(sp.sa, sp.sb, na, nb, lev)
+        ps = oracle.PrunedSpace(sp, off, cols)
+        wd = np.linalg.eigvalsh(oracle.hamiltonian_dense_pruned(ps, h, eri, 0.0))
+        m, N = ps.ndet, sp.ndet
+        assert np.all(w[:m] <= wd + 1e-10) and np.all(wd <= w[N - m:] + 1e-10)
+        e0.append(wd[0])
+    assert all(a >= b - 1e-12 for a, b in zip(e0, e0[1:]))
+    assert abs(e0[-1] - w[0]) < 1e-10  # level 8 keeps every determinant
+
+
+def test_pruned_space_validation():
+    sp = oracle.make_space(6, 3, 3)
+    with pytest.raises(ValueError):
+        oracle.PrunedSpace(sp, np.zeros(sp.la, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    off = np.zeros(sp.la + 1, dtype=np.int64)
+    off[1:] = 2
+    with pytest.raises(ValueError):  # descending beta indices
+        oracle.PrunedSpace(sp, off, np.array([3, 1], dtype=np.int32))
+
+
+def test_pruned_davidson_matches_dense():
+    n, na, nb = 8, 4, 4
+    sp, ps, h, eri = _pruned_case(n, na, nb, None, None, 3, seed=95)
+    w = np.linalg.eigvalsh(oracle.hamiltonian_dense_pruned(ps, h, eri, 0.0))
+    e, _, info = oracle.solve_pruned(ps, h, eri, 0.0, 3)
+    assert info["converged"] and np.max(np.abs(e - w[:3])) < 1e-8
