@@ -331,6 +331,41 @@ tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *
                             int nroots, const tbsci_davidson_opts *opts, double *energies, double *vecs,
                             tbsci_davidson_info *info);
 
+/* --------------------------------------------------------- pruned spaces */
+
+/* The general TBSCI space D_TBSCI (Sec. II.A, Eq. 6): inside the TPB space of
+ * tables a x b, determinant (w, u) is kept when beta index u is in the set I_w
+ * of alpha string w (the membership test of Algorithm 1, Sec. II.C). I_w is
+ * given as CSR: `off` HOST [l_a + 1] (off[0] = 0, non-decreasing) and `cols`
+ * HOST [off[l_a]] with each row's beta indices strictly ascending in
+ * 0..l_b-1. Determinant (w, u) has the compressed index off[w] + (position of
+ * u in I_w); vectors on a pruned space are DEVICE arrays [nvec][off[l_a]].
+ * H on the space is the principal submatrix of H on its determinants. Arrays
+ * are copied. Errors: EINVAL (null pointers, a malformed CSR, an index out of
+ * range or not ascending), ENOMEM, ECUDA. */
+typedef struct tbsci_pruned tbsci_pruned;
+tbsci_status tbsci_pruned_create(tbsci_ctx *ctx, const tbsci_tables *a, const tbsci_tables *b, const int64_t *off,
+                                 const int32_t *cols, tbsci_pruned **out);
+tbsci_status tbsci_pruned_count(const tbsci_pruned *pr, int64_t *ndet);
+void tbsci_pruned_destroy(tbsci_pruned *pr);
+
+/* sigma = H.c on a pruned space (Sec. II.A, Eq. 6; the classes of Sec. II.C):
+ * c and sigma are compressed DEVICE arrays [nvec][ndet] of F64 or F32 (the
+ * tensor-core types run as F32 here); sigma is overwritten. Enqueued on
+ * `stream`. `pr` must come from the tables a and b. Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+tbsci_status tbsci_sigma_pruned(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                                const tbsci_pruned *pr, const void *c, void *sigma, int nvec, tbsci_dtype dtype,
+                                tbsci_stream stream);
+/* Diagonal H_KK of the pruned space into the DEVICE array diag[ndet] (FP64). */
+tbsci_status tbsci_diagonal_pruned(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                                   const tbsci_pruned *pr, double *diag, tbsci_stream stream);
+/* tbsci_davidson on a pruned space: vecs is a DEVICE array [nroots][ndet]
+ * (compressed) or NULL; options, guess and errors as tbsci_davidson. */
+tbsci_status tbsci_davidson_pruned(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
+                                   const tbsci_pruned *pr, int nroots, const tbsci_davidson_opts *opts,
+                                   double *energies, double *vecs, tbsci_davidson_info *info);
+
 /* --------------------------------------------------------------- serving */
 
 /* A request loop for many solves (no counterpart in the paper, which runs one

@@ -17,7 +17,7 @@ for _n in dir(B):
         globals()[_n] = getattr(B, _n)
 del _n
 
-__all__ = ["Context", "Space", "Server", "B"] + [n for n in dir(B) if n.startswith(("tbsci_", "TBSCI_"))]
+__all__ = ["Context", "Space", "Pruned", "Server", "B"] + [n for n in dir(B) if n.startswith(("tbsci_", "TBSCI_"))]
 
 
 class Context:
@@ -119,10 +119,63 @@ class Space:
         e, info = B.tbsci_davidson(self.ctx.handle, self.ham, self.ta, self.tb, nroots, vecs=vecs, **kw)
         return (e, info, vecs) if want_vectors else (e, info)
 
+    def prune(self, off, cols):
+        """The pruned space D_TBSCI of this space: per alpha string w the ascending
+        beta indices cols[off[w]:off[w + 1]]."""
+        return Pruned(self, off, cols)
+
     def close(self):
         for fn, h in reversed(self._handles):
             fn(h)
         self._handles = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pruned:
+    """A pruned TBSCI space inside a ``Space`` (compressed vectors [nvec, ndet])."""
+
+    def __init__(self, space: Space, off, cols):
+        self.space = space
+        self.handle = B.tbsci_pruned_create(space.ctx.handle, space.ta, space.tb, off, cols)
+        self.ndet = B.tbsci_pruned_count(self.handle)
+
+    def sigma(self, c, out=None, stream=None, dtype=None):
+        import torch
+        nvec = c.shape[0] if c.dim() == 2 else 1
+        assert c.is_cuda and c.is_contiguous() and c.numel() == nvec * self.ndet
+        if out is None:
+            out = torch.empty_like(c)
+        if dtype is None:
+            dtype = B.TBSCI_F64 if c.dtype == torch.float64 else B.TBSCI_F32
+        sp = self.space
+        B.tbsci_sigma_pruned(sp.ctx.handle, sp.ham, sp.ta, sp.tb, self.handle, c, out, nvec, dtype, stream)
+        return out
+
+    def diagonal(self, stream=None):
+        import torch
+        sp = self.space
+        d = torch.empty(self.ndet, dtype=torch.float64, device="cuda:%d" % sp.ctx.device)
+        B.tbsci_diagonal_pruned(sp.ctx.handle, sp.ham, sp.ta, sp.tb, self.handle, d, stream)
+        return d
+
+    def davidson(self, nroots, want_vectors=False, **kw):
+        import torch
+        sp = self.space
+        vecs = None
+        if want_vectors:
+            vecs = torch.empty((nroots, self.ndet), dtype=torch.float64, device="cuda:%d" % sp.ctx.device)
+        e, info = B.tbsci_davidson_pruned(sp.ctx.handle, sp.ham, sp.ta, sp.tb, self.handle, nroots, vecs=vecs, **kw)
+        return (e, info, vecs) if want_vectors else (e, info)
+
+    def close(self):
+        if self.handle is not None:
+            B.tbsci_pruned_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

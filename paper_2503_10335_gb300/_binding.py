@@ -30,6 +30,8 @@ EXPORTS = [
     "tbsci_overlap_noalloc", "tbsci_server_create", "tbsci_submit", "tbsci_poll", "tbsci_server_load",
     "tbsci_server_destroy", "tbsci_sigma_autotune", "tbsci_tune_cache_save", "tbsci_tune_cache_load",
     "tbsci_tune_cache_size", "tbsci_create_ex", "tbsci_hbm_used",
+    "tbsci_pruned_create", "tbsci_pruned_count", "tbsci_pruned_destroy", "tbsci_sigma_pruned",
+    "tbsci_diagonal_pruned", "tbsci_davidson_pruned",
 ]
 
 
@@ -140,6 +142,13 @@ def load(path: str | None = None):
         "tbsci_create": ([I, PP], I),
         "tbsci_create_ex": ([ctypes.POINTER(Options), PP], I),
         "tbsci_hbm_used": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
+        "tbsci_pruned_create": ([P, P, P, P, P, PP], I),
+        "tbsci_pruned_count": ([P, ctypes.POINTER(I64)], I),
+        "tbsci_pruned_destroy": ([P], None),
+        "tbsci_sigma_pruned": ([P, P, P, P, P, P, P, I, I, P], I),
+        "tbsci_diagonal_pruned": ([P, P, P, P, P, P, P], I),
+        "tbsci_davidson_pruned": ([P, P, P, P, P, I, ctypes.POINTER(DavidsonOpts), P, P,
+                                   ctypes.POINTER(DavidsonInfo)], I),
         "tbsci_destroy": ([P], None),
         "tbsci_last_error": ([P], ctypes.c_char_p),
         "tbsci_status_string": ([I], ctypes.c_char_p),
@@ -373,6 +382,55 @@ def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max
     e = np.zeros(nroots)
     info = DavidsonInfo()
     st = load().tbsci_davidson(ctx, ham, ta, tb, nroots, ctypes.byref(o), _ptr(e), _ptr(vecs), ctypes.byref(info))
+    if check or st not in (TBSCI_OK, TBSCI_ENOCONV):
+        _check(ctx, st)
+    d = info.as_dict()
+    d["status"] = st
+    return e, d
+
+
+def tbsci_pruned_create(ctx, ta, tb, off, cols):
+    """Pruned space from host CSR arrays (off [la + 1], cols [off[la]])."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(ctx, load().tbsci_pruned_create(ctx, ta, tb, _ptr(off), _ptr(cols) if len(cols) else None,
+                                           ctypes.byref(out)))
+    return out
+
+
+def tbsci_pruned_count(pr) -> int:
+    n = ctypes.c_int64()
+    st = load().tbsci_pruned_count(pr, ctypes.byref(n))
+    if st:
+        raise TbsciError(st, "pruned_count")
+    return n.value
+
+
+def tbsci_pruned_destroy(pr):
+    load().tbsci_pruned_destroy(pr)
+
+
+def tbsci_sigma_pruned(ctx, ham, ta, tb, pr, c, sigma, nvec: int, dtype: int = TBSCI_F64, stream=None):
+    _check(ctx, load().tbsci_sigma_pruned(ctx, ham, ta, tb, pr, _ptr(c), _ptr(sigma), int(nvec), int(dtype),
+                                          _stream(stream)))
+
+
+def tbsci_diagonal_pruned(ctx, ham, ta, tb, pr, diag, stream=None):
+    _check(ctx, load().tbsci_diagonal_pruned(ctx, ham, ta, tb, pr, _ptr(diag), _stream(stream)))
+
+
+def tbsci_davidson_pruned(ctx, ham, ta, tb, pr, nroots: int, vecs=None, max_subspace=0, max_iter=0,
+                          tol_energy=0.0, tol_residual=0.0, mixed=False, tol_mixed_residual=0.0, stream=None,
+                          check=True, restart_keep=0, basis_f32=False, max_subspace_refine=0):
+    """tbsci_davidson on a pruned space; ``vecs``: device FP64 [nroots][ndet] or None."""
+    o = DavidsonOpts(max_subspace, restart_keep, max_iter, tol_energy, tol_residual, int(mixed),
+                     tol_mixed_residual,
+                     None if stream is None else _stream(stream).value, int(basis_f32), max_subspace_refine)
+    e = np.zeros(nroots)
+    info = DavidsonInfo()
+    st = load().tbsci_davidson_pruned(ctx, ham, ta, tb, pr, nroots, ctypes.byref(o), _ptr(e), _ptr(vecs),
+                                      ctypes.byref(info))
     if check or st not in (TBSCI_OK, TBSCI_ENOCONV):
         _check(ctx, st)
     d = info.as_dict()

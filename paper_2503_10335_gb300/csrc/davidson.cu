@@ -373,6 +373,7 @@ struct DavEngine {
     tbsci_ctx *ctx = nullptr;
     tbsci_ham *ham = nullptr;
     Plan *plan = nullptr;
+    const tbsci_pruned *pr = nullptr;  // set: the solve runs on this pruned subspace
     cudaStream_t st = nullptr;
     bool own_stream = false;
     cudaEvent_t evt = nullptr;
@@ -486,7 +487,7 @@ struct DavEngine {
         TB_CHECK(ctx, m_max >= nroots + 1 && m_max <= kMaxBasis, TBSCI_EINVAL,
                  "max_subspace must be in nroots+1..128");
         TB_CHECK(ctx, keep >= nroots && keep < m_max, TBSCI_EINVAL, "restart_keep must be in nroots..max_subspace-1");
-        N = plan->A.l * plan->B.l;
+        N = pr ? pr->nd : plan->A.l * plan->B.l;
         TB_CHECK(ctx, N >= nroots, TBSCI_EINVAL, "space has fewer determinants than roots");
         if (opt.stream) {
             st = (cudaStream_t)opt.stream;
@@ -543,7 +544,8 @@ struct DavEngine {
         theta_prev.assign(nroots, INFINITY);
         rnorm.assign(nroots, INFINITY);
         e32.assign(nroots, 0.0);
-        TB_TRY(diagonal_launch(ctx, ham, plan, diag.p, st));
+        if (pr) TB_TRY(pruned_diagonal_launch(ctx, ham, plan, pr, diag.p, st));
+        else TB_TRY(diagonal_launch(ctx, ham, plan, diag.p, st));
         // guess: unit vectors at the nroots lowest (H_KK, K), each mixed with the next
         // four lowest determinants so that every symmetry sector is present
         const int extra = (int)std::min<int64_t>(4, N - nroots);
@@ -918,10 +920,11 @@ struct DavEngine {
 };
 
 tbsci_status engine_create(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
-                           DavEngine **out) {
+                           DavEngine **out, const tbsci_pruned *pr) {
     tbsci_davidson_opts opt{};
     if (o) opt = *o;
     auto e = std::make_unique<DavEngine>();
+    e->pr = pr;
     TB_TRY(e->init(ctx, ham, plan, nroots, opt));
     *out = e.release();
     return TBSCI_OK;
@@ -962,12 +965,12 @@ size_t engine_device_bytes(int64_t N, int nroots, const tbsci_davidson_opts *o) 
 }
 
 tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
-                          double *energies, double *vecs, tbsci_davidson_info *info) {
+                          double *energies, double *vecs, tbsci_davidson_info *info, const tbsci_pruned *pr) {
     tbsci_davidson_opts opt{};
     if (o) opt = *o;
     if (!opt.stream) opt.stream = (tbsci_stream)ctx->stream;
     DavEngine *raw = nullptr;
-    TB_TRY(engine_create(ctx, ham, plan, nroots, &opt, &raw));
+    TB_TRY(engine_create(ctx, ham, plan, nroots, &opt, &raw, pr));
     std::unique_ptr<DavEngine> e(raw);
     cudaEvent_t s0, s1;
     TB_CUDA(ctx, cudaEventCreate(&s0));
@@ -981,7 +984,8 @@ tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots
         tbsci_dtype dt;
         if (e->wants_sigma(&c, &s, &k, &dt)) {
             cudaEventRecord(s0, e->st);
-            st = sigma_launch(ctx, ham, plan, c, s, k, dt, e->st);
+            st = pr ? pruned_sigma_launch(ctx, ham, plan, pr, c, s, k, dt, e->st)
+                    : sigma_launch(ctx, ham, plan, c, s, k, dt, e->st);
             if (st != TBSCI_OK) break;
             cudaEventRecord(s1, e->st);
             st = e->sigma_done();

@@ -153,6 +153,21 @@ struct SpinPlan {
     std::vector<int64_t> h_soff, h_doff;
 };
 
+// Beta single links of one column order split by the column part their target
+// lies in (part p = columns [p W, (p + 1) W)): per slice of 32 columns and part,
+// a sliced-ELL block (offset, width) whose padding entries point at the part's
+// first column with a zero coefficient. Used when a c row does not fit in
+// shared memory and is staged one part at a time.
+struct PartLayout {
+    int P = 0;
+    int64_t W = 0;
+    DevBuf<int64_t> off;   // [nslices * P]
+    DevBuf<int32_t> w;     // [nslices * P]
+    DevBuf<int2> ci;       // {target, 2 * pair + (sign < 0)}
+    DevBuf<double> val;    // same-spin string-Hamiltonian value
+    DevBuf<float> valf;
+};
+
 struct Plan {
     uint64_t ida = 0, idb = 0;
     int norb = 0, npair = 0;
@@ -184,11 +199,29 @@ struct Plan {
     int tune_threads[2] = {0, 0}, tune_nv[2] = {0, 0}, tune_stage[2] = {0, 0};
     // autotuned SIMT pass of the tensor-core sigma types (shared-memory mode, threads; 0 = default)
     int tune_rest_mode = 0, tune_rest_threads = 0;
+    // split path for rows longer than shared memory: part layouts by part count,
+    // and the transposed c / sigma scratch of the beta-double class
+    std::vector<std::unique_ptr<PartLayout>> parts;
+    DevBuf<unsigned char> d_trans;
+    DevBuf<int32_t> d_ipermb;  // inverse of d_permb
     tbsci_sigma_counts counts{};
     size_t charged = 0;  // device bytes counted against the context's budget
 };
 
 }  // namespace tbsci
+
+// A pruned TBSCI space (Sec. II.A, Eq. 6): per alpha string w the ascending
+// beta indices I_w, CSR off[la + 1] / cols[nd]; compressed vectors [nd].
+struct tbsci_pruned {
+    tbsci_ctx *ctx = nullptr;
+    uint64_t ida = 0, idb = 0;  // the tables of the TPB space it is taken from
+    int64_t la = 0, lb = 0, nd = 0;
+    tbsci::DevBuf<int64_t> d_off;
+    tbsci::DevBuf<int32_t> d_cols;
+    tbsci::DevBuf<int32_t> d_rows;  // alpha rows ordered by work (descending)
+    std::vector<int64_t> h_off;
+    size_t charged = 0;
+};
 
 struct tbsci_ham {
     tbsci_ctx *ctx = nullptr;
@@ -250,6 +283,12 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
                                int nvec, cudaStream_t st, int mode = -1, int threads = 0,
                                const int32_t *rows = nullptr, int64_t nrows = 0);
+// sigma_split.cu: sigma for rows longer than shared memory (column parts + the
+// same-spin double classes as column-tiled products); see the file head
+int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem);
+template <typename T>
+tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int extra_parts,
+                          int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode);
 // sigma_tc.cu: the diagonal, alpha singles and all alpha-beta classes on the
 // tensor cores (3xTF32 or BF16 products, FP32 accumulation), added into s.
 tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s, int nvec,
@@ -259,8 +298,9 @@ tbsci_status diagonal_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *p
 
 // davidson.cu: resumable Davidson engine (one solve) and its drivers
 struct DavEngine;
+// pr != NULL: the solve runs on that pruned subspace of the plan's space
 tbsci_status engine_create(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
-                           DavEngine **out);
+                           DavEngine **out, const tbsci_pruned *pr = nullptr);
 void engine_destroy(DavEngine *e);
 // The sigma the engine needs next: c/s device pointers ([k][N], dtype dt), on the engine stream.
 bool engine_wants_sigma(DavEngine *e, const void **c, void **s, int *k, tbsci_dtype *dt);
@@ -272,7 +312,13 @@ cudaStream_t engine_stream(const DavEngine *e);
 tbsci_status engine_results(DavEngine *e, double *energies, double *vecs, tbsci_davidson_info *info);
 size_t engine_device_bytes(int64_t N, int nroots, const tbsci_davidson_opts *o);
 tbsci_status davidson_run(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
-                          double *energies, double *vecs, tbsci_davidson_info *info);
+                          double *energies, double *vecs, tbsci_davidson_info *info,
+                          const tbsci_pruned *pr = nullptr);
+// pruned.cu: sigma and diagonal on a pruned space (compressed vectors [nvec][nd])
+tbsci_status pruned_sigma_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const tbsci_pruned *pr,
+                                 const void *c, void *s, int nvec, tbsci_dtype dt, cudaStream_t st);
+tbsci_status pruned_diagonal_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const tbsci_pruned *pr,
+                                    double *diag, cudaStream_t st);
 
 tbsci_status overlap_run(tbsci_ctx *ctx, const double *A, int ma, const double *B, int mb, int64_t n, double *S,
                          cudaStream_t st);

@@ -502,6 +502,9 @@ tbsci_status launch_typed(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, c
         if (stage < 0) stage = P->tune_stage[ti];
     }
     if (stage < 0) stage = 0;
+    if (stage >= 3)  // rows longer than shared memory: column parts + double-class products
+        return split_launch<T>(ctx, ham, const_cast<Plan *>(P), c, s, nvec, stage - 3, threads, rows, nrows, st,
+                               rows ? 1 : 0);
     if (rows) {  // grid over the sample; vstride keeps the full row count
         A.rowsa = rows;
         A.la = nrows;
@@ -729,6 +732,23 @@ tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, con
 
 }  // namespace
 
+namespace {
+
+// time of the split path's parts that do not depend on the row kernel's shape
+template <typename T>
+tbsci_status timed_split(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const T *c, T *s, cudaStream_t st,
+                         cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    TB_TRY(split_launch<T>(ctx, ham, plan, c, s, 1, 0, 512, nullptr, 0, st, 2));  // warm-up, scratch
+    TB_CUDA(ctx, cudaEventRecord(e0, st));
+    TB_TRY(split_launch<T>(ctx, ham, plan, c, s, 1, 0, 512, nullptr, 0, st, 2));
+    TB_CUDA(ctx, cudaEventRecord(e1, st));
+    TB_CUDA(ctx, cudaEventSynchronize(e1));
+    TB_CUDA(ctx, cudaEventElapsedTime(ms, e0, e1));
+    return TBSCI_OK;
+}
+
+}  // namespace
+
 tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, const void *c, void *s, int nvec,
                             tbsci_dtype dt, cudaStream_t st, double *best_ms) {
     TB_CHECK(ctx, dt == TBSCI_F64 || dt == TBSCI_F32 || dt == TBSCI_F32_TC_TF32 || dt == TBSCI_F32_TC_BF16,
@@ -824,14 +844,40 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
                 }
             }
         }
-        for (int nv = 2; nv <= nvmax && ret == TBSCI_OK; ++nv) {
-            float ms = 0.f;
-            ret = trial(nv, bt, bs, dsample.p, nrows, 1, &ms);
-            if (ret == TBSCI_OK && ms < best) {
-                best = ms;
-                bn = nv;
-            }
+        // split path (rows longer than shared memory): the row kernel is timed on
+        // the sample; the double-class products, transposes and combine do not
+        // depend on its shape, so their full-space time is measured once and
+        // added in proportion to the sample
+        if (ret == TBSCI_OK && variant(1, 0) != 0 && split_min_parts(ctx, npair, lb, ti == 0 ? 8 : 4) >= 1) {
+            float fixed = 0.f;
+            ret = dt == TBSCI_F64
+                      ? timed_split<double>(ctx, ham, plan, static_cast<const double *>(c), static_cast<double *>(s),
+                                            st, e0, e1, &fixed)
+                      : timed_split<float>(ctx, ham, plan, static_cast<const float *>(c), static_cast<float *>(s),
+                                           st, e0, e1, &fixed);
+            const float share = fixed * (float)nrows / (float)la;
+            const int split_threads[2] = {512, 1024};
+            for (int stage = 3; stage <= 4 && ret == TBSCI_OK; ++stage)
+                for (int t = 0; t < 2 && ret == TBSCI_OK; ++t) {
+                    float ms = 0.f;
+                    ret = trial(1, split_threads[t], stage, dsample.p, nrows, 1, &ms);
+                    if (ret == TBSCI_OK && ms + share < best) {
+                        best = ms + share;
+                        bt = split_threads[t];
+                        bn = 1;
+                        bs = stage;
+                    }
+                }
         }
+        if (bs < 3)
+            for (int nv = 2; nv <= nvmax && ret == TBSCI_OK; ++nv) {
+                float ms = 0.f;
+                ret = trial(nv, bt, bs, dsample.p, nrows, 1, &ms);
+                if (ret == TBSCI_OK && ms < best) {
+                    best = ms;
+                    bn = nv;
+                }
+            }
     }
     if (ret == TBSCI_OK) {
         plan->tune_threads[ti] = bt;

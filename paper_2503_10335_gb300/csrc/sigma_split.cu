@@ -1,0 +1,497 @@
+// sigma = H.c for spaces whose rows are longer than shared memory (Sec. II.B,
+// Eq. 7; the classes of Sec. II.C), as three passes that keep every gather in
+// shared memory and every read of a link table or c row inside L2:
+//
+//  K1 (k_sigma_parts): one CTA per alpha row Ia, as the fused kernel, for the
+//     diagonal, the same-spin beta singles with the alpha-beta Coulomb term
+//     ([0,0], [0,1]) and the alpha singles with their alpha-beta part ([1,0],
+//     [1,1]). The c row of each alpha term is staged in shared memory in column
+//     parts, and the beta single links of every column are split by the part
+//     their target lies in (PartLayout), so each gather reads shared memory.
+//     The sigma row accumulates in global memory (one owner thread per column).
+//  K2 (k_dbl_spmm on C): the alpha doubles ([2,0]) as a sparse x dense product
+//     sigma[Ia, :] += sum_{Ja} h(Ia, Ja) c[Ja, :], in column tiles. CTAs run
+//     tile by tile, so the CTAs in flight share one column tile of c in L2 and
+//     read each link once per tile.
+//  K3 (k_dbl_spmm on C^T): the beta doubles ([0,2]) the same way on the
+//     transposed vector, sigma^T[Ib, :] = sum_{Jb} h(Ib, Jb) c^T[Jb, :],
+//     then added back transposed.
+// Every column is summed in a fixed order: results do not depend on the launch.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace tbsci {
+
+namespace {
+
+template <typename T>
+struct SplitArgs {
+    int64_t la, lb;
+    const T *C;
+    T *S;
+    int npair, na, P;
+    int64_t W;
+    const uint64_t *stra;
+    const int64_t *a_soff;
+    const int2 *a_sci;
+    const T *a_sval;
+    const T *Ea, *Eb;
+    const T *V;   // [npair][npair]
+    const T *U1;  // [npair][lb], columns in permb order
+    const int32_t *permb, *rowsa;
+    T ecore;
+    const int64_t *poff;
+    const int32_t *pw;
+    const int2 *pci;
+    const T *pval;
+};
+
+template <typename T>
+__host__ __device__ size_t split_head_bytes(int npair) {
+    return ((2 * npair + 2) * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15);
+}
+
+template <typename T, int kThreads>
+__global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int npair = A.npair;
+    T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2 npair + 2]: coefficient by (pair, sign); last two zero
+    int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair + 2);
+    T *sC = reinterpret_cast<T *>(smem_raw + split_head_bytes<T>(npair));  // [W]: one part of a c row
+    const int64_t Ia = A.rowsa[blockIdx.x];
+    const int64_t lb = A.lb, W = A.W;
+    const int P = A.P;
+    const T *__restrict__ C = A.C;
+    T *__restrict__ S = A.S + Ia * lb;  // the row in column order: S[j] is column permb[j]
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (uint64_t s = A.stra[Ia]; s; s &= s - 1) {
+            const int p = __ffsll((long long)s) - 1;
+            sOcc[k++] = p * (p + 1) / 2 + p;
+        }
+        sV2[2 * npair] = T(0);
+        sV2[2 * npair + 1] = T(0);
+    }
+    __syncthreads();
+    const int na = A.na;
+    const T eIa = A.ecore + A.Ea[Ia];
+    const int64_t t0 = A.a_soff[Ia], t1 = A.a_soff[Ia + 1];
+    // t = t0 - 1: the Ja = Ia term; then the alpha singles of Ia
+    for (int64_t t = t0 - 1; t < t1; ++t) {
+        const bool self = t < t0;
+        int64_t Ja = Ia;
+        int pr = 0;
+        T sa = T(1), ha = T(0);
+        if (!self) {
+            const int2 ea = __ldg(A.a_sci + t);
+            Ja = ea.x;
+            pr = ea.y >> 1;
+            sa = (ea.y & 1) ? T(-1) : T(1);
+            ha = __ldg(A.a_sval + t);
+        }
+        const T *__restrict__ Crow = C + Ja * lb;
+        const T *__restrict__ Urow = A.U1 + (size_t)pr * lb;
+        for (int p = 0; p < P; ++p) {
+            const int64_t base = (int64_t)p * W, len = min(W, lb - base);
+            __syncthreads();  // the previous pass is done with sC and sV2
+            if (p == 0)
+                for (int x = threadIdx.x; x < npair; x += kThreads) {
+                    T v;
+                    if (self) {  // W_Ia[x] = sum_{q in Ia} (qq|x)
+                        v = T(0);
+                        for (int k = 0; k < na; ++k) v += A.V[(size_t)sOcc[k] * npair + x];
+                    } else {
+                        v = sa * A.V[(size_t)pr * npair + x];
+                    }
+                    sV2[2 * x] = v;
+                    sV2[2 * x + 1] = -v;
+                }
+            for (int64_t j = threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(Crow + base + j);
+            __syncthreads();
+            for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
+                const int64_t ib = A.permb[j];
+                const int64_t sl = j >> 5;
+                const int lane = (int)(j & 31);
+                T acc = (self && p == 0) ? T(0) : S[j];
+                if ((uint64_t)(ib - base) < (uint64_t)len) {  // the column's own c value is in this part
+                    T coef;
+                    if (self) {
+                        coef = eIa + __ldg(A.Eb + ib);
+                        for (int k = 0; k < na; ++k) coef += __ldg(A.U1 + (size_t)sOcc[k] * lb + j);
+                    } else {
+                        coef = ha + sa * __ldg(Urow + j);
+                    }
+                    acc += coef * sC[ib - base];
+                }
+                const int64_t o = A.poff[sl * P + p] + lane;
+                const int w = A.pw[sl * P + p];
+                const int2 *ci = A.pci + o;
+                const T *cv = A.pval + o;
+                T acc2 = T(0);
+                int k = 0;
+                for (; k + 1 < w; k += 2) {
+                    const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                    T x0 = sV2[e0.y], x1 = sV2[e1.y];
+                    if (self) {
+                        x0 += __ldg(cv + 32 * k);
+                        x1 += __ldg(cv + 32 * (k + 1));
+                    }
+                    acc += x0 * sC[e0.x - base];
+                    acc2 += x1 * sC[e1.x - base];
+                }
+                if (k < w) {
+                    const int2 e = __ldg(ci + 32 * k);
+                    T x = sV2[e.y];
+                    if (self) x += __ldg(cv + 32 * k);
+                    acc += x * sC[e.x - base];
+                }
+                S[j] = acc + acc2;
+            }
+        }
+    }
+}
+
+constexpr int kDblRows = 16;  // rows of a CTA of the double-class product
+
+// Y[r, cols of tile] (+)= sum_{t in row r} val[t] X[col[t], cols of tile]; X and Y
+// are [rows][ld]; CTA b serves column tile b / nrb and rows (b % nrb) * kDblRows..
+template <typename T, int TW>
+__global__ void __launch_bounds__(TW, 1024 / TW) k_dbl_spmm(const T *__restrict__ X, T *Y, int64_t rows, int64_t ld,
+                                                 const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                 const T *__restrict__ val, int64_t nrb, int accumulate) {
+    __shared__ int32_t sCol[TW];
+    __shared__ T sVal[TW];
+    const int64_t b = blockIdx.x;
+    const int64_t tile = b / nrb, rb = b - tile * nrb;
+    const int64_t c = tile * TW + threadIdx.x;
+    const bool ok = c < ld;
+    const int64_t r0 = rb * kDblRows, r1 = min(rows, r0 + kDblRows);
+    for (int64_t r = r0; r < r1; ++r) {
+        const int64_t t0 = off[r], t1 = off[r + 1];
+        T acc = (accumulate && ok) ? Y[r * ld + c] : T(0), acc2 = T(0);
+        for (int64_t ch = t0; ch < t1; ch += TW) {
+            const int n = (int)(t1 - ch < (int64_t)TW ? t1 - ch : (int64_t)TW);
+            __syncthreads();
+            if (threadIdx.x < n) {
+                sCol[threadIdx.x] = __ldg(col + ch + threadIdx.x);
+                sVal[threadIdx.x] = __ldg(val + ch + threadIdx.x);
+            }
+            __syncthreads();
+            if (ok) {
+                const T *__restrict__ Xc = X + c;
+                int k = 0;
+                for (; k + 3 < n; k += 4) {
+                    const T x0 = __ldg(Xc + (size_t)sCol[k] * ld), x1 = __ldg(Xc + (size_t)sCol[k + 1] * ld);
+                    const T x2 = __ldg(Xc + (size_t)sCol[k + 2] * ld), x3 = __ldg(Xc + (size_t)sCol[k + 3] * ld);
+                    acc += sVal[k] * x0;
+                    acc2 += sVal[k + 1] * x1;
+                    acc += sVal[k + 2] * x2;
+                    acc2 += sVal[k + 3] * x3;
+                }
+                for (; k < n; ++k) acc += sVal[k] * __ldg(Xc + (size_t)sCol[k] * ld);
+            }
+        }
+        if (ok) Y[r * ld + c] = acc + acc2;
+    }
+}
+
+// out[c][r] = in[r][c] (in: rows x cols), 32 x 32 tiles through shared memory
+template <typename T>
+__global__ void k_transpose(const T *__restrict__ in, T *out, int64_t rows, int64_t cols) {
+    __shared__ T tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[i][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][i];
+    }
+}
+
+// y[r][c] = p[r][ip[c]] + z[c][r]: the K1 rows (column order, ip = inverse of
+// permb) plus the transposed beta-double product (z: cols x rows)
+template <typename T>
+__global__ void k_combine(T *y, const T *__restrict__ pz, const int32_t *__restrict__ ip, const T *__restrict__ z,
+                          int64_t rows, int64_t cols) {
+    __shared__ T tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) tile[threadIdx.x][i] = z[c * rows + r];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) y[r * cols + c] = pz[r * cols + __ldg(ip + c)] + tile[i][threadIdx.x];
+    }
+}
+
+// Per-part sliced-ELL layout of the beta single links in permb order (built on the host).
+tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int nparts, PartLayout **out) {
+    for (auto &pl : P->parts)
+        if (pl->P == nparts) {
+            *out = pl.get();
+            return TBSCI_OK;
+        }
+    const int64_t lb = P->B.l, nsl = (lb + 31) / 32;
+    const int64_t W = (lb + nparts - 1) / nparts;
+    const int64_t ns = P->B.h_soff.empty() ? 0 : P->B.h_soff[lb];
+    std::vector<int2> sci(ns);
+    std::vector<double> sval(ns);
+    std::vector<int32_t> perm(lb);
+    if (ns) {
+        TB_CUDA(ctx, cudaMemcpy(sci.data(), P->B.d_sci.p, ns * sizeof(int2), cudaMemcpyDeviceToHost));
+        TB_CUDA(ctx, cudaMemcpy(sval.data(), P->B.d_sval.p, ns * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if (lb) TB_CUDA(ctx, cudaMemcpy(perm.data(), P->d_permb.p, lb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const std::vector<int64_t> &off = P->B.h_soff;
+    std::vector<int64_t> loff((size_t)nsl * nparts);
+    std::vector<int32_t> lw((size_t)nsl * nparts);
+    int64_t total = 0;
+    std::vector<int32_t> cnt(32 * (size_t)nparts);
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int lane = 0; lane < 32; ++lane) {
+            const int64_t j = sl * 32 + lane;
+            if (j >= lb) break;
+            const int64_t ib = perm[j];
+            for (int64_t t = off[ib]; t < off[ib + 1]; ++t) ++cnt[lane * nparts + sci[t].x / W];
+        }
+        for (int p = 0; p < nparts; ++p) {
+            int32_t w = 0;
+            for (int lane = 0; lane < 32; ++lane) w = std::max(w, cnt[lane * nparts + p]);
+            loff[sl * nparts + p] = total;
+            lw[sl * nparts + p] = w;
+            total += 32 * (int64_t)w;
+        }
+    }
+    const int zero_idx = 2 * ham->npair;
+    std::vector<int2> ci(std::max<int64_t>(total, 1));
+    std::vector<double> v(std::max<int64_t>(total, 1), 0.0);
+    std::vector<float> vf(std::max<int64_t>(total, 1), 0.f);
+    std::vector<int32_t> fill(32 * (size_t)nparts);
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+        std::fill(fill.begin(), fill.end(), 0);
+        for (int lane = 0; lane < 32; ++lane) {
+            const int64_t j = sl * 32 + lane;
+            if (j < lb) {
+                const int64_t ib = perm[j];
+                for (int64_t t = off[ib]; t < off[ib + 1]; ++t) {
+                    const int p = (int)(sci[t].x / W);
+                    const int64_t pos = loff[sl * nparts + p] + 32 * (int64_t)fill[lane * nparts + p]++ + lane;
+                    ci[pos] = sci[t];
+                    v[pos] = sval[t];
+                    vf[pos] = (float)sval[t];
+                }
+            }
+            for (int p = 0; p < nparts; ++p)  // padding: the part's first column, zero coefficient
+                for (int k = fill[lane * nparts + p]; k < lw[sl * nparts + p]; ++k)
+                    ci[loff[sl * nparts + p] + 32 * (int64_t)k + lane] = make_int2((int)(p * W), zero_idx);
+        }
+    }
+    auto pl = std::make_unique<PartLayout>();
+    pl->P = nparts;
+    pl->W = W;
+    const size_t bytes = loff.size() * 12 + ci.size() * (sizeof(int2) + 12);
+    TB_TRY(charge(ctx, bytes, "column-part link layout"));
+    cudaError_t e = pl->off.alloc(loff.size());
+    if (e == cudaSuccess) e = pl->w.alloc(lw.size());
+    if (e == cudaSuccess) e = pl->ci.alloc(ci.size());
+    if (e == cudaSuccess) e = pl->val.alloc(v.size());
+    if (e == cudaSuccess) e = pl->valf.alloc(vf.size());
+    if (e == cudaSuccess && !loff.empty())
+        e = cudaMemcpy(pl->off.p, loff.data(), loff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !lw.empty())
+        e = cudaMemcpy(pl->w.p, lw.data(), lw.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->ci.p, ci.data(), ci.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->val.p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->valf.p, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        uncharge(ctx, bytes);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA,
+                    std::string("column-part link layout: ") + cudaGetErrorString(e));
+    }
+    P->charged += bytes;
+    *out = pl.get();
+    P->parts.push_back(std::move(pl));
+    return TBSCI_OK;
+}
+
+template <typename T, int TH>
+tbsci_status launch_parts_th(tbsci_ctx *ctx, const SplitArgs<T> &A, size_t smem, cudaStream_t st) {
+    auto k = k_sigma_parts<T, TH>;
+    TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<(unsigned)A.la, TH, smem, st>>>(A);
+    TB_CUDA(ctx, cudaGetLastError());
+    return TBSCI_OK;
+}
+
+template <typename T>
+constexpr int dbl_tile() { return sizeof(T) == 8 ? 128 : 256; }
+
+template <typename T>
+tbsci_status launch_dbl(tbsci_ctx *ctx, const T *X, T *Y, int64_t rows, int64_t ld, const int64_t *off,
+                        const int32_t *col, const T *val, bool accumulate, cudaStream_t st) {
+    if (rows == 0 || ld == 0) return TBSCI_OK;
+    constexpr int TW = dbl_tile<T>();
+    const int64_t nrb = (rows + kDblRows - 1) / kDblRows, ntiles = (ld + TW - 1) / TW;
+    TB_CHECK(ctx, nrb * ntiles <= INT32_MAX, TBSCI_EINVAL, "double-class product: grid too large");
+    k_dbl_spmm<T, TW><<<(unsigned)(nrb * ntiles), TW, 0, st>>>(X, Y, rows, ld, off, col, val, nrb, accumulate ? 1 : 0);
+    TB_CUDA(ctx, cudaGetLastError());
+    return TBSCI_OK;
+}
+
+template <typename T>
+SplitArgs<T> split_args(const tbsci_ham *ham, const Plan *P, const PartLayout *pl);
+
+template <>
+SplitArgs<double> split_args<double>(const tbsci_ham *ham, const Plan *P, const PartLayout *pl) {
+    SplitArgs<double> A{};
+    A.la = P->A.l;
+    A.lb = P->B.l;
+    A.npair = P->npair;
+    A.na = P->A.nelec;
+    A.P = pl->P;
+    A.W = pl->W;
+    A.stra = P->A.d_str;
+    A.a_soff = P->A.d_soff;
+    A.a_sci = P->A.d_sci.p;
+    A.a_sval = P->A.d_sval.p;
+    A.Ea = P->A.d_E.p;
+    A.Eb = P->B.d_E.p;
+    A.V = ham->d_V.p;
+    A.U1 = P->d_U1.p;
+    A.permb = P->d_permb.p;
+    A.rowsa = P->d_rowsa.p;
+    A.ecore = ham->ecore;
+    A.poff = pl->off.p;
+    A.pw = pl->w.p;
+    A.pci = pl->ci.p;
+    A.pval = pl->val.p;
+    return A;
+}
+
+template <>
+SplitArgs<float> split_args<float>(const tbsci_ham *ham, const Plan *P, const PartLayout *pl) {
+    SplitArgs<float> A{};
+    A.la = P->A.l;
+    A.lb = P->B.l;
+    A.npair = P->npair;
+    A.na = P->A.nelec;
+    A.P = pl->P;
+    A.W = pl->W;
+    A.stra = P->A.d_str;
+    A.a_soff = P->A.d_soff;
+    A.a_sci = P->A.d_sci.p;
+    A.a_sval = P->A.d_svalf.p;
+    A.Ea = P->A.d_Ef.p;
+    A.Eb = P->B.d_Ef.p;
+    A.V = ham->d_Vf.p;
+    A.U1 = P->d_U1f.p;
+    A.permb = P->d_permb.p;
+    A.rowsa = P->d_rowsa.p;
+    A.ecore = (float)ham->ecore;
+    A.poff = pl->off.p;
+    A.pw = pl->w.p;
+    A.pci = pl->ci.p;
+    A.pval = pl->valf.p;
+    return A;
+}
+
+template <typename T>
+const T *dval_of(const SpinPlan &sp);
+template <>
+const double *dval_of<double>(const SpinPlan &sp) { return sp.d_dval.p; }
+template <>
+const float *dval_of<float>(const SpinPlan &sp) { return sp.d_dvalf.p; }
+
+}  // namespace
+
+int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem) {
+    const size_t head = elem == 8 ? split_head_bytes<double>(npair) : split_head_bytes<float>(npair);
+    const size_t avail = ctx->smem_optin > head ? ctx->smem_optin - head : 0;
+    const int64_t wmax = (int64_t)(avail / elem);
+    if (wmax <= 0) return 0;
+    return (int)std::max<int64_t>(1, (lb + wmax - 1) / wmax);
+}
+
+// mode 0: the whole sigma; 1: K1 alone on the listed alpha rows (a tuning
+// sample; its output is scratch); 2: K2, K3 and the combine alone (the part of
+// the time that does not depend on the K1 shape; sigma is not meaningful)
+template <typename T>
+tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int extra_parts,
+                          int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode) {
+    const int64_t la = P->A.l, lb = P->B.l;
+    if (la == 0 || lb == 0) return TBSCI_OK;
+    const int pmin = split_min_parts(ctx, P->npair, lb, sizeof(T));
+    TB_CHECK(ctx, pmin >= 1, TBSCI_EINVAL, "split sigma: no room for a column part in shared memory");
+    TB_CHECK(ctx, (la + 31) / 32 <= 65535, TBSCI_EINVAL, "split sigma: too many alpha strings");
+    const int nparts = (int)std::min<int64_t>(lb, pmin + std::max(0, extra_parts));
+    PartLayout *pl = nullptr;
+    TB_TRY(build_parts(ctx, ham, P, nparts, &pl));
+    const size_t need = 2 * (size_t)la * lb * sizeof(T);
+    if (P->d_trans.n < need) {
+        uncharge(ctx, P->d_trans.bytes());
+        P->charged -= std::min(P->charged, P->d_trans.bytes());
+        P->d_trans.release();
+        TB_TRY(charge(ctx, need, "split sigma scratch"));
+        const cudaError_t e = P->d_trans.alloc(need);
+        if (e != cudaSuccess) {
+            uncharge(ctx, need);
+            return fail(ctx, e == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA,
+                        std::string("split sigma scratch: ") + cudaGetErrorString(e));
+        }
+        P->charged += need;
+    }
+    if (!P->d_ipermb.p) {
+        std::vector<int32_t> perm(lb), ip(lb);
+        TB_CUDA(ctx, cudaMemcpy(perm.data(), P->d_permb.p, lb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int64_t j = 0; j < lb; ++j) ip[perm[j]] = (int32_t)j;
+        TB_CUDA(ctx, P->d_ipermb.alloc(lb));
+        TB_CUDA(ctx, cudaMemcpy(P->d_ipermb.p, ip.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    SplitArgs<T> A = split_args<T>(ham, P, pl);
+    if (rows) {
+        A.rowsa = rows;
+        A.la = nrows;
+    }
+    const size_t smem = split_head_bytes<T>(P->npair) + (size_t)pl->W * sizeof(T);
+    T *ct = reinterpret_cast<T *>(P->d_trans.p), *sz = ct + (size_t)la * lb;
+    const dim3 tb(32, 8), tgrid((unsigned)((lb + 31) / 32), (unsigned)((la + 31) / 32));
+    for (int v = 0; v < nvec; ++v) {
+        const T *cv = c + (size_t)v * la * lb;
+        T *sv = s + (size_t)v * la * lb;
+        if (mode != 1) {
+            // [0,2]: sz = H_beta,doubles c^T (c^T in ct)
+            k_transpose<T><<<tgrid, tb, 0, st>>>(cv, ct, la, lb);
+            TB_CUDA(ctx, cudaGetLastError());
+            TB_TRY(launch_dbl<T>(ctx, ct, sz, lb, la, P->B.d_doff, P->B.d_dcol.p, dval_of<T>(P->B), false, st));
+        }
+        if (mode != 2) {
+            // K1 rows in column order into ct (free once c^T has been used)
+            A.C = cv;
+            A.S = ct;
+            if (threads >= 1024) TB_TRY((launch_parts_th<T, 1024>(ctx, A, smem, st)));
+            else TB_TRY((launch_parts_th<T, 512>(ctx, A, smem, st)));
+        }
+        if (mode == 1) continue;
+        k_combine<T><<<tgrid, tb, 0, st>>>(sv, ct, P->d_ipermb.p, sz, la, lb);
+        TB_CUDA(ctx, cudaGetLastError());
+        // [2,0]: sigma += H_alpha,doubles c
+        TB_TRY(launch_dbl<T>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, dval_of<T>(P->A), true, st));
+    }
+    return TBSCI_OK;
+}
+
+template tbsci_status split_launch<double>(tbsci_ctx *, const tbsci_ham *, Plan *, const double *, double *, int, int,
+                                           int, const int32_t *, int64_t, cudaStream_t, int);
+template tbsci_status split_launch<float>(tbsci_ctx *, const tbsci_ham *, Plan *, const float *, float *, int, int,
+                                          int, const int32_t *, int64_t, cudaStream_t, int);
+
+}  // namespace tbsci
