@@ -16,10 +16,15 @@ Table II, which are not available):
   orbitals by construction and is positive semi-definite over orbital pairs;
 * ``ecore = 0``.
 
-Selected string sets follow the weight-selection shape of Sec. III.B: the
-reference (aufbau) string ``bits 0..N-1``, then every string within a double
-excitation of it, then a seeded uniform sample of triples and quadruples (the
-order of candidates before sampling is ascending integer value).
+Selected string sets follow the weight-selection shape of Sec. III.B: a
+reference string, then every string within a double excitation of it, then a
+seeded uniform sample of triples and quadruples (the order of candidates before
+sampling is ascending integer value). The reference of a named workload is its
+lowest-energy string (the argmin of the one-spin string energy over all
+C(n, N) strings, ties to the smaller integer), stored below as a constant that
+tests/golden/make_golden.py computes with the oracle and a CPU test pins; other
+selections (tests, the serving stream, whose per-request Hamiltonians would
+need the string-energy formula here) use the aufbau string ``bits 0..N-1``.
 """
 from __future__ import annotations
 
@@ -67,12 +72,13 @@ def reference_string(nelec: int) -> int:
     return (1 << nelec) - 1
 
 
-def _strings_at_level(norb: int, nelec: int, level: int) -> list[int]:
-    """All strings that differ from the aufbau string by exactly ``level`` electrons,
-    ascending by integer value."""
-    occ = list(range(nelec))
-    vir = list(range(nelec, norb))
-    ref = reference_string(nelec)
+def _strings_at_level(norb: int, nelec: int, level: int, ref: int | None = None) -> list[int]:
+    """All strings that differ from the reference string (default: aufbau) by
+    exactly ``level`` electrons, ascending by integer value."""
+    if ref is None:
+        ref = reference_string(nelec)
+    occ = [i for i in range(norb) if (ref >> i) & 1]
+    vir = [i for i in range(norb) if not (ref >> i) & 1]
     out = []
     for holes in itertools.combinations(occ, level):
         base = ref
@@ -87,15 +93,16 @@ def _strings_at_level(norb: int, nelec: int, level: int) -> list[int]:
     return out
 
 
-def excitation_candidates(norb: int, nelec: int, max_level: int) -> list[list[int]]:
+def excitation_candidates(norb: int, nelec: int, max_level: int, ref: int | None = None) -> list[list[int]]:
     """``[level0, level1, ...]`` candidate lists up to ``max_level`` (inclusive)."""
-    return [_strings_at_level(norb, nelec, k) for k in range(max_level + 1)]
+    return [_strings_at_level(norb, nelec, k, ref) for k in range(max_level + 1)]
 
 
-def selected_strings(norb: int, nelec: int, count: int, seed: int, shuffle: bool = True) -> np.ndarray:
+def selected_strings(norb: int, nelec: int, count: int, seed: int, shuffle: bool = True,
+                     reference: int | None = None) -> np.ndarray:
     """Selected string set of ``min(count, C(norb, nelec))`` strings (uint64).
 
-    Reference string, all singles and doubles of it, then a seeded sample without
+    ``reference`` (default: the aufbau string), all singles and doubles of it, then a seeded sample without
     replacement from the union of triples and quadruples. When ``count`` is below
     ``1 + #singles + #doubles`` the reference comes first, then singles, then
     doubles, each level in seeded random order, truncated. When ``count`` exceeds
@@ -107,7 +114,9 @@ def selected_strings(norb: int, nelec: int, count: int, seed: int, shuffle: bool
     total = math.comb(norb, nelec)
     count = int(min(count, total))
     maxlev = min(nelec, norb - nelec)
-    levels = excitation_candidates(norb, nelec, min(2, maxlev))
+    if reference is not None and (bin(int(reference)).count("1") != nelec or int(reference) >> norb):
+        raise ValueError("reference string must have nelec bits below norb")
+    levels = excitation_candidates(norb, nelec, min(2, maxlev), reference)
     low = [s for lev in levels for s in lev]
     if count <= len(low):
         chosen = []
@@ -123,7 +132,7 @@ def selected_strings(norb: int, nelec: int, count: int, seed: int, shuffle: bool
             hi = lev + 1 if lev + 1 <= maxlev else lev
             pool = []
             for k in range(lev, hi + 1):
-                pool.extend(_strings_at_level(norb, nelec, k))
+                pool.extend(_strings_at_level(norb, nelec, k, reference))
             pool.sort()
             take = min(need, len(pool))
             pick = rng.choice(len(pool), size=take, replace=False)
@@ -184,6 +193,7 @@ class Workload:
     seed_vec: int
     notes: str = ""
     extras: dict = field(default_factory=dict)
+    reference: int | None = None  # centre of the selection (None: aufbau)
 
     def hamiltonian(self):
         return synth_hamiltonian(self.norb, self.seed_ints)
@@ -192,7 +202,7 @@ class Workload:
         """Selected alpha strings (uint64, shuffled) or ``None`` for the full space."""
         if self.count_alpha is None:
             return None
-        return selected_strings(self.norb, self.nalpha, self.count_alpha, self.seed_sel)
+        return selected_strings(self.norb, self.nalpha, self.count_alpha, self.seed_sel, reference=self.reference)
 
     def beta_selection(self, distinct: bool = False):
         """Selected beta strings; identical to the alpha set (closed shell) unless
@@ -200,18 +210,20 @@ class Workload:
         if self.count_beta is None:
             return None
         seed = self.seed_sel + 1 if distinct else self.seed_sel
-        return selected_strings(self.norb, self.nbeta, self.count_beta, seed)
+        return selected_strings(self.norb, self.nbeta, self.count_beta, seed, reference=self.reference)
 
 
 WORKLOADS = {
     "fci8": Workload("fci8", 8, 4, 4, None, None, 1, 1, 1001, 2001, 3001,
                      "norb=8, 4+4 electrons, all 70 x 70 strings (4,900 determinants)"),
     "sel16": Workload("sel16", 16, 8, 8, 3000, 3000, 3, 3, 1002, 2002, 3002,
-                      "norb=16, 8+8 electrons, 3,000 x 3,000 selected strings (9.0M determinants)"),
+                      "norb=16, 8+8 electrons, 3,000 x 3,000 selected strings (9.0M determinants)",
+                      reference=0b10010111001101),
     "fci16": Workload("fci16", 16, 8, 8, None, None, 1, 1, 1003, 2003, 3003,
                       "norb=16, 8+8 electrons, 12,870 x 12,870 strings (165.6M determinants)"),
     "sel24": Workload("sel24", 24, 12, 12, 40000, 40000, 1, 1, 1004, 2004, 3004,
-                      "norb=24, 12+12 electrons, 40,000 x 40,000 selected strings (1.6B determinants)"),
+                      "norb=24, 12+12 electrons, 40,000 x 40,000 selected strings (1.6B determinants)",
+                      reference=0b101110011011111100),
 }
 
 

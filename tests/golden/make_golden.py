@@ -14,7 +14,7 @@ the file is written: the oracle's Davidson at tight tolerances (|dE| < 1e-11,
 ||r|| < 1e-7) and ARPACK Lanczos (scipy.sparse.linalg.eigsh, smallest
 algebraic). The Davidson values are stored.
 
-    python tests/golden/make_golden.py [fci8] [sel12]
+    python tests/golden/make_golden.py [fci8] [sel12] [refs]
 """
 import os
 import sys
@@ -74,8 +74,24 @@ def fci8():
                       "synthetic Hamiltonian seed 1001 (oracle dense H + numpy eigvalsh)")
 
 
+def refs():
+    """Prints the selection centres of the named selected workloads: the argmin of
+    the one-spin string energy over all C(n, N) strings (the oracle's diagonal
+    of the space with no beta electron), ties to the smaller integer. They are
+    stored as constants in tbsci_inputs.WORKLOADS."""
+    for name, wl in sorted(WORKLOADS.items()):
+        if wl.count_alpha is None:
+            continue
+        h, eri, _ = wl.hamiltonian()
+        sp = oracle.make_space(wl.norb, wl.nalpha, 0)
+        E = oracle.diagonal(sp, h, eri, 0.0)
+        print("%s reference=0b%s" % (name, bin(int(sp.sa[int(np.argmin(E))]))[2:]))
+
+
 def main(argv):
     which = argv or ["fci8", "sel12"]
+    if "refs" in which:
+        refs()
     if "fci8" in which:
         fci8()
     if "sel12" in which:

@@ -512,3 +512,23 @@ def test_pruned_davidson_matches_dense():
     w = np.linalg.eigvalsh(oracle.hamiltonian_dense_pruned(ps, h, eri, 0.0))
     e, _, info = oracle.solve_pruned(ps, h, eri, 0.0, 3)
     assert info["converged"] and np.max(np.abs(e - w[:3])) < 1e-8
+
+
+@pytest.mark.parametrize("name", ["sel16", "sel24"])
+def test_workload_selection_centre_is_the_lowest_energy_string(name):
+    """The selected workloads are centred on their lowest-energy string: the
+    argmin over all C(n, N) strings of the one-spin string energy (the oracle's
+    diagonal with no beta electron), ties to the smaller integer. The constant
+    stored in tbsci_inputs must be that string, and the selection must hold it
+    and every string within a double excitation of it."""
+    from tbsci_inputs import WORKLOADS
+    wl = WORKLOADS[name]
+    h, eri, _ = wl.hamiltonian()
+    sp = oracle.make_space(wl.norb, wl.nalpha, 0)
+    E = oracle.diagonal(sp, h, eri, 0.0)
+    assert int(sp.sa[int(np.argmin(E))]) == wl.reference
+    sel = set(int(x) for x in wl.alpha_selection())
+    ref = wl.reference
+    near = [int(s) for s in sp.sa if bin(int(s) ^ ref).count("1") <= 4]
+    assert ref in sel and all(s in sel for s in near)
+    assert len(sel) == wl.count_alpha
