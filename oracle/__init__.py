@@ -17,6 +17,10 @@ What it computes (each function cites the passage it follows):
   space by the spin-orbital Slater-Condon rules (Sec. II.C, Eq. 8), sigma = H.c.
 * ``davidson`` -- standard Davidson (Sec. III.A) with restart to the Ritz
   vectors when the subspace is full (Sec. III.C), in numpy FP64.
+* ``string_weights`` / ``select_by_weight`` / ``coefficient_histogram`` -- the
+  bitstring selection of Sec. III.B (weights as sums of squared coefficients,
+  a threshold relative to the HF string's weight) and the coefficient
+  distribution of Fig. 3 (counts of |c_K / c_HF| per logarithmic bin).
 * ``PrunedSpace`` / ``sigma_pruned`` / ``diagonal_pruned`` -- the general TBSCI
   space D_TBSCI of Sec. II.A, Eq. 6: per alpha string w a set I_w of allowed beta
   strings; H on it is the principal submatrix of H on the member determinants.
@@ -254,6 +258,35 @@ def hamiltonian_dense(space: Space, h, eri, ecore) -> np.ndarray:
     return H
 
 
+# ------------------------------------------- bitstring selection (Sec. III.B)
+
+def string_weights(C, la: int, lb: int):
+    """Weights of the alpha and beta strings of a TPB vector (Sec. III.B): after
+    normalising, W_a(w) = sum_u c(w, u)^2 and W_b(u) = sum_w c(w, u)^2."""
+    c = np.asarray(C, dtype=np.float64).reshape(la, lb)
+    c = c / np.linalg.norm(c)
+    return (c * c).sum(axis=1), (c * c).sum(axis=0)
+
+
+def select_by_weight(weights, delta: float, ref: int | None = None):
+    """Indices (ascending) of the strings whose weight is at least ``delta``
+    times the HF string's weight (Sec. III.B). The HF string is ``ref`` when
+    given, else the string of largest weight."""
+    w = np.asarray(weights, dtype=np.float64)
+    h = w[int(np.argmax(w))] if ref is None else w[ref]
+    return np.nonzero(w >= delta * h)[0]
+
+
+def coefficient_histogram(C, edges):
+    """Counts of |c_K| per bin [edges[k], edges[k+1]) (Fig. 3 bins |c_K / c_HF|
+    on a logarithmic scale; the caller scales the edges by |c_HF|). Returns
+    ``nbins + 2`` counts: below edges[0], the bins, at or above edges[-1]."""
+    a = np.abs(np.asarray(C, dtype=np.float64).ravel())
+    e = np.asarray(edges, dtype=np.float64)
+    idx = np.searchsorted(e, a, side="right")  # 0: below the first edge
+    return np.bincount(idx, minlength=len(e) + 1).astype(np.int64)
+
+
 # ---------------------------------------------------- pruned spaces (D_TBSCI)
 
 class PrunedSpace:
@@ -280,6 +313,29 @@ class PrunedSpace:
         """TPB indices w * lb + u of the member determinants, in compressed order."""
         w = np.repeat(np.arange(self.space.la, dtype=np.int64), np.diff(self.off))
         return w * self.space.lb + self.cols
+
+
+def string_irrep(s: int, irreps) -> int:
+    """Irrep of a string in an abelian point group: the XOR of the labels of its
+    occupied orbitals (product of one-electron irreps, Sec. II.A on symmetry)."""
+    out = 0
+    for i in range(len(irreps)):
+        if (int(s) >> i) & 1:
+            out ^= int(irreps[i])
+    return out
+
+
+def symmetry_space(space: Space, irreps, target: int) -> PrunedSpace:
+    """The symmetry-allowed determinants of a TPB space (Sec. II.A): (w, u) with
+    irrep(w) XOR irrep(u) = target."""
+    ga = [string_irrep(s, irreps) for s in space.sa]
+    gb = [string_irrep(s, irreps) for s in space.sb]
+    cols, off = [], [0]
+    for w in range(space.la):
+        row = [u for u in range(space.lb) if ga[w] ^ gb[u] == target]
+        cols.extend(row)
+        off.append(len(cols))
+    return PrunedSpace(space, np.array(off, dtype=np.int64), np.array(cols, dtype=np.int32))
 
 
 def sigma_pruned(ps: PrunedSpace, h, eri, ecore, C, rows=None, nthreads: int = 0, with_bound: bool = False):

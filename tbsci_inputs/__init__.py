@@ -45,6 +45,8 @@ __all__ = [
     "serving_stream",
     "excitation_level",
     "prune_by_total_level",
+    "orbital_irreps",
+    "synth_hamiltonian_symmetric",
 ]
 
 
@@ -63,6 +65,38 @@ def synth_hamiltonian(norb: int, seed: int, scale: float = 0.3, hoff_std: float 
     nfac = 2 * n
     A = rng.normal(0.0, 1.0, size=(nfac, n, n))
     L = scale * 0.5 * (A + np.transpose(A, (0, 2, 1)))
+    eri = np.einsum("pij,pkl->ijkl", L, L)
+    return h, np.ascontiguousarray(eri), 0.0
+
+
+def orbital_irreps(norb: int, seed: int, nirrep: int = 8) -> np.ndarray:
+    """Seeded irrep labels 0..nirrep-1 of the orbitals of an abelian point group
+    (D2h: 8 irreps; labels multiply as bitwise XOR)."""
+    return np.random.default_rng(seed).integers(0, nirrep, size=norb).astype(np.int32)
+
+
+def synth_hamiltonian_symmetric(norb: int, seed: int, irreps, scale: float = 0.3, hoff_std: float = 0.05):
+    """The recipe of ``synth_hamiltonian`` with point-group symmetry: h_ij = 0
+    unless irreps i and j are equal, and each factor L^P carries an irrep G_P with
+    L^P_ij = 0 unless irrep(i) XOR irrep(j) = G_P, so (ij|kl) = 0 unless the four
+    labels XOR to 0 (8-fold symmetric and positive semi-definite as before)."""
+    rng = np.random.default_rng(seed)
+    n = int(norb)
+    g = np.asarray(irreps, dtype=np.int64)
+    diag = np.sort(rng.uniform(-2.0, 0.0, size=n))
+    h = np.zeros((n, n))
+    iu = np.triu_indices(n, 1)
+    off = rng.normal(0.0, hoff_std, size=len(iu[0]))
+    h[iu] = off
+    h = h + h.T
+    h[g[:, None] != g[None, :]] = 0.0
+    h[np.diag_indices(n)] = diag
+    nfac = 2 * n
+    A = rng.normal(0.0, 1.0, size=(nfac, n, n))
+    L = scale * 0.5 * (A + np.transpose(A, (0, 2, 1)))
+    gp = rng.integers(0, int(g.max()) + 1 if len(g) else 1, size=nfac)
+    mask = (g[:, None] ^ g[None, :])[None, :, :] == gp[:, None, None]
+    L = L * mask
     eri = np.einsum("pij,pkl->ijkl", L, L)
     return h, np.ascontiguousarray(eri), 0.0
 

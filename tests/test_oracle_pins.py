@@ -532,3 +532,89 @@ def test_workload_selection_centre_is_the_lowest_energy_string(name):
     near = [int(s) for s in sp.sa if bin(int(s) ^ ref).count("1") <= 4]
     assert ref in sel and all(s in sel for s in near)
     assert len(sel) == wl.count_alpha
+
+
+# ------------------------------------------- bitstring selection (Sec. III.B)
+
+def test_string_weights_sum_to_one_and_brute_force():
+    rng = np.random.default_rng(11)
+    C = rng.standard_normal((7, 5))
+    wa, wb = oracle.string_weights(C, 7, 5)
+    assert abs(wa.sum() - 1.0) < 1e-14 and abs(wb.sum() - 1.0) < 1e-14
+    n2 = sum(C[i, j] ** 2 for i in range(7) for j in range(5))
+    for i in range(7):
+        assert abs(wa[i] - sum(C[i, j] ** 2 for j in range(5)) / n2) < 1e-15
+    for j in range(5):
+        assert abs(wb[j] - sum(C[i, j] ** 2 for i in range(7)) / n2) < 1e-15
+    # a single determinant carries all the weight of its two strings
+    D = np.zeros((7, 5))
+    D[3, 2] = -2.0
+    wa, wb = oracle.string_weights(D, 7, 5)
+    assert wa[3] == 1.0 and wb[2] == 1.0 and wa.sum() == 1.0
+
+
+def test_select_by_weight_threshold_semantics():
+    w = np.array([0.5, 0.2, 0.05, 0.2, 0.05])
+    assert list(oracle.select_by_weight(w, 1.0)) == [0]
+    assert list(oracle.select_by_weight(w, 0.4)) == [0, 1, 3]
+    assert list(oracle.select_by_weight(w, 0.1)) == [0, 1, 2, 3, 4]
+    assert list(oracle.select_by_weight(w, 1.0, ref=1)) == [0, 1, 3]
+    assert list(oracle.select_by_weight(w, 0.0)) == [0, 1, 2, 3, 4]
+
+
+def test_coefficient_histogram_brute_force():
+    rng = np.random.default_rng(12)
+    c = rng.standard_normal(500) * 10.0 ** rng.uniform(-6, 0, 500)
+    c[:3] = 0.0
+    edges = 10.0 ** np.arange(-6, 1)
+    got = oracle.coefficient_histogram(c, edges)
+    want = np.zeros(len(edges) + 1, dtype=np.int64)
+    for x in np.abs(c):
+        k = 0
+        while k < len(edges) and x >= edges[k]:
+            k += 1
+        want[k] += 1
+    assert np.array_equal(got, want) and got.sum() == 500
+
+
+# ------------------------------------------------ point-group symmetry blocks
+
+@pytest.mark.parametrize("n,na,nb", [(6, 3, 3), (7, 3, 2)])
+def test_symmetric_h_is_block_diagonal_and_blocks_give_the_spectrum(n, na, nb):
+    """With D2h-labelled integrals (h and (ij|kl) vanish unless the labels
+    multiply to the totally symmetric irrep) H couples only determinants of equal
+    irrep: every element between different blocks is zero, and the union of the
+    spectra of the eight symmetry blocks is the spectrum of H (dense, exact)."""
+    from tbsci_inputs import orbital_irreps, synth_hamiltonian_symmetric
+    g = orbital_irreps(n, seed=900 + n)
+    h, eri, _ = synth_hamiltonian_symmetric(n, 901 + n, g)
+    # the integrals obey the selection rule
+    for i, j, k, l in itertools.product(range(n), repeat=4):
+        if g[i] ^ g[j] ^ g[k] ^ g[l]:
+            assert eri[i, j, k, l] == 0.0
+    sp = oracle.make_space(n, na, nb)
+    H = oracle.hamiltonian_dense(sp, h, eri, 0.0)
+    Hb = brute_force_h(n, sp.sa, sp.sb, h, eri, 0.0)
+    assert np.max(np.abs(H - Hb)) < 1e-12
+    irr = np.array([oracle.string_irrep(a, g) ^ oracle.string_irrep(b, g) for a in sp.sa for b in sp.sb])
+    assert np.all(H[irr[:, None] != irr[None, :]] == 0.0)
+    spectra = []
+    total = 0
+    for t in range(8):
+        ps = oracle.symmetry_space(sp, g, t)
+        total += ps.ndet
+        if ps.ndet:
+            assert np.array_equal(ps.members(), np.nonzero(irr == t)[0])
+            spectra.append(np.linalg.eigvalsh(oracle.hamiltonian_dense_pruned(ps, h, eri, 0.0)))
+    assert total == sp.ndet
+    assert np.max(np.abs(np.sort(np.concatenate(spectra)) - np.linalg.eigvalsh(H))) < 1e-10
+
+
+def test_string_irrep_brute_force():
+    g = [1, 2, 4, 3, 0, 7]
+    for s in range(64):
+        want = 0
+        for i in range(6):
+            if s & (1 << i):
+                want ^= g[i]
+        assert oracle.string_irrep(s, g) == want
