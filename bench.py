@@ -541,6 +541,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--serving", action="store_true", help="serving stream instead of the sigma bench")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-cache", default=None,
+                    help="tune-cache file loaded into the context (with --no-autotune: pins the launch shape)")
     ap.add_argument("--precision-study", action="store_true")
     ap.add_argument("--modes", default="1,2,3", help="Davidson mixed modes for --precision-study")
     ap.add_argument("--max-iter", type=int, default=0)
@@ -574,7 +576,7 @@ def main():
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
     nvec = wl.nvec
-    ctx = tb.Context(local)
+    ctx = tb.Context(local, tune_cache=args.tune_cache) if args.tune_cache else tb.Context(local)
     stream = torch.cuda.current_stream()
     if dist:
         dist.barrier()

@@ -346,6 +346,18 @@ tbsci_status tbsci_davidson(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *
 typedef struct tbsci_pruned tbsci_pruned;
 tbsci_status tbsci_pruned_create(tbsci_ctx *ctx, const tbsci_tables *a, const tbsci_tables *b, const int64_t *off,
                                  const int32_t *cols, tbsci_pruned **out);
+/* Point-group symmetry blocking (Sec. II.A): the pruned space of the
+ * determinants of irrep `target` in an abelian point group (D2h or a subgroup,
+ * irrep labels 0..7 multiplying as bitwise XOR). orb_irrep: HOST [norb] labels
+ * of the orbitals; a string's irrep is the XOR of its occupied orbitals'
+ * labels, and (w, u) is kept when irrep(w) XOR irrep(u) = target. The paper
+ * sorts the beta strings by irrep so that each I_w is one interval; here the
+ * strings keep ascending order and I_w is the irrep class of beta strings,
+ * passed to tbsci_pruned_create. With integrals of that symmetry, H couples no
+ * two blocks, so the blocks' spectra together are the spectrum of H.
+ * Errors: EINVAL (labels or target outside 0..7), ENOMEM, ECUDA. */
+tbsci_status tbsci_pruned_create_symmetry(tbsci_ctx *ctx, const tbsci_tables *a, const tbsci_tables *b,
+                                          const int32_t *orb_irrep, int target, tbsci_pruned **out);
 tbsci_status tbsci_pruned_count(const tbsci_pruned *pr, int64_t *ndet);
 void tbsci_pruned_destroy(tbsci_pruned *pr);
 
@@ -365,6 +377,33 @@ tbsci_status tbsci_diagonal_pruned(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_t
 tbsci_status tbsci_davidson_pruned(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b,
                                    const tbsci_pruned *pr, int nroots, const tbsci_davidson_opts *opts,
                                    double *energies, double *vecs, tbsci_davidson_info *info);
+
+/* ---------------------------------------------------- bitstring selection */
+
+/* Weights of the strings of a TPB vector (Sec. III.B): with c normalised,
+ * W_a(w) = sum_u c(w, u)^2 and W_b(u) = sum_w c(w, u)^2. c: DEVICE FP64
+ * [l_a][l_b] (need not be normalised); wa, wb: HOST [l_a], [l_b]. Fixed
+ * reduction order (run-to-run identical). Blocks until done.
+ * Errors: EINVAL (null pointers, a zero vector), ENOMEM, ECUDA. */
+tbsci_status tbsci_string_weights(tbsci_ctx *ctx, const tbsci_tables *a, const tbsci_tables *b, const double *c,
+                                  double *wa, double *wb, tbsci_stream stream);
+/* Bitstring selection by weight (Sec. III.B): the alpha (beta) strings whose
+ * weight in c is at least delta times the weight of the HF string, read as the
+ * string of largest weight. sel_a / sel_b: HOST arrays of capacity l_a / l_b
+ * that receive the kept strings in ascending order; *na / *nb their counts.
+ * The kept sets define the next TPB space. Errors: EINVAL (null pointers,
+ * delta < 0, an empty space, a zero vector), ENOMEM, ECUDA. */
+tbsci_status tbsci_select_by_weight(tbsci_ctx *ctx, const tbsci_tables *a, const tbsci_tables *b, const double *c,
+                                    double delta, uint64_t *sel_a, int64_t *na, uint64_t *sel_b, int64_t *nb,
+                                    tbsci_stream stream);
+/* Coefficient distribution (Fig. 3): counts[k] = number of entries of the DEVICE
+ * FP64 array x[n] with edges[k-1] <= |x| < edges[k] (counts[0]: |x| < edges[0];
+ * counts[nedges]: |x| >= edges[nedges-1]). edges: HOST, strictly ascending,
+ * 1..256 values; for the paper's bins of |c_K / c_HF| on a logarithmic scale
+ * pass edges 10^e |c_HF|. counts: HOST [nedges + 1]. Exact integer counts.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+tbsci_status tbsci_coefficient_histogram(tbsci_ctx *ctx, const double *x, int64_t n, const double *edges, int nedges,
+                                         int64_t *counts, tbsci_stream stream);
 
 /* --------------------------------------------------------------- serving */
 

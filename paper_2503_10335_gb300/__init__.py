@@ -119,10 +119,31 @@ class Space:
         e, info = B.tbsci_davidson(self.ctx.handle, self.ham, self.ta, self.tb, nroots, vecs=vecs, **kw)
         return (e, info, vecs) if want_vectors else (e, info)
 
+    def string_weights(self, c):
+        """(W_a, W_b) of the FP64 device vector c [la, lb] (Sec. III.B)."""
+        return B.tbsci_string_weights(self.ctx.handle, self.ta, self.tb, c, self.la, self.lb)
+
+    def select_by_weight(self, c, delta):
+        """The alpha and beta strings whose weight in c is at least delta times the
+        largest (the HF string's) weight (Sec. III.B): the next space's strings."""
+        return B.tbsci_select_by_weight(self.ctx.handle, self.ta, self.tb, c, delta, self.la, self.lb)
+
+    def coefficient_histogram(self, c, c_hf, lo=-12, hi=0, per_decade=1):
+        """Counts of |c_K / c_HF| per logarithmic bin from 10^lo to 10^hi (Fig. 3):
+        returns (bin edges of the ratio, counts incl. the under- and overflow bins)."""
+        ratios = 10.0 ** (np.arange(lo * per_decade, hi * per_decade + 1) / per_decade)
+        counts = B.tbsci_coefficient_histogram(self.ctx.handle, c, ratios * abs(float(c_hf)))
+        return ratios, counts
+
     def prune(self, off, cols):
         """The pruned space D_TBSCI of this space: per alpha string w the ascending
         beta indices cols[off[w]:off[w + 1]]."""
         return Pruned(self, off, cols)
+
+    def symmetry_block(self, orb_irrep, target):
+        """The determinants of irrep ``target`` (abelian point group, labels 0..7)."""
+        return Pruned(self, None, None, handle=B.tbsci_pruned_create_symmetry(self.ctx.handle, self.ta, self.tb,
+                                                                              orb_irrep, target))
 
     def close(self):
         for fn, h in reversed(self._handles):
@@ -139,9 +160,10 @@ class Space:
 class Pruned:
     """A pruned TBSCI space inside a ``Space`` (compressed vectors [nvec, ndet])."""
 
-    def __init__(self, space: Space, off, cols):
+    def __init__(self, space: Space, off, cols, handle=None):
         self.space = space
-        self.handle = B.tbsci_pruned_create(space.ctx.handle, space.ta, space.tb, off, cols)
+        self.handle = handle if handle is not None else B.tbsci_pruned_create(space.ctx.handle, space.ta, space.tb,
+                                                                               off, cols)
         self.ndet = B.tbsci_pruned_count(self.handle)
 
     def sigma(self, c, out=None, stream=None, dtype=None):

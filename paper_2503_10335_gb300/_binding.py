@@ -31,7 +31,8 @@ EXPORTS = [
     "tbsci_server_destroy", "tbsci_sigma_autotune", "tbsci_tune_cache_save", "tbsci_tune_cache_load",
     "tbsci_tune_cache_size", "tbsci_create_ex", "tbsci_hbm_used",
     "tbsci_pruned_create", "tbsci_pruned_count", "tbsci_pruned_destroy", "tbsci_sigma_pruned",
-    "tbsci_diagonal_pruned", "tbsci_davidson_pruned",
+    "tbsci_diagonal_pruned", "tbsci_davidson_pruned", "tbsci_string_weights", "tbsci_select_by_weight",
+    "tbsci_coefficient_histogram", "tbsci_pruned_create_symmetry",
 ]
 
 
@@ -142,7 +143,11 @@ def load(path: str | None = None):
         "tbsci_create": ([I, PP], I),
         "tbsci_create_ex": ([ctypes.POINTER(Options), PP], I),
         "tbsci_hbm_used": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
+        "tbsci_string_weights": ([P, P, P, P, P, P, P], I),
+        "tbsci_select_by_weight": ([P, P, P, P, D, P, ctypes.POINTER(I64), P, ctypes.POINTER(I64), P], I),
+        "tbsci_coefficient_histogram": ([P, P, I64, P, I, P, P], I),
         "tbsci_pruned_create": ([P, P, P, P, P, PP], I),
+        "tbsci_pruned_create_symmetry": ([P, P, P, P, I, PP], I),
         "tbsci_pruned_count": ([P, ctypes.POINTER(I64)], I),
         "tbsci_pruned_destroy": ([P], None),
         "tbsci_sigma_pruned": ([P, P, P, P, P, P, P, I, I, P], I),
@@ -389,6 +394,31 @@ def tbsci_davidson(ctx, ham, ta, tb, nroots: int, vecs=None, max_subspace=0, max
     return e, d
 
 
+def tbsci_string_weights(ctx, ta, tb, c, la: int, lb: int, stream=None):
+    """(W_a [la], W_b [lb]) numpy arrays for the FP64 device vector c."""
+    wa, wb = np.zeros(la), np.zeros(lb)
+    _check(ctx, load().tbsci_string_weights(ctx, ta, tb, _ptr(c), _ptr(wa), _ptr(wb), _stream(stream)))
+    return wa, wb
+
+
+def tbsci_select_by_weight(ctx, ta, tb, c, delta: float, la: int, lb: int, stream=None):
+    """(kept alpha strings, kept beta strings) as uint64 numpy arrays."""
+    sa, sb = np.zeros(la, dtype=np.uint64), np.zeros(lb, dtype=np.uint64)
+    na, nb = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load().tbsci_select_by_weight(ctx, ta, tb, _ptr(c), float(delta), _ptr(sa), ctypes.byref(na),
+                                              _ptr(sb), ctypes.byref(nb), _stream(stream)))
+    return sa[:na.value].copy(), sb[:nb.value].copy()
+
+
+def tbsci_coefficient_histogram(ctx, x, edges, stream=None) -> np.ndarray:
+    """Counts [len(edges) + 1] of |x| per bin of the ascending edges."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    counts = np.zeros(len(e) + 1, dtype=np.int64)
+    _check(ctx, load().tbsci_coefficient_histogram(ctx, _ptr(x), int(x.numel()), _ptr(e), len(e), _ptr(counts),
+                                                   _stream(stream)))
+    return counts
+
+
 def tbsci_pruned_create(ctx, ta, tb, off, cols):
     """Pruned space from host CSR arrays (off [la + 1], cols [off[la]])."""
     off = np.ascontiguousarray(off, dtype=np.int64)
@@ -396,6 +426,14 @@ def tbsci_pruned_create(ctx, ta, tb, off, cols):
     out = ctypes.c_void_p()
     _check(ctx, load().tbsci_pruned_create(ctx, ta, tb, _ptr(off), _ptr(cols) if len(cols) else None,
                                            ctypes.byref(out)))
+    return out
+
+
+def tbsci_pruned_create_symmetry(ctx, ta, tb, orb_irrep, target: int):
+    """Symmetry block of irrep ``target`` (orbital labels 0..7, XOR products)."""
+    g = np.ascontiguousarray(orb_irrep, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(ctx, load().tbsci_pruned_create_symmetry(ctx, ta, tb, _ptr(g), int(target), ctypes.byref(out)))
     return out
 
 

@@ -932,6 +932,8 @@ tbsci_status engine_create(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroot
 
 void engine_destroy(DavEngine *e) { delete e; }
 
+void engine_set_ctx(DavEngine *e, tbsci_ctx *ctx) { e->ctx = ctx; }
+
 bool engine_wants_sigma(DavEngine *e, const void **c, void **s, int *k, tbsci_dtype *dt) {
     return e->wants_sigma(c, s, k, dt);
 }

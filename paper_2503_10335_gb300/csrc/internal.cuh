@@ -153,19 +153,24 @@ struct SpinPlan {
     std::vector<int64_t> h_soff, h_doff;
 };
 
-// Beta single links of one column order split by the column part their target
-// lies in (part p = columns [p W, (p + 1) W)): per slice of 32 columns and part,
-// a sliced-ELL block (offset, width) whose padding entries point at the part's
-// first column with a zero coefficient. Used when a c row does not fit in
-// shared memory and is staged one part at a time.
+// Beta single links split by the column part their target lies in (part p =
+// columns [p W, (p + 1) W)), for a c row staged in shared memory one part at a
+// time. Columns are taken in their own order `perm` (by link count in part 0,
+// then part 1, ..., descending) so the 32 columns of a slice have similar counts
+// in every part; per slice and part a sliced-ELL block (offset, width) whose
+// padding entries point at the part's first column with a zero coefficient.
+// U is the beta Coulomb table with its columns in `perm` order.
 struct PartLayout {
     int P = 0;
     int64_t W = 0;
-    DevBuf<int64_t> off;   // [nslices * P]
-    DevBuf<int32_t> w;     // [nslices * P]
-    DevBuf<int2> ci;       // {target, 2 * pair + (sign < 0)}
-    DevBuf<double> val;    // same-spin string-Hamiltonian value
+    DevBuf<int32_t> perm, iperm;  // column order and its inverse
+    DevBuf<int64_t> off;          // [nslices * P]
+    DevBuf<int32_t> w;            // [nslices * P]
+    DevBuf<int2> ci;              // {target, 2 * pair + (sign < 0)}
+    DevBuf<double> val;           // same-spin string-Hamiltonian value
     DevBuf<float> valf;
+    DevBuf<double> U;             // [npair][l_b], columns in perm order
+    DevBuf<float> Uf;
 };
 
 struct Plan {
@@ -203,7 +208,6 @@ struct Plan {
     // and the transposed c / sigma scratch of the beta-double class
     std::vector<std::unique_ptr<PartLayout>> parts;
     DevBuf<unsigned char> d_trans;
-    DevBuf<int32_t> d_ipermb;  // inverse of d_permb
     tbsci_sigma_counts counts{};
     size_t charged = 0;  // device bytes counted against the context's budget
 };
@@ -285,9 +289,12 @@ tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan 
                                const int32_t *rows = nullptr, int64_t nrows = 0);
 // sigma_split.cu: sigma for rows longer than shared memory (column parts + the
 // same-spin double classes as column-tiled products); see the file head
-int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem);
+// smallest number of column parts of a c row that fits in shared memory beside
+// the accumulators of 1/nc of a sigma row (0: none fits)
+int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc);
+// variant: 0, 1, 2 -> 1, 2, 4 CTAs per alpha row, each with the minimal parts
 template <typename T>
-tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int extra_parts,
+tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int variant,
                           int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode);
 // sigma_tc.cu: the diagonal, alpha singles and all alpha-beta classes on the
 // tensor cores (3xTF32 or BF16 products, FP32 accumulation), added into s.
@@ -302,6 +309,9 @@ struct DavEngine;
 tbsci_status engine_create(tbsci_ctx *ctx, tbsci_ham *ham, Plan *plan, int nroots, const tbsci_davidson_opts *o,
                            DavEngine **out, const tbsci_pruned *pr = nullptr);
 void engine_destroy(DavEngine *e);
+// the context whose error slot and device the engine uses from now on (a
+// server builds an engine on its set-up thread and drives it from the scheduler)
+void engine_set_ctx(DavEngine *e, tbsci_ctx *ctx);
 // The sigma the engine needs next: c/s device pointers ([k][N], dtype dt), on the engine stream.
 bool engine_wants_sigma(DavEngine *e, const void **c, void **s, int *k, tbsci_dtype *dt);
 // Call once that sigma is enqueued on, or ordered before, the engine stream.

@@ -346,6 +346,39 @@ tbsci_status tbsci_pruned_create(tbsci_ctx *ctx, const tbsci_tables *a, const tb
     return TBSCI_OK;
 }
 
+// Symmetry blocks (Sec. II.A): each I_w is the class of beta strings whose irrep
+// is target XOR irrep(w); a string's irrep is the XOR of the labels of its
+// occupied orbitals. The classes are built once and copied per alpha string.
+tbsci_status tbsci_pruned_create_symmetry(tbsci_ctx *ctx, const tbsci_tables *a, const tbsci_tables *b,
+                                          const int32_t *orb_irrep, int target, tbsci_pruned **out) {
+    if (!ctx) return TBSCI_EINVAL;
+    TB_CUDA(ctx, cudaSetDevice(ctx->device));
+    TB_CHECK(ctx, a && b && orb_irrep && out, TBSCI_EINVAL, "tbsci_pruned_create_symmetry: null argument");
+    TB_CHECK(ctx, a->norb == b->norb, TBSCI_EINVAL, "tbsci_pruned_create_symmetry: norb differs between the sets");
+    TB_CHECK(ctx, target >= 0 && target < 8, TBSCI_EINVAL, "tbsci_pruned_create_symmetry: target irrep not in 0..7");
+    for (int i = 0; i < a->norb; ++i)
+        TB_CHECK(ctx, orb_irrep[i] >= 0 && orb_irrep[i] < 8, TBSCI_EINVAL,
+                 "tbsci_pruned_create_symmetry: orbital irrep not in 0..7");
+    std::vector<uint64_t> sa(a->count), sb(b->count);
+    if (a->count) TB_CUDA(ctx, cudaMemcpy(sa.data(), a->d_str.p, a->count * 8, cudaMemcpyDeviceToHost));
+    if (b->count) TB_CUDA(ctx, cudaMemcpy(sb.data(), b->d_str.p, b->count * 8, cudaMemcpyDeviceToHost));
+    auto irrep = [&](uint64_t s) {
+        int g = 0;
+        for (; s; s &= s - 1) g ^= orb_irrep[__builtin_ctzll(s)];
+        return g;
+    };
+    std::vector<int32_t> cls[8];
+    for (int64_t u = 0; u < b->count; ++u) cls[irrep(sb[u])].push_back((int32_t)u);
+    std::vector<int64_t> off(a->count + 1, 0);
+    for (int64_t w = 0; w < a->count; ++w) off[w + 1] = off[w] + (int64_t)cls[target ^ irrep(sa[w])].size();
+    std::vector<int32_t> cols((size_t)off[a->count]);
+    for (int64_t w = 0; w < a->count; ++w) {
+        const std::vector<int32_t> &c = cls[target ^ irrep(sa[w])];
+        std::copy(c.begin(), c.end(), cols.begin() + off[w]);
+    }
+    return tbsci_pruned_create(ctx, a, b, off.data(), cols.empty() ? nullptr : cols.data(), out);
+}
+
 tbsci_status tbsci_pruned_count(const tbsci_pruned *pr, int64_t *ndet) {
     if (!pr || !ndet) return TBSCI_EINVAL;
     *ndet = pr->nd;

@@ -4,7 +4,10 @@
 // private context and, every round:
 //   1. admits queued requests in arrival order while a slot is free and the
 //      HBM budget holds the request's estimated footprint (strings, tables,
-//      prepared space, Davidson vectors), building its device objects;
+//      prepared space, Davidson vectors) and hands them to a set-up thread,
+//      which builds their device objects with its own context and stream while
+//      the scheduler keeps advancing the running solves; set-up requests join
+//      the running ones as they become ready;
 //   2. polls every admitted solve's Davidson engine without blocking, so the
 //      host logic of whichever solves have finished a phase runs while the
 //      device keeps working on the others (each solve has its own stream);
@@ -87,8 +90,16 @@ size_t spin_bytes(int n, int N, int64_t l) {
 
 struct tbsci_server {
     tbsci_server_opts opts{};
-    tbsci_ctx *ctx = nullptr;
-    std::thread th;
+    tbsci_ctx *ctx = nullptr;   // the scheduler thread's context
+    tbsci_ctx *sctx = nullptr;  // the set-up thread's context
+    std::thread th, setup_th;
+    // requests handed to the set-up thread (owned here) and their outcomes
+    std::vector<std::unique_ptr<Req>> in_setup;
+    std::mutex smu;
+    std::condition_variable scv;
+    std::deque<std::pair<Req *, bool>> setup_q;  // request, injected admission failure
+    std::vector<std::pair<Req *, tbsci_status>> setup_done;
+    bool setup_stop = false;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::unique_ptr<Req>> queue;
@@ -138,8 +149,9 @@ struct tbsci_server {
         cv_done.notify_all();
     }
 
+    // Builds a request's device objects (set-up thread, its own context).
     tbsci_status setup(Req &q) {
-        tbsci_ctx *c = ctx;
+        tbsci_ctx *c = sctx;
         TB_TRY(tbsci_build_strings(c, q.r.norb, q.r.nalpha, q.full_a ? nullptr : q.alpha.data(),
                                    (int64_t)q.alpha.size(), &q.sa));
         TB_TRY(tbsci_build_strings(c, q.r.norb, q.r.nbeta, q.full_b ? nullptr : q.beta.data(), (int64_t)q.beta.size(),
@@ -160,7 +172,43 @@ struct tbsci_server {
         o.stream = (tbsci_stream)q.stream;
         TB_TRY(tbsci::engine_create(c, q.ham, q.plan, q.r.nroots, &o, &q.eng));
         TB_CUDA(c, cudaEventCreateWithFlags(&q.ready, cudaEventDisableTiming));
+        tbsci::engine_set_ctx(q.eng, ctx);  // polled and driven by the scheduler from here on
         return TBSCI_OK;
+    }
+
+    void setup_loop() {
+        cudaSetDevice(opts.device);
+        for (;;) {
+            std::pair<Req *, bool> job;
+            {
+                std::unique_lock<std::mutex> lk(smu);
+                scv.wait(lk, [&] { return setup_stop || !setup_q.empty(); });
+                if (setup_q.empty()) break;  // stopping, nothing left
+                job = setup_q.front();
+                setup_q.pop_front();
+            }
+            const tbsci_status st = job.second ? TBSCI_ENOMEM : setup(*job.first);
+            std::lock_guard<std::mutex> lk(smu);
+            setup_done.push_back({job.first, st});
+        }
+    }
+
+    // Moves requests whose set-up finished into the running set (or ends them).
+    bool collect_setups() {
+        std::vector<std::pair<Req *, tbsci_status>> done_now;
+        {
+            std::lock_guard<std::mutex> lk(smu);
+            done_now.swap(setup_done);
+        }
+        for (auto &d : done_now) {
+            auto it = std::find_if(in_setup.begin(), in_setup.end(),
+                                   [&](const std::unique_ptr<Req> &x) { return x.get() == d.first; });
+            std::unique_ptr<Req> q = std::move(*it);
+            in_setup.erase(it);
+            if (d.second != TBSCI_OK) finish(q, d.second);
+            else active.push_back(std::move(q));
+        }
+        return !done_now.empty();
     }
 
     // Admission in arrival order while a slot and the budget allow.
@@ -170,12 +218,12 @@ struct tbsci_server {
             std::unique_ptr<Req> q;
             {
                 std::lock_guard<std::mutex> lk(mu);
-                if (queue.empty() || (int)active.size() >= opts.max_active) break;
+                if (queue.empty() || (int)(active.size() + in_setup.size()) >= opts.max_active) break;
                 Req &f = *queue.front();
                 if (f.bytes > opts.hbm_budget) {
                     q = std::move(queue.front());
                     queue.pop_front();
-                } else if (used + f.bytes > opts.hbm_budget && !active.empty()) {
+                } else if (used + f.bytes > opts.hbm_budget && !(active.empty() && in_setup.empty())) {
                     break;  // wait until running solves release memory
                 } else {
                     q = std::move(queue.front());
@@ -191,20 +239,21 @@ struct tbsci_server {
             ++admissions;
             q->t_admit = now();
             used += q->bytes;
-            tbsci_status st = (opts.fail_admission_at > 0 && admissions == opts.fail_admission_at)
-                                  ? TBSCI_ENOMEM
-                                  : setup(*q);
-            if (st != TBSCI_OK) {
-                finish(q, st);
-                continue;
+            const bool inject = opts.fail_admission_at > 0 && admissions == opts.fail_admission_at;
+            Req *raw = q.get();
+            in_setup.push_back(std::move(q));
+            {
+                std::lock_guard<std::mutex> lk(smu);
+                setup_q.push_back({raw, inject});
             }
-            active.push_back(std::move(q));
+            scv.notify_one();
         }
         return any;
     }
 
     void round() {
         bool progressed = admit();
+        progressed |= collect_setups();
         // host logic of every solve whose device phase has completed
         for (size_t i = 0; i < active.size(); ++i) {
             bool prog = false;
@@ -286,8 +335,8 @@ struct tbsci_server {
         for (;;) {
             {
                 std::unique_lock<std::mutex> lk(mu);
-                if (stop && active.empty()) break;
-                if (queue.empty() && active.empty()) {
+                if (stop && active.empty() && in_setup.empty()) break;
+                if (queue.empty() && active.empty() && in_setup.empty()) {
                     cv_work.wait_for(lk, std::chrono::milliseconds(20));
                     continue;
                 }
@@ -309,9 +358,16 @@ tbsci_status tbsci_server_create(const tbsci_server_opts *o, tbsci_server **out)
     if (srv->opts.max_queue <= 0) srv->opts.max_queue = 4096;
     tbsci_status st = tbsci_create(srv->opts.device, &srv->ctx);
     if (st != TBSCI_OK) return st;
+    st = tbsci_create(srv->opts.device, &srv->sctx);
+    if (st != TBSCI_OK) {
+        tbsci_destroy(srv->ctx);
+        return st;
+    }
     if (srv->opts.tune_cache) {
         st = tbsci_tune_cache_load(srv->ctx, srv->opts.tune_cache);
+        if (st == TBSCI_OK) st = tbsci_tune_cache_load(srv->sctx, srv->opts.tune_cache);
         if (st != TBSCI_OK) {
+            tbsci_destroy(srv->sctx);
             tbsci_destroy(srv->ctx);
             return st;
         }
@@ -320,11 +376,13 @@ tbsci_status tbsci_server_create(const tbsci_server_opts *o, tbsci_server **out)
     cudaDeviceGetStreamPriorityRange(&srv->prio_low, &srv->prio_high);
     if (cudaStreamCreateWithPriority(&srv->sstream, cudaStreamNonBlocking, srv->prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&srv->sig_done, cudaEventDisableTiming) != cudaSuccess) {
+        tbsci_destroy(srv->sctx);
         tbsci_destroy(srv->ctx);
         return TBSCI_ECUDA;
     }
     srv->t0 = Clock::now();
     tbsci_server *raw = srv.get();
+    srv->setup_th = std::thread([raw] { raw->setup_loop(); });
     srv->th = std::thread([raw] { raw->loop(); });
     *out = srv.release();
     return TBSCI_OK;
@@ -398,12 +456,19 @@ void tbsci_server_destroy(tbsci_server *srv) {
         srv->cv_work.notify_all();
     }
     if (srv->th.joinable()) srv->th.join();
+    {
+        std::lock_guard<std::mutex> lk(srv->smu);
+        srv->setup_stop = true;
+    }
+    srv->scv.notify_all();
+    if (srv->setup_th.joinable()) srv->setup_th.join();
     for (auto &q : dropped) srv->finish(q, TBSCI_EBUSY);
     cudaSetDevice(srv->opts.device);
     if (srv->sig_done) cudaEventDestroy(srv->sig_done);
     if (srv->sstream) cudaStreamDestroy(srv->sstream);
-    tbsci_ctx *ctx = srv->ctx;
+    tbsci_ctx *ctx = srv->ctx, *sctx = srv->sctx;
     delete srv;
+    tbsci_destroy(sctx);
     tbsci_destroy(ctx);
 }
 

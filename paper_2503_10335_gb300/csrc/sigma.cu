@@ -309,28 +309,38 @@ __global__ void __launch_bounds__(kThreads) k_sigma_rest_pair(SigArgs<float> A) 
     sigma_row<float, 2, STAGE, false, kThreads, true, true>(A, A.rowsa[blockIdx.x], smem_raw);
 }
 
-// One launch over the alpha rows of several jobs (a job = one vector of one
-// space): CTA b serves row b - cta_off[j] of job j, the last j with
-// cta_off[j] <= b. Jobs are independent, so results equal per-job launches.
+// One persistent launch over the alpha rows of several jobs (a job = one vector
+// of one space): the grid is what fits on the GPU at once, and each CTA claims
+// the next row of the concatenated job list from a device counter until the
+// list is exhausted. Row b is row b - cta_off[j] of job j, the last j with
+// cta_off[j] <= b; jobs are ordered heaviest rows first, each job's rows in its
+// own work order. Jobs are independent, so results equal per-job launches.
 template <typename T, int kThreads>
 __global__ void __launch_bounds__(kThreads) k_sigma_batch(const SigArgs<T> *__restrict__ jobs,
-                                                          const int64_t *__restrict__ cta_off, int njobs) {
+                                                          const int64_t *__restrict__ cta_off, int njobs,
+                                                          int64_t nrows, int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SigArgs<T> sA;
-    __shared__ int64_t sRow;
-    if (threadIdx.x == 0) {
-        const int64_t b = blockIdx.x;
-        int lo = 0, hi = njobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (cta_off[mid] <= b) lo = mid;
-            else hi = mid - 1;
+    __shared__ int64_t sRow, sNext;
+    for (;;) {
+        if (threadIdx.x == 0) sNext = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t b = sNext;
+        if (b >= nrows) break;  // block-uniform
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = njobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cta_off[mid] <= b) lo = mid;
+                else hi = mid - 1;
+            }
+            sA = jobs[lo];
+            sRow = sA.rowsa[b - cta_off[lo]];
         }
-        sA = jobs[lo];
-        sRow = sA.rowsa[b - cta_off[lo]];
+        __syncthreads();
+        sigma_row<T, 1, true, true, kThreads>(sA, sRow, smem_raw);
+        __syncthreads();  // sA, sRow and shared memory are reused by the next row
     }
-    __syncthreads();
-    sigma_row<T, 1, true, true, kThreads>(sA, sRow, smem_raw);
 }
 
 // Hd(Ia,Ib) = ecore + E_a(Ia) + E_b(Ib) + sum_{p in Ia} U[pp][Ib]
@@ -527,14 +537,33 @@ tbsci_status launch_typed(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, c
     return TBSCI_OK;
 }
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 256;  // CTA size of jobs whose space has no tuned shape
+
+template <typename T, int TH>
+tbsci_status launch_batch_th(tbsci_ctx *ctx, const SigArgs<T> *dargs, const int64_t *doff, int njobs, int64_t rows,
+                             int *counter, size_t smem, cudaStream_t st) {
+    auto kern = k_sigma_batch<T, TH>;
+    TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TH, smem));
+    const int64_t grid = std::min<int64_t>(rows, (int64_t)std::max(1, per_sm) * ctx->num_sms);
+    TB_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
+    kern<<<(unsigned)grid, TH, smem, st>>>(dargs, doff, njobs, rows, counter);
+    TB_CUDA(ctx, cudaGetLastError());
+    return TBSCI_OK;
+}
 
 template <typename T>
 tbsci_status launch_batch_typed(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs, cudaStream_t st, BatchScratch *scr) {
-    std::vector<SigArgs<T>> args;
-    std::vector<int64_t> off;
-    size_t smem = 0;
-    int64_t ctas = 0;
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    // one persistent launch per CTA size: each space's tuned size when it has one
+    struct Item {
+        SigArgs<T> a;
+        double row_work;
+        int threads;
+    };
+    std::vector<Item> items;
+    size_t smem[3] = {0, 0, 0};
     for (int j = 0; j < njobs; ++j) {
         SigArgs<T> A = make_args<T>(jobs[j].ham, jobs[j].plan);
         if (A.la == 0 || A.lb == 0) continue;
@@ -544,19 +573,45 @@ tbsci_status launch_batch_typed(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
                                    static_cast<T *>(jobs[j].s), jobs[j].nvec, st));
             continue;
         }
-        smem = std::max(smem, sm);
+        const Plan *P = jobs[j].plan;
+        int th = P->tune_threads[ti] > 0 && P->tune_threads[ti] <= 512 ? P->tune_threads[ti] : kBatchThreads;
+        const int g = th == 512 ? 2 : th == 256 ? 1 : 0;
+        th = g == 2 ? 512 : g == 1 ? 256 : 128;
+        smem[g] = std::max(smem[g], sm);
+        const double work = (double)P->counts.nnz / (double)std::max<int64_t>(1, A.la);
         for (int v = 0; v < jobs[j].nvec; ++v) {
             A.C = static_cast<const T *>(jobs[j].c) + (size_t)v * A.vstride;
             A.S = static_cast<T *>(jobs[j].s) + (size_t)v * A.vstride;
-            args.push_back(A);
-            off.push_back(ctas);
-            ctas += A.la;
+            items.push_back({A, work, th});
         }
     }
-    if (args.empty()) return TBSCI_OK;
-    TB_CHECK(ctx, ctas <= INT32_MAX, TBSCI_EINVAL, "batched sigma: too many rows in one launch");
+    if (items.empty()) return TBSCI_OK;
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+        return x.threads != y.threads ? x.threads > y.threads : x.row_work > y.row_work;
+    });
+    std::vector<SigArgs<T>> args;
+    std::vector<int64_t> off;
+    struct Group {
+        int threads;
+        int first, count;
+        int64_t rows;
+    };
+    std::vector<Group> groups;
+    int64_t rows = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+        if (groups.empty() || groups.back().threads != items[i].threads) {
+            groups.push_back({items[i].threads, (int)i, 0, 0});
+            rows = 0;
+        }
+        args.push_back(items[i].a);
+        off.push_back(rows);
+        rows += items[i].a.la;
+        groups.back().count++;
+        groups.back().rows = rows;
+    }
     const size_t abytes = args.size() * sizeof(SigArgs<T>), obytes = off.size() * sizeof(int64_t);
-    const size_t need = ((abytes + 255) & ~size_t(255)) + obytes;
+    const size_t aoff = (abytes + 255) & ~size_t(255), coff = (aoff + obytes + 255) & ~size_t(255);
+    const size_t need = coff + 16 * sizeof(int);
     // double-buffered pinned staging: wait for the copy that last used this half
     const int half = scr->flip ^= 1;
     if (scr->h_bytes[half] < need) {
@@ -564,6 +619,7 @@ tbsci_status launch_batch_typed(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
             TB_CUDA(ctx, cudaEventSynchronize(scr->copied[half]));
             cudaFreeHost(scr->h_stage[half]);
             scr->h_stage[half] = nullptr;
+            scr->h_bytes[half] = 0;
         }
         TB_CUDA(ctx, cudaMallocHost(&scr->h_stage[half], 2 * need));
         scr->h_bytes[half] = 2 * need;
@@ -572,16 +628,24 @@ tbsci_status launch_batch_typed(tbsci_ctx *ctx, const SigmaJob *jobs, int njobs,
     TB_CUDA(ctx, cudaEventSynchronize(scr->copied[half]));
     unsigned char *h = static_cast<unsigned char *>(scr->h_stage[half]);
     std::memcpy(h, args.data(), abytes);
-    std::memcpy(h + ((abytes + 255) & ~size_t(255)), off.data(), obytes);
+    std::memcpy(h + aoff, off.data(), obytes);
     if (scr->d_stage.n < need) TB_CUDA(ctx, scr->d_stage.alloc(2 * need));
-    TB_CUDA(ctx, cudaMemcpyAsync(scr->d_stage.p, h, need, cudaMemcpyHostToDevice, st));
+    TB_CUDA(ctx, cudaMemcpyAsync(scr->d_stage.p, h, coff, cudaMemcpyHostToDevice, st));
     TB_CUDA(ctx, cudaEventRecord(scr->copied[half], st));
     const SigArgs<T> *dargs = reinterpret_cast<const SigArgs<T> *>(scr->d_stage.p);
-    const int64_t *doff = reinterpret_cast<const int64_t *>(scr->d_stage.p + ((abytes + 255) & ~size_t(255)));
-    auto kern = k_sigma_batch<T, kBatchThreads>;
-    TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)ctas, kBatchThreads, smem, st>>>(dargs, doff, (int)args.size());
-    TB_CUDA(ctx, cudaGetLastError());
+    const int64_t *doff = reinterpret_cast<const int64_t *>(scr->d_stage.p + aoff);
+    int *counters = reinterpret_cast<int *>(scr->d_stage.p + coff);
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const Group &g = groups[gi];
+        const int sl = g.threads == 512 ? 2 : g.threads == 256 ? 1 : 0;
+        const SigArgs<T> *ga = dargs + g.first;
+        const int64_t *go = doff + g.first;
+        int *ctr = counters + gi;
+        TB_CHECK(ctx, g.rows <= INT32_MAX, TBSCI_EINVAL, "batched sigma: too many rows in one launch");
+        if (g.threads == 512) TB_TRY((launch_batch_th<T, 512>(ctx, ga, go, g.count, g.rows, ctr, smem[sl], st)));
+        else if (g.threads == 256) TB_TRY((launch_batch_th<T, 256>(ctx, ga, go, g.count, g.rows, ctr, smem[sl], st)));
+        else TB_TRY((launch_batch_th<T, 128>(ctx, ga, go, g.count, g.rows, ctr, smem[sl], st)));
+    }
     return TBSCI_OK;
 }
 
@@ -848,7 +912,7 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
         // the sample; the double-class products, transposes and combine do not
         // depend on its shape, so their full-space time is measured once and
         // added in proportion to the sample
-        if (ret == TBSCI_OK && variant(1, 0) != 0 && split_min_parts(ctx, npair, lb, ti == 0 ? 8 : 4) >= 1) {
+        if (ret == TBSCI_OK && variant(1, 0) != 0 && split_min_parts(ctx, npair, lb, ti == 0 ? 8 : 4, 4) >= 1) {
             float fixed = 0.f;
             ret = dt == TBSCI_F64
                       ? timed_split<double>(ctx, ham, plan, static_cast<const double *>(c), static_cast<double *>(s),
@@ -857,7 +921,7 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
                                            st, e0, e1, &fixed);
             const float share = fixed * (float)nrows / (float)la;
             const int split_threads[2] = {512, 1024};
-            for (int stage = 3; stage <= 4 && ret == TBSCI_OK; ++stage)
+            for (int stage = 3; stage <= 5 && ret == TBSCI_OK; ++stage)
                 for (int t = 0; t < 2 && ret == TBSCI_OK; ++t) {
                     float ms = 0.f;
                     ret = trial(1, split_threads[t], stage, dsample.p, nrows, 1, &ms);

@@ -2,13 +2,14 @@
 // Eq. 7; the classes of Sec. II.C), as three passes that keep every gather in
 // shared memory and every read of a link table or c row inside L2:
 //
-//  K1 (k_sigma_parts): one CTA per alpha row Ia, as the fused kernel, for the
-//     diagonal, the same-spin beta singles with the alpha-beta Coulomb term
-//     ([0,0], [0,1]) and the alpha singles with their alpha-beta part ([1,0],
-//     [1,1]). The c row of each alpha term is staged in shared memory in column
-//     parts, and the beta single links of every column are split by the part
-//     their target lies in (PartLayout), so each gather reads shared memory.
-//     The sigma row accumulates in global memory (one owner thread per column).
+//  K1 (k_sigma_parts): the diagonal, the same-spin beta singles with the
+//     alpha-beta Coulomb term ([0,0], [0,1]) and the alpha singles with their
+//     alpha-beta part ([1,0], [1,1]). NC CTAs serve one alpha row Ia; CTA k owns
+//     every NC-th slice of 32 columns and keeps their sigma accumulators in
+//     shared memory for the whole row. The c row of each alpha term is staged
+//     in shared memory one column part at a time, and the beta single links of
+//     every column are split by the part their target lies in (PartLayout), so
+//     every gather reads shared memory and the sigma row is written once.
 //  K2 (k_dbl_spmm on C): the alpha doubles ([2,0]) as a sparse x dense product
 //     sigma[Ia, :] += sum_{Ja} h(Ia, Ja) c[Ja, :], in column tiles. CTAs run
 //     tile by tile, so the CTAs in flight share one column tile of c in L2 and
@@ -31,17 +32,17 @@ template <typename T>
 struct SplitArgs {
     int64_t la, lb;
     const T *C;
-    T *S;
-    int npair, na, P;
+    T *S;  // K1 output: rows in the layout's column order
+    int npair, na, P, NC;
     int64_t W;
     const uint64_t *stra;
     const int64_t *a_soff;
     const int2 *a_sci;
     const T *a_sval;
     const T *Ea, *Eb;
-    const T *V;   // [npair][npair]
-    const T *U1;  // [npair][lb], columns in permb order
-    const int32_t *permb, *rowsa;
+    const T *V;  // [npair][npair]
+    const T *U;  // [npair][lb], columns in the layout's order
+    const int32_t *perm, *rowsa;
     T ecore;
     const int64_t *poff;
     const int32_t *pw;
@@ -61,11 +62,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
     T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2 npair + 2]: coefficient by (pair, sign); last two zero
     int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair + 2);
     T *sC = reinterpret_cast<T *>(smem_raw + split_head_bytes<T>(npair));  // [W]: one part of a c row
-    const int64_t Ia = A.rowsa[blockIdx.x];
+    T *sAcc = sC + A.W;  // accumulators of this CTA's column slices
+    const int NC = A.NC, P = A.P;
+    const int64_t Ia = A.rowsa[blockIdx.x / NC];
+    const int kk = (int)(blockIdx.x % NC);
     const int64_t lb = A.lb, W = A.W;
-    const int P = A.P;
+    const int64_t nsl = (lb + 31) / 32;
+    const int64_t nloc = (nsl - kk + NC - 1) / NC * 32;  // local columns: slices kk, kk + NC, ...
     const T *__restrict__ C = A.C;
-    T *__restrict__ S = A.S + Ia * lb;  // the row in column order: S[j] is column permb[j]
     if (threadIdx.x == 0) {
         int k = 0;
         for (uint64_t s = A.stra[Ia]; s; s &= s - 1) {
@@ -75,6 +79,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
         sV2[2 * npair] = T(0);
         sV2[2 * npair + 1] = T(0);
     }
+    for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) sAcc[jl] = T(0);
     __syncthreads();
     const int na = A.na;
     const T eIa = A.ecore + A.Ea[Ia];
@@ -93,7 +98,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
             ha = __ldg(A.a_sval + t);
         }
         const T *__restrict__ Crow = C + Ja * lb;
-        const T *__restrict__ Urow = A.U1 + (size_t)pr * lb;
+        const T *__restrict__ Urow = A.U + (size_t)pr * lb;
         for (int p = 0; p < P; ++p) {
             const int64_t base = (int64_t)p * W, len = min(W, lb - base);
             __syncthreads();  // the previous pass is done with sC and sV2
@@ -111,23 +116,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
                 }
             for (int64_t j = threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(Crow + base + j);
             __syncthreads();
-            for (int64_t j = threadIdx.x; j < lb; j += kThreads) {
-                const int64_t ib = A.permb[j];
-                const int64_t sl = j >> 5;
-                const int lane = (int)(j & 31);
-                T acc = (self && p == 0) ? T(0) : S[j];
+            for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) {
+                const int64_t sl = (jl >> 5) * NC + kk;
+                const int lane = (int)(jl & 31);
+                const int64_t j = sl * 32 + lane;
+                if (j >= lb) continue;
+                const int64_t ib = __ldg(A.perm + j);
+                T acc = sAcc[jl];
                 if ((uint64_t)(ib - base) < (uint64_t)len) {  // the column's own c value is in this part
                     T coef;
                     if (self) {
                         coef = eIa + __ldg(A.Eb + ib);
-                        for (int k = 0; k < na; ++k) coef += __ldg(A.U1 + (size_t)sOcc[k] * lb + j);
+                        for (int k = 0; k < na; ++k) coef += __ldg(A.U + (size_t)sOcc[k] * lb + j);
                     } else {
                         coef = ha + sa * __ldg(Urow + j);
                     }
                     acc += coef * sC[ib - base];
                 }
-                const int64_t o = A.poff[sl * P + p] + lane;
-                const int w = A.pw[sl * P + p];
+                const int64_t o = __ldg(A.poff + sl * P + p) + lane;
+                const int w = __ldg(A.pw + sl * P + p);
                 const int2 *ci = A.pci + o;
                 const T *cv = A.pval + o;
                 T acc2 = T(0);
@@ -148,9 +155,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
                     if (self) x += __ldg(cv + 32 * k);
                     acc += x * sC[e.x - base];
                 }
-                S[j] = acc + acc2;
+                sAcc[jl] = acc + acc2;
             }
         }
+    }
+    __syncthreads();
+    T *__restrict__ S = A.S + Ia * lb;  // the row in the layout's column order
+    for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) {
+        const int64_t j = ((jl >> 5) * NC + kk) * 32 + (jl & 31);
+        if (j < lb) S[j] = sAcc[jl];
     }
 }
 
@@ -214,8 +227,8 @@ __global__ void k_transpose(const T *__restrict__ in, T *out, int64_t rows, int6
     }
 }
 
-// y[r][c] = p[r][ip[c]] + z[c][r]: the K1 rows (column order, ip = inverse of
-// permb) plus the transposed beta-double product (z: cols x rows)
+// y[r][c] = p[r][ip[c]] + z[c][r]: the K1 rows (in a layout's column order, ip its
+// inverse) plus the transposed beta-double product (z: cols x rows)
 template <typename T>
 __global__ void k_combine(T *y, const T *__restrict__ pz, const int32_t *__restrict__ ip, const T *__restrict__ z,
                           int64_t rows, int64_t cols) {
@@ -232,7 +245,19 @@ __global__ void k_combine(T *y, const T *__restrict__ pz, const int32_t *__restr
     }
 }
 
-// Per-part sliced-ELL layout of the beta single links in permb order (built on the host).
+// k_permute_cols equivalent for the part layout's Coulomb tables:
+// out[r][j] = in[r][perm[j]]
+__global__ void k_gather_cols(const double *__restrict__ in, int64_t rows, int64_t lb, const int32_t *__restrict__ perm,
+                              double *out, float *outf) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = blockIdx.y;
+    if (j >= lb || r >= rows) return;
+    const double v = in[r * lb + perm[j]];
+    out[r * lb + j] = v;
+    outf[r * lb + j] = (float)v;
+}
+
+// Part layout of the beta single links for `nparts` column parts (built on the host).
 tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int nparts, PartLayout **out) {
     for (auto &pl : P->parts)
         if (pl->P == nparts) {
@@ -244,67 +269,75 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
     const int64_t ns = P->B.h_soff.empty() ? 0 : P->B.h_soff[lb];
     std::vector<int2> sci(ns);
     std::vector<double> sval(ns);
-    std::vector<int32_t> perm(lb);
     if (ns) {
         TB_CUDA(ctx, cudaMemcpy(sci.data(), P->B.d_sci.p, ns * sizeof(int2), cudaMemcpyDeviceToHost));
         TB_CUDA(ctx, cudaMemcpy(sval.data(), P->B.d_sval.p, ns * sizeof(double), cudaMemcpyDeviceToHost));
     }
-    if (lb) TB_CUDA(ctx, cudaMemcpy(perm.data(), P->d_permb.p, lb * sizeof(int32_t), cudaMemcpyDeviceToHost));
     const std::vector<int64_t> &off = P->B.h_soff;
+    // links per column and part; columns ordered by count in part 0, then 1, ... (descending)
+    std::vector<int32_t> cp((size_t)lb * nparts, 0);
+    for (int64_t ib = 0; ib < lb; ++ib)
+        for (int64_t t = off[ib]; t < off[ib + 1]; ++t) ++cp[(size_t)ib * nparts + sci[t].x / W];
+    std::vector<int32_t> perm(lb), iperm(lb);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) {
+        for (int p = 0; p < nparts; ++p) {
+            const int32_t a = cp[(size_t)x * nparts + p], b = cp[(size_t)y * nparts + p];
+            if (a != b) return a > b;
+        }
+        return false;
+    });
+    for (int64_t j = 0; j < lb; ++j) iperm[perm[j]] = (int32_t)j;
     std::vector<int64_t> loff((size_t)nsl * nparts);
     std::vector<int32_t> lw((size_t)nsl * nparts);
     int64_t total = 0;
-    std::vector<int32_t> cnt(32 * (size_t)nparts);
-    for (int64_t sl = 0; sl < nsl; ++sl) {
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (int lane = 0; lane < 32; ++lane) {
-            const int64_t j = sl * 32 + lane;
-            if (j >= lb) break;
-            const int64_t ib = perm[j];
-            for (int64_t t = off[ib]; t < off[ib + 1]; ++t) ++cnt[lane * nparts + sci[t].x / W];
-        }
+    for (int64_t sl = 0; sl < nsl; ++sl)
         for (int p = 0; p < nparts; ++p) {
             int32_t w = 0;
-            for (int lane = 0; lane < 32; ++lane) w = std::max(w, cnt[lane * nparts + p]);
+            for (int64_t j = sl * 32; j < std::min(lb, sl * 32 + 32); ++j)
+                w = std::max(w, cp[(size_t)perm[j] * nparts + p]);
             loff[sl * nparts + p] = total;
             lw[sl * nparts + p] = w;
             total += 32 * (int64_t)w;
         }
-    }
     const int zero_idx = 2 * ham->npair;
     std::vector<int2> ci(std::max<int64_t>(total, 1));
     std::vector<double> v(std::max<int64_t>(total, 1), 0.0);
     std::vector<float> vf(std::max<int64_t>(total, 1), 0.f);
-    std::vector<int32_t> fill(32 * (size_t)nparts);
-    for (int64_t sl = 0; sl < nsl; ++sl) {
-        std::fill(fill.begin(), fill.end(), 0);
+    std::vector<int32_t> fill(nparts);
+    for (int64_t sl = 0; sl < nsl; ++sl)
         for (int lane = 0; lane < 32; ++lane) {
             const int64_t j = sl * 32 + lane;
+            std::fill(fill.begin(), fill.end(), 0);
             if (j < lb) {
                 const int64_t ib = perm[j];
                 for (int64_t t = off[ib]; t < off[ib + 1]; ++t) {
                     const int p = (int)(sci[t].x / W);
-                    const int64_t pos = loff[sl * nparts + p] + 32 * (int64_t)fill[lane * nparts + p]++ + lane;
+                    const int64_t pos = loff[sl * nparts + p] + 32 * (int64_t)fill[p]++ + lane;
                     ci[pos] = sci[t];
                     v[pos] = sval[t];
                     vf[pos] = (float)sval[t];
                 }
             }
             for (int p = 0; p < nparts; ++p)  // padding: the part's first column, zero coefficient
-                for (int k = fill[lane * nparts + p]; k < lw[sl * nparts + p]; ++k)
+                for (int k = fill[p]; k < lw[sl * nparts + p]; ++k)
                     ci[loff[sl * nparts + p] + 32 * (int64_t)k + lane] = make_int2((int)(p * W), zero_idx);
         }
-    }
     auto pl = std::make_unique<PartLayout>();
     pl->P = nparts;
     pl->W = W;
-    const size_t bytes = loff.size() * 12 + ci.size() * (sizeof(int2) + 12);
+    const int64_t np = ham->npair;
+    const size_t bytes = loff.size() * 12 + ci.size() * (sizeof(int2) + 12) + (size_t)lb * 8 + (size_t)np * lb * 12;
     TB_TRY(charge(ctx, bytes, "column-part link layout"));
     cudaError_t e = pl->off.alloc(loff.size());
     if (e == cudaSuccess) e = pl->w.alloc(lw.size());
     if (e == cudaSuccess) e = pl->ci.alloc(ci.size());
     if (e == cudaSuccess) e = pl->val.alloc(v.size());
     if (e == cudaSuccess) e = pl->valf.alloc(vf.size());
+    if (e == cudaSuccess) e = pl->perm.alloc(lb);
+    if (e == cudaSuccess) e = pl->iperm.alloc(lb);
+    if (e == cudaSuccess) e = pl->U.alloc((size_t)np * lb);
+    if (e == cudaSuccess) e = pl->Uf.alloc((size_t)np * lb);
     if (e == cudaSuccess && !loff.empty())
         e = cudaMemcpy(pl->off.p, loff.data(), loff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !lw.empty())
@@ -312,6 +345,14 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
     if (e == cudaSuccess) e = cudaMemcpy(pl->ci.p, ci.data(), ci.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->val.p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->valf.p, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->perm.p, perm.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->iperm.p, iperm.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_gather_cols<<<dim3((unsigned)((lb + 127) / 128), (unsigned)np), 128, 0, ctx->stream>>>(
+            P->d_U.p, np, lb, pl->perm.p, pl->U.p, pl->Uf.p);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    }
     if (e != cudaSuccess) {
         uncharge(ctx, bytes);
         return fail(ctx, e == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA,
@@ -327,7 +368,7 @@ template <typename T, int TH>
 tbsci_status launch_parts_th(tbsci_ctx *ctx, const SplitArgs<T> &A, size_t smem, cudaStream_t st) {
     auto k = k_sigma_parts<T, TH>;
     TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k<<<(unsigned)A.la, TH, smem, st>>>(A);
+    k<<<(unsigned)(A.la * A.NC), TH, smem, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
 }
@@ -366,8 +407,8 @@ SplitArgs<double> split_args<double>(const tbsci_ham *ham, const Plan *P, const 
     A.Ea = P->A.d_E.p;
     A.Eb = P->B.d_E.p;
     A.V = ham->d_V.p;
-    A.U1 = P->d_U1.p;
-    A.permb = P->d_permb.p;
+    A.U = pl->U.p;
+    A.perm = pl->perm.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = ham->ecore;
     A.poff = pl->off.p;
@@ -393,8 +434,8 @@ SplitArgs<float> split_args<float>(const tbsci_ham *ham, const Plan *P, const Pa
     A.Ea = P->A.d_Ef.p;
     A.Eb = P->B.d_Ef.p;
     A.V = ham->d_Vf.p;
-    A.U1 = P->d_U1f.p;
-    A.permb = P->d_permb.p;
+    A.U = pl->Uf.p;
+    A.perm = pl->perm.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = (float)ham->ecore;
     A.poff = pl->off.p;
@@ -413,10 +454,12 @@ const float *dval_of<float>(const SpinPlan &sp) { return sp.d_dvalf.p; }
 
 }  // namespace
 
-int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem) {
+int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc) {
     const size_t head = elem == 8 ? split_head_bytes<double>(npair) : split_head_bytes<float>(npair);
-    const size_t avail = ctx->smem_optin > head ? ctx->smem_optin - head : 0;
-    const int64_t wmax = (int64_t)(avail / elem);
+    const int64_t nsl = (lb + 31) / 32;
+    const size_t acc = (size_t)((nsl + nc - 1) / nc) * 32 * elem;
+    if (ctx->smem_optin <= head + acc) return 0;
+    const int64_t wmax = (int64_t)((ctx->smem_optin - head - acc) / elem);
     if (wmax <= 0) return 0;
     return (int)std::max<int64_t>(1, (lb + wmax - 1) / wmax);
 }
@@ -425,14 +468,19 @@ int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem) {
 // sample; its output is scratch); 2: K2, K3 and the combine alone (the part of
 // the time that does not depend on the K1 shape; sigma is not meaningful)
 template <typename T>
-tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int extra_parts,
+tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int variant,
                           int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode) {
     const int64_t la = P->A.l, lb = P->B.l;
     if (la == 0 || lb == 0) return TBSCI_OK;
-    const int pmin = split_min_parts(ctx, P->npair, lb, sizeof(T));
-    TB_CHECK(ctx, pmin >= 1, TBSCI_EINVAL, "split sigma: no room for a column part in shared memory");
+    // CTAs per alpha row: 1, 2 or 4 (the first that leaves room for a c part)
+    int nc = 1 << std::min(2, std::max(0, variant)), nparts = 0;
+    for (; nc <= 4; nc *= 2) {
+        nparts = split_min_parts(ctx, P->npair, lb, sizeof(T), nc);
+        if (nparts >= 1) break;
+    }
+    TB_CHECK(ctx, nparts >= 1 && nc <= 4, TBSCI_EINVAL, "split sigma: no room for a column part in shared memory");
     TB_CHECK(ctx, (la + 31) / 32 <= 65535, TBSCI_EINVAL, "split sigma: too many alpha strings");
-    const int nparts = (int)std::min<int64_t>(lb, pmin + std::max(0, extra_parts));
+    nparts = (int)std::min<int64_t>(lb, nparts);
     PartLayout *pl = nullptr;
     TB_TRY(build_parts(ctx, ham, P, nparts, &pl));
     const size_t need = 2 * (size_t)la * lb * sizeof(T);
@@ -449,19 +497,15 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
         }
         P->charged += need;
     }
-    if (!P->d_ipermb.p) {
-        std::vector<int32_t> perm(lb), ip(lb);
-        TB_CUDA(ctx, cudaMemcpy(perm.data(), P->d_permb.p, lb * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        for (int64_t j = 0; j < lb; ++j) ip[perm[j]] = (int32_t)j;
-        TB_CUDA(ctx, P->d_ipermb.alloc(lb));
-        TB_CUDA(ctx, cudaMemcpy(P->d_ipermb.p, ip.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice));
-    }
     SplitArgs<T> A = split_args<T>(ham, P, pl);
+    A.NC = nc;
     if (rows) {
         A.rowsa = rows;
         A.la = nrows;
     }
-    const size_t smem = split_head_bytes<T>(P->npair) + (size_t)pl->W * sizeof(T);
+    const int64_t nsl = (lb + 31) / 32;
+    const size_t smem = split_head_bytes<T>(P->npair) + (size_t)pl->W * sizeof(T) +
+                        (size_t)((nsl + nc - 1) / nc) * 32 * sizeof(T);
     T *ct = reinterpret_cast<T *>(P->d_trans.p), *sz = ct + (size_t)la * lb;
     const dim3 tb(32, 8), tgrid((unsigned)((lb + 31) / 32), (unsigned)((la + 31) / 32));
     for (int v = 0; v < nvec; ++v) {
@@ -474,14 +518,14 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
             TB_TRY(launch_dbl<T>(ctx, ct, sz, lb, la, P->B.d_doff, P->B.d_dcol.p, dval_of<T>(P->B), false, st));
         }
         if (mode != 2) {
-            // K1 rows in column order into ct (free once c^T has been used)
+            // K1 rows in the layout's column order into ct (free once c^T has been used)
             A.C = cv;
             A.S = ct;
             if (threads >= 1024) TB_TRY((launch_parts_th<T, 1024>(ctx, A, smem, st)));
             else TB_TRY((launch_parts_th<T, 512>(ctx, A, smem, st)));
         }
         if (mode == 1) continue;
-        k_combine<T><<<tgrid, tb, 0, st>>>(sv, ct, P->d_ipermb.p, sz, la, lb);
+        k_combine<T><<<tgrid, tb, 0, st>>>(sv, ct, pl->iperm.p, sz, la, lb);
         TB_CUDA(ctx, cudaGetLastError());
         // [2,0]: sigma += H_alpha,doubles c
         TB_TRY(launch_dbl<T>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, dval_of<T>(P->A), true, st));

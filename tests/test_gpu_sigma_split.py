@@ -1,5 +1,7 @@
 """The split sigma path for rows longer than shared memory (row a4-a6 at the
-norb-24 workload): the row kernel with c rows staged in column parts, plus the
+norb-24 workload): the row kernel with c rows staged in column parts (stage 3,
+4, 5: one, two or four CTAs per alpha row, each keeping the sigma accumulators
+of its share of the columns in shared memory), plus the
 alpha-double and beta-double classes as column-tiled sparse x dense products
 (the latter on the transposed vector). Each launch shape is pinned through a
 tune-cache file and compared with the oracle element by element, on spaces that
@@ -53,7 +55,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("threads,stage", [(512, 3), (1024, 4)])
+@pytest.mark.parametrize("threads,stage", [(512, 3), (1024, 4), (512, 5)])
 @pytest.mark.parametrize("n,na,nb,acnt,bcnt,nvec", CASES)
 def test_split_sigma_parity(tb, tmp_path, n, na, nb, acnt, bcnt, nvec, threads, stage, dtype):
     import torch
@@ -79,10 +81,10 @@ def test_split_sigma_parity(tb, tmp_path, n, na, nb, acnt, bcnt, nvec, threads, 
     ctx.close()
 
 
-@pytest.mark.parametrize("n,dtype,stage", [(18, "f64", 3), (18, "f64", 4), (19, "f64", 3), (19, "f32", 3)])
+@pytest.mark.parametrize("n,dtype,stage", [(18, "f64", 3), (18, "f64", 5), (19, "f64", 4), (19, "f32", 3)])
 def test_split_sigma_long_rows(tb, tmp_path, n, dtype, stage):
     """Full beta string spaces of norb 18 / 19 (48,620 / 92,378 strings; 389 KB /
-    739 KB per FP64 row, so 2 to 5 column parts) with 6 selected alpha strings:
+    739 KB per FP64 row, so many column parts) with 6 selected alpha strings:
     500 sampled rows against the oracle."""
     import torch
     na = nb = 9
