@@ -22,6 +22,10 @@ sel16_sigma = the same measurement on norb=16, 3,000 x 3,000 selected strings
          (9.0M determinants), FP64, 3 vectors.
 davidson = Davidson time to 1e-9 / 1e-5 on the 9.0M-determinant space, FP64
          and mixed precision.
+serving = the 512-request stream replayed live at twice the FP64 sequential
+         service rate through a one-slot FP64 server and through the
+         mixed-precision batching server: p50 / p99 latency, throughput and the
+         energy difference of every result (--no-serving skips it).
 --impl reference runs the oracle alone as the reference arm.
 
 Under torchrun (N > 1) every rank runs an independent replica (the path does
@@ -360,6 +364,52 @@ def run_serving(args, print_line=True):
     return out
 
 
+def run_selection_study(args):
+    """Bitstring selection loop (Sec. III.B) and coefficient distributions (Fig. 3)
+    on a synthetic Hamiltonian with the recipe's two-electron scale 0.1 (the
+    default 0.3 spreads the ground-state weight evenly over the strings): the
+    full string space of norb 14, 7+7 electrons (11.8M determinants) is solved,
+    its strings are weighed and selected at each delta, and each selected TPB
+    space is solved again. Reports sizes, energies (and their distance from the
+    full-space energy), solve times and the |c_K / c_HF| histograms."""
+    import torch
+    import paper_2503_10335_gb300 as tb
+    from tbsci_inputs import synth_hamiltonian
+    n, N = args.sel_norb, args.sel_norb // 2
+    h, eri, ecore = synth_hamiltonian(n, seed=1014, scale=0.1)
+    ctx = tb.Context(0)
+    full = tb.Space(ctx, n, N, N, h, eri, ecore)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_full, info, X = full.davidson(1, want_vectors=True, mixed=1)
+    t_full = time.perf_counter() - t0
+    c0 = X[0].contiguous()
+    c_hf = float(torch.max(torch.abs(c0)))
+    ratios, counts = full.coefficient_histogram(c0, c_hf, lo=-12, hi=0)
+    out = {"metric": METRIC, "mode": "selection_study", "norb": n, "nelec": [N, N], "two_electron_scale": 0.1,
+           "full": {"ndet": full.ndet, "energy": float(e_full[0]), "seconds": t_full,
+                    "iterations": info["iterations"], "histogram": counts.tolist()},
+           "bin_edges_c_over_c_hf": ratios.tolist(), "runs": []}
+    for delta in [float(x) for x in args.deltas.split(",")]:
+        ka, kb = full.select_by_weight(c0, delta)
+        sub = tb.Space(ctx, n, N, N, h, eri, ecore, alpha=ka, beta=kb)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, inf, Xs = sub.davidson(1, want_vectors=True, mixed=1)
+        dt = time.perf_counter() - t0
+        xs = Xs[0].contiguous()
+        _, hs = sub.coefficient_histogram(xs, float(torch.max(torch.abs(xs))), lo=-12, hi=0)
+        out["runs"].append({"delta": delta, "n_alpha": len(ka), "n_beta": len(kb), "ndet": sub.ndet,
+                            "fraction_of_full": sub.ndet / full.ndet, "energy": float(e[0]),
+                            "minus_full_Eh": float(e[0] - e_full[0]), "seconds": dt,
+                            "iterations": inf["iterations"], "histogram": hs.tolist()})
+        sub.close()
+        del Xs, xs
+    full.close()
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_precision_study(args):
     """Davidson on one workload with every low-precision sigma type: the energy
     reached by the low-precision phase, its error against the final FP64-refined
@@ -538,12 +588,17 @@ def main():
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the norb=16 selected-space sigma leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-stream leg of the default run")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--serving", action="store_true", help="serving stream instead of the sigma bench")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-cache", default=None,
                     help="tune-cache file loaded into the context (with --no-autotune: pins the launch shape)")
     ap.add_argument("--precision-study", action="store_true")
+    ap.add_argument("--selection-study", action="store_true",
+                    help="bitstring selection loop and coefficient histograms")
+    ap.add_argument("--sel-norb", type=int, default=14)
+    ap.add_argument("--deltas", default="1e-2,1e-3,1e-4,1e-5")
     ap.add_argument("--modes", default="1,2,3", help="Davidson mixed modes for --precision-study")
     ap.add_argument("--max-iter", type=int, default=0)
     ap.add_argument("--basis-f32", action="store_true", help="--precision-study: FP32-stored Davidson basis")
@@ -563,6 +618,8 @@ def main():
         return run_serving(args)
     if args.precision_study:
         return run_precision_study(args)
+    if args.selection_study:
+        return run_selection_study(args)
 
     import torch
     import paper_2503_10335_gb300 as tb
@@ -617,6 +674,11 @@ def main():
     if not args.no_davidson and rank == 0:
         dav = _davidson_leg(tb, ctx, WORKLOADS["sel16"])
 
+    serving = None
+    if not args.no_serving and rank == 0 and ws == 1:
+        serving = run_serving(args, print_line=False)
+        serving.pop("metric", None)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -625,7 +687,7 @@ def main():
             "config": dict(rec["config"], parallelism="replicas" if ws > 1 else "single"),
             "roofline": rec["roofline"], "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": rec["launches_per_step"] * args.steps,
-            "clocks": rec["clocks"], "sel16_sigma": extra, "davidson": dav,
+            "clocks": rec["clocks"], "sel16_sigma": extra, "davidson": dav, "serving": serving,
             "counts": rec["counts"], "setup_seconds": rec["setup_seconds"], "autotune_ms": rec["autotune_ms"],
             "step_ms_min": rec["step_ms_min"], "step_ms_max": rec["step_ms_max"],
         }

@@ -249,13 +249,22 @@ typedef struct tbsci_sigma_counts {
     int32_t tuned_nv[2];      /* autotuned vectors per CTA for F64 / F32 */
     int32_t tuned_stage[2];   /* autotuned shared-memory use for F64 / F32: 0 c row
                                  staged and sigma row accumulated in shared memory
-                                 where they fit, 1 sigma row only, 2 neither */
+                                 where they fit, 1 sigma row only, 2 neither;
+                                 3, 4, 5: the split path for rows longer than shared
+                                 memory with 1, 2 or 4 CTAs per alpha row (the row
+                                 kernel stages c rows in column parts and keeps its
+                                 share of the sigma row in shared memory; the
+                                 same-spin double classes run as column-tiled
+                                 products) */
     int32_t tuned_rest[2];    /* tensor-core types: autotuned mode and CTA size of
                                  the SIMT pass for the classes the tensor cores
                                  leave out (0, 0 = defaults). Modes: 0 c row and
                                  sigma row in shared memory where they fit, 1 c row
                                  only, 2 neither, 3 two alpha rows per CTA sharing
-                                 the beta links (even l_alpha; else as 1) */
+                                 the beta links (even l_alpha; else as 1), 4 the
+                                 column-tiled products of the split path (beta
+                                 classes on the transposed vector, alpha doubles on
+                                 c) */
 } tbsci_sigma_counts;
 tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                                     const tbsci_tables *b, tbsci_sigma_counts *out);
@@ -312,10 +321,13 @@ typedef struct tbsci_davidson_info {
 
 /* Lowest nroots (1..8) eigenpairs of H on a x b by standard Davidson (Sec. III.A)
  * with restart to the lowest restart_keep Ritz vectors when the basis is full
- * (Sec. III.C). Memory: 2 * max_subspace + restart_keep + 3 * nroots + 1 FP64
+ * (Sec. III.C); an FP64 basis also keeps the previous iteration's Ritz vectors
+ * at a restart (orthonormalised against the kept ones, while a slot is left for
+ * a correction). Memory: 2 * max_subspace + restart_keep + 4 * nroots + 1 FP64
  * vectors (+ 2 * nroots FP32 in mixed mode); with basis_f32, 3 * nroots + 1 FP64
- * vectors plus the larger of 2 * max_subspace + restart_keep FP32 vectors and
- * 2 * m_ref + m_ref / 2 FP64 vectors (m_ref = the refinement basis size). Guess: guess k is the unit vector
+ * vectors plus the larger of 2 * max_subspace + restart_keep + nroots FP32
+ * vectors and 2 * m_ref + m_ref / 2 + nroots FP64 vectors (m_ref = the
+ * refinement basis size). Guess: guess k is the unit vector
  * at the k-th lowest H_KK (ties by K) plus 0.1 (1 + ((j + k) mod 4)) / 4 times
  * the unit vector at the (nroots + j)-th lowest, j < 4, orthonormalised, so
  * every symmetry sector is present. Each iteration: Rayleigh

@@ -390,7 +390,7 @@ def solve_pruned(ps: PrunedSpace, h, eri, ecore, nroots, nthreads=0, **kw):
 # --------------------------------------------------------------- Davidson
 
 def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, max_iter=1000,
-             restart_keep=None):
+             restart_keep=None, restart_prev=True):
     """Standard Davidson (Sec. III.A) for the lowest ``nroots`` eigenpairs.
 
     Steps, in order, each iteration: Rayleigh matrix G = V^T W; eigenpairs of G;
@@ -400,7 +400,10 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     below 1e-8 clamped to +-1e-8, zero -> +1e-8); when the subspace would exceed
     ``max_subspace`` restart from the lowest ``restart_keep`` Ritz vectors
     (default ``max(nroots, max_subspace // 2)``; the paper's restart scheme,
-    Sec. III.C, keeps a bounded number of vectors and says no more); orthogonalise
+    Sec. III.C, keeps a bounded number of vectors and says no more), and with
+    ``restart_prev`` also the previous iteration's Ritz vectors, orthonormalised
+    against the kept ones in the coefficient space of the basis (while room is
+    left for one correction); orthogonalise
     the new directions twice against the basis and each other, normalise, and
     drop those whose norm fell below 1e-10 of their pre-projection norm.
 
@@ -432,6 +435,7 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     W = apply_h(V)
     nsigma = nroots
     theta_prev = None
+    p_prev = None  # the previous iteration's Ritz vectors, coefficients in the current basis
     info = dict(iterations=0, converged=False, nsigma=0)
     for it in range(1, max_iter + 1):
         G = V @ W.T
@@ -457,9 +461,25 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
             small = np.abs(d) < 1e-8
             d[small] = np.where(d[small] < 0, -1e-8, 1e-8)
             T.append(R[k] / d)
+        p_cur = Y
         if V.shape[0] + len(T) > max_subspace:
             keep = min(restart_keep, V.shape[0])
-            V, W = Yall[:, :keep].T @ V, Yall[:, :keep].T @ W
+            Q = Yall[:, :keep]
+            if restart_prev and p_prev is not None:
+                extra = []
+                for z in p_prev.T:
+                    z0 = np.linalg.norm(z)
+                    for _ in range(2):
+                        z = z - Q @ (Q.T @ z)
+                        for u in extra:
+                            z = z - (u @ z) * u
+                    nz = np.linalg.norm(z)
+                    if nz > 1e-8 * z0 and keep + len(extra) + 1 < max_subspace:
+                        extra.append(z / nz)
+                if extra:
+                    Q = np.hstack([Q, np.array(extra).T])
+            V, W = Q.T @ V, Q.T @ W
+            p_cur = Q.T @ Y
         newV = []
         for t in T:
             t0 = np.linalg.norm(t)
@@ -477,6 +497,7 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
             nsigma += len(newV)
             V = np.vstack([V, Vn])
             W = np.vstack([W, Wn])
+        p_prev = np.vstack([p_cur, np.zeros((V.shape[0] - p_cur.shape[0], nroots))])
     info["converged"] = False
     return theta_prev, X, info
 

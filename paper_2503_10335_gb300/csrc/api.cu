@@ -374,7 +374,7 @@ tbsci_status tbsci_tune_cache_load(tbsci_ctx *ctx, const char *path) {
                                   &e.nv[0], &e.stage[0], &e.threads[1], &e.nv[1], &e.stage[1], &e.rest_mode,
                                   &e.rest_threads);
         bool ok = n == 11 && k0 >= 1 && k0 <= 64 && k1 >= 0 && k2 >= 0 && threads_ok(e.rest_threads) &&
-                  e.rest_mode >= 0 && e.rest_mode <= 3;
+                  e.rest_mode >= 0 && e.rest_mode <= 4;
         for (int i = 0; i < 2 && ok; ++i)
             ok = threads_ok(e.threads[i]) && e.nv[i] >= 0 && e.nv[i] <= 4 && e.stage[i] >= 0 && e.stage[i] <= 5 &&
                  (e.stage[i] < 3 ? e.threads[i] != 1024 : (e.threads[i] == 0 || e.threads[i] >= 512));

@@ -33,7 +33,9 @@ constexpr int kMB = 4;  // rows of B per dot block
 // work goes to padding (FP64 throughput bounds these dots on this GPU).
 template <typename T, int MB = kMB>
 __global__ void __launch_bounds__(kDotThreads) k_dots(const T *__restrict__ A, int ma, const T *__restrict__ B, int mb,
-                                                      int64_t N, double *partial, int ldp) {
+                                                      int64_t N, double *partial, int ldp,
+                                                      const int *__restrict__ skip = nullptr) {
+    if (skip && *skip) return;  // a pass the device decided is not needed
     __shared__ double sh[kDotThreads / 32][kMA * MB];
     const int i0 = blockIdx.y * kMA, j0 = blockIdx.z * MB;
     const int na = min(kMA, ma - i0), nb = min(MB, mb - j0);
@@ -100,7 +102,9 @@ constexpr int kMaxOut = 8;
 // flight); the accumulator tile KOUT x U stays small enough for 4 CTAs per SM.
 template <typename TA, typename TO, int KOUT>
 __global__ void __launch_bounds__(256) k_lincomb(const TA *__restrict__ A, int m, TO *out, int kout, int64_t N,
-                                                 double beta, const double *__restrict__ Y, double yscale) {
+                                                 double beta, const double *__restrict__ Y, double yscale,
+                                                 const int *__restrict__ skip) {
+    if (skip && *skip) return;
     constexpr int U = KOUT >= 4 ? 2 : 4;
     __shared__ double sY[kMaxBasis * KOUT];
     for (int x = threadIdx.x; x < m * kout; x += blockDim.x) sY[x] = yscale * Y[x];
@@ -144,11 +148,21 @@ __global__ void __launch_bounds__(256) k_lincomb(const TA *__restrict__ A, int m
 
 template <typename TA, typename TO>
 void launch_lincomb(int grid, cudaStream_t st, const TA *A, int m, TO *out, int kout, int64_t N, double beta,
-                    const double *Y, double yscale) {
-    if (kout <= 1) k_lincomb<TA, TO, 1><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale);
-    else if (kout <= 2) k_lincomb<TA, TO, 2><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale);
-    else if (kout <= 4) k_lincomb<TA, TO, 4><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale);
-    else k_lincomb<TA, TO, 8><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale);
+                    const double *Y, double yscale, const int *skip = nullptr) {
+    if (kout <= 1) k_lincomb<TA, TO, 1><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
+    else if (kout <= 2) k_lincomb<TA, TO, 2><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
+    else if (kout <= 4) k_lincomb<TA, TO, 4><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
+    else k_lincomb<TA, TO, 8><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
+}
+
+// Second Gram-Schmidt pass needed? "Twice is enough" (Daniel-Gragg-Kaufman-
+// Stewart, eta = 1/sqrt(2)): skip it when every correction kept at least half of
+// its squared norm in the first pass. norms[2 j] = ||t_j||^2 before, after[j] after.
+__global__ void k_gs_decide(const double *__restrict__ norms, const double *__restrict__ after, int nb, int *skip) {
+    if (threadIdx.x != 0) return;
+    int ok = 1;
+    for (int j = 0; j < nb; ++j) ok &= (after[j * (nb + 1)] >= 0.5 * norms[2 * j]) ? 1 : 0;
+    *skip = ok;
 }
 
 // y = x / sqrt(*nrm2) (zero when the norm is zero); y may be x
@@ -384,6 +398,7 @@ struct DavEngine {
     int lgrid = 0;    // blocks of the linear combinations (no reduction: sized for occupancy)
     int rgrid = 0;    // blocks of the residual kernel (fixed per problem size, like nblocks)
     DevBuf<double> V, W, X, WY, T, diag, R, partial, red, dY, dY2, dtheta, scal, coef;
+    DevBuf<int> gs_skip;  // 1: the second block Gram-Schmidt pass is not needed
     DevBuf<float> v32, w32;
     // FP32-stored basis and images (basis_f32, low-precision phase only); the
     // Rayleigh problem is then solved against the overlap Sm = V^T V
@@ -398,6 +413,11 @@ struct DavEngine {
     bool mixed_mode = false;  // the solve has a low-precision phase
     tbsci_dtype lowp = TBSCI_F32;  // sigma type of the low-precision phase
     std::vector<double> G, theta, theta_prev, rnorm, e32, Yv;
+    // the previous iteration's Ritz vectors as coefficients [i][k] over the first
+    // p_rows basis vectors (later vectors have zero coefficients); kept beside the
+    // lowest Ritz vectors at a restart of an FP64 basis
+    std::vector<double> p_prev;
+    int p_rows = 0;
     std::vector<int> todo;
     int it = 0, it32 = 0, stall32 = 0, nsig = 0, nsig32 = 0;
     double best32 = INFINITY;
@@ -420,25 +440,26 @@ struct DavEngine {
     void *vs(int k) { return b32 ? (void *)(V32.p + (size_t)k * N) : (void *)(V.p + (size_t)k * N); }
     void *ws(int k) { return b32 ? (void *)(W32.p + (size_t)k * N) : (void *)(W.p + (size_t)k * N); }
 
-    // out[i][j] = A_i . B_j over basis-typed rows, FP64 accumulation
-    tbsci_status dots(const void *A, int ma, const void *B, int mb, double *out) {
+    // out[i][j] = A_i . B_j over basis-typed rows, FP64 accumulation; skip: a
+    // device flag that, when set, turns the product into no work
+    tbsci_status dots(const void *A, int ma, const void *B, int mb, double *out, const int *skip = nullptr) {
         const int ldp = ma * mb;
         if (mb == 1) {  // one column (Rayleigh columns, projections of one vector, norms)
             dim3 grid(nblocks, (ma + kMA - 1) / kMA, 1);
             if (b32)
                 k_dots<float, 1><<<grid, kDotThreads, 0, st>>>((const float *)A, ma, (const float *)B, mb, N,
-                                                               partial.p, ldp);
+                                                               partial.p, ldp, skip);
             else
                 k_dots<double, 1><<<grid, kDotThreads, 0, st>>>((const double *)A, ma, (const double *)B, mb, N,
-                                                                partial.p, ldp);
+                                                                partial.p, ldp, skip);
         } else {
             dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + kMB - 1) / kMB);
             if (b32)
                 k_dots<float><<<grid, kDotThreads, 0, st>>>((const float *)A, ma, (const float *)B, mb, N, partial.p,
-                                                            ldp);
+                                                            ldp, skip);
             else
                 k_dots<double><<<grid, kDotThreads, 0, st>>>((const double *)A, ma, (const double *)B, mb, N,
-                                                             partial.p, ldp);
+                                                             partial.p, ldp, skip);
         }
         TB_CUDA(ctx, cudaGetLastError());
         k_reduce_partials<<<(ldp + 127) / 128, 128, 0, st>>>(partial.p, nblocks, ldp, ldp, out);
@@ -446,9 +467,10 @@ struct DavEngine {
         return TBSCI_OK;
     }
     // basis-typed out = beta * out + yscale * sum_i Y[i][k] A_i
-    tbsci_status lincomb(const void *A, int mm, void *out, int kout, double beta, const double *Ydev, double yscale) {
-        if (b32) launch_lincomb(lgrid, st, (const float *)A, mm, (float *)out, kout, N, beta, Ydev, yscale);
-        else launch_lincomb(lgrid, st, (const double *)A, mm, (double *)out, kout, N, beta, Ydev, yscale);
+    tbsci_status lincomb(const void *A, int mm, void *out, int kout, double beta, const double *Ydev, double yscale,
+                         const int *skip = nullptr) {
+        if (b32) launch_lincomb(lgrid, st, (const float *)A, mm, (float *)out, kout, N, beta, Ydev, yscale, skip);
+        else launch_lincomb(lgrid, st, (const double *)A, mm, (double *)out, kout, N, beta, Ydev, yscale, skip);
         TB_CUDA(ctx, cudaGetLastError());
         return TBSCI_OK;
     }
@@ -518,6 +540,7 @@ struct DavEngine {
         TB_CUDA(ctx, dtheta.alloc(kMaxOut));
         TB_CUDA(ctx, scal.alloc(2 * kMaxOut));
         TB_CUDA(ctx, coef.alloc((size_t)m_max * kMaxOut));
+        TB_CUDA(ctx, gs_skip.alloc(1));
         TB_CUDA(ctx, cudaMallocHost(&hG, (size_t)2 * m_max * m_max * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hY, (size_t)m_max * m_max * sizeof(double)));
         TB_CUDA(ctx, cudaMallocHost(&hY2, (size_t)m_max * m_max * sizeof(double)));
@@ -764,6 +787,7 @@ struct DavEngine {
             f32 = false;
             if (b32) TB_TRY(leave_basis32());
             else TB_CUDA(ctx, cudaMemcpyAsync(V.p, X.p, (size_t)nroots * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            p_rows = 0;
             m = 0;
             sig_lo = 0;
             sig_hi = nroots;
@@ -785,22 +809,62 @@ struct DavEngine {
         for (int k = 0; k < nroots; ++k)
             if (rnorm[k] >= (f32 ? tol_rm : tol_r)) todo.push_back(k);
         bool restarted = false;
+        // Ritz vectors of this iteration as coefficients over the current basis
+        std::vector<double> p_cur((size_t)m * nroots);
+        for (int i = 0; i < m; ++i)
+            for (int k = 0; k < nroots; ++k) p_cur[(size_t)i * nroots + k] = Yv[(size_t)i * m + k];
         if (m + (int)todo.size() > m_max) {
-            // thick restart: keep the lowest `kk` Ritz vectors and their images
+            // thick restart: keep the lowest `kk` Ritz vectors and their images, and
+            // (FP64 basis) the previous iteration's Ritz vectors orthonormalised
+            // against them in coefficient space, while room is left for a correction
             const int kk = std::min(keep, m);
-            if (b32 && !R32.p) TB_CUDA(ctx, R32.alloc((size_t)keep * N));
-            if (!b32 && !R.p) TB_CUDA(ctx, R.alloc((size_t)keep * N));
-            // coefficients in chunks of up to 8 Ritz vectors, each chunk row-major [i][k]
-            for (int k0 = 0; k0 < kk; k0 += kMaxOut) {
-                const int kc = std::min(kMaxOut, kk - k0);
-                for (int i = 0; i < m; ++i)
-                    for (int k = 0; k < kc; ++k) hY2[(size_t)k0 * m + (size_t)i * kc + k] = Yv[(size_t)i * m + k0 + k];
+            std::vector<double> Q((size_t)m * (kk + nroots), 0.0);  // columns of the new basis, [i][col]
+            const int ldq = kk + nroots;
+            for (int i = 0; i < m; ++i)
+                for (int k = 0; k < kk; ++k) Q[(size_t)i * ldq + k] = Yv[(size_t)i * m + k];
+            int kq = kk;
+            if (!b32 && p_rows > 0) {
+                for (int k = 0; k < nroots && kq + 1 < m_max; ++k) {
+                    std::vector<double> z(m, 0.0);
+                    for (int i = 0; i < std::min(p_rows, m); ++i) z[i] = p_prev[(size_t)i * nroots + k];
+                    double z0 = 0.0;
+                    for (double x : z) z0 += x * x;
+                    for (int pass = 0; pass < 2; ++pass)
+                        for (int c = 0; c < kq; ++c) {
+                            double d = 0.0;
+                            for (int i = 0; i < m; ++i) d += Q[(size_t)i * ldq + c] * z[i];
+                            for (int i = 0; i < m; ++i) z[i] -= d * Q[(size_t)i * ldq + c];
+                        }
+                    double nz = 0.0;
+                    for (double x : z) nz += x * x;
+                    if (!(nz > 1e-16 * z0) || z0 == 0.0) continue;
+                    nz = std::sqrt(nz);
+                    for (int i = 0; i < m; ++i) Q[(size_t)i * ldq + kq] = z[i] / nz;
+                    ++kq;
+                }
             }
-            TB_CUDA(ctx, cudaMemcpyAsync(dY2.p, hY2, (size_t)m * kk * sizeof(double), cudaMemcpyHostToDevice, st));
+            if (b32 && !R32.p) TB_CUDA(ctx, R32.alloc((size_t)(keep + nroots) * N));
+            if (!b32 && !R.p) TB_CUDA(ctx, R.alloc((size_t)(keep + nroots) * N));
+            // coefficients in chunks of up to 8 columns, each chunk row-major [i][k]
+            for (int k0 = 0; k0 < kq; k0 += kMaxOut) {
+                const int kc = std::min(kMaxOut, kq - k0);
+                for (int i = 0; i < m; ++i)
+                    for (int k = 0; k < kc; ++k) hY2[(size_t)k0 * m + (size_t)i * kc + k] = Q[(size_t)i * ldq + k0 + k];
+            }
+            // the Ritz vectors of this iteration in the new basis: Q^T p_cur
+            std::vector<double> pn((size_t)kq * nroots, 0.0);
+            for (int c = 0; c < kq; ++c)
+                for (int k = 0; k < nroots; ++k) {
+                    double d = 0.0;
+                    for (int i = 0; i < m; ++i) d += Q[(size_t)i * ldq + c] * p_cur[(size_t)i * nroots + k];
+                    pn[(size_t)c * nroots + k] = d;
+                }
+            p_cur.swap(pn);
+            TB_CUDA(ctx, cudaMemcpyAsync(dY2.p, hY2, (size_t)m * kq * sizeof(double), cudaMemcpyHostToDevice, st));
             for (int half = 0; half < 2; ++half) {
                 void *src = half == 0 ? vs(0) : ws(0);
-                for (int k0 = 0; k0 < kk; k0 += kMaxOut) {
-                    const int kc = std::min(kMaxOut, kk - k0);
+                for (int k0 = 0; k0 < kq; k0 += kMaxOut) {
+                    const int kc = std::min(kMaxOut, kq - k0);
                     if (b32)
                         launch_lincomb(lgrid, st, (const float *)src, m, R32.p + (size_t)k0 * N, kc, N, 0.0,
                                        dY2.p + (size_t)k0 * m, 1.0);
@@ -809,12 +873,14 @@ struct DavEngine {
                                        dY2.p + (size_t)k0 * m, 1.0);
                     TB_CUDA(ctx, cudaGetLastError());
                 }
-                TB_CUDA(ctx, cudaMemcpyAsync(src, b32 ? (void *)R32.p : (void *)R.p, (size_t)kk * N * es(),
+                TB_CUDA(ctx, cudaMemcpyAsync(src, b32 ? (void *)R32.p : (void *)R.p, (size_t)kq * N * es(),
                                              cudaMemcpyDeviceToDevice, st));
             }
-            m = kk;
+            m = kq;
             restarted = true;
         }
+        p_prev.swap(p_cur);
+        p_rows = m;  // corrections appended below have zero coefficients
         // restart_keep + nroots may exceed the basis: the lowest roots' corrections
         // take the free slots (keep < max_subspace leaves at least one)
         if (m + (int)todo.size() > m_max) todo.resize(m_max - m);
@@ -834,10 +900,16 @@ struct DavEngine {
             }
             TB_TRY(dots(vs(m + j), 1, vs(m + j), 1, scal.p + 2 * j));
         }
-        for (int pass = 0; pass < 2; ++pass) {
-            TB_TRY(dots(vs(0), m, Tb, nb, coef.p));
-            TB_TRY(lincomb(vs(0), m, Tb, nb, 1.0, coef.p, -1.0));
-        }
+        // block projection against the basis: S = V^T T, T -= V S; the second pass
+        // runs only when the first removed more than half of a correction's
+        // squared norm (decided on the device, no host round trip)
+        TB_TRY(dots(vs(0), m, Tb, nb, coef.p));
+        TB_TRY(lincomb(vs(0), m, Tb, nb, 1.0, coef.p, -1.0));
+        TB_TRY(dots(Tb, nb, Tb, nb, red.p));
+        k_gs_decide<<<1, 32, 0, st>>>(scal.p, red.p, nb, gs_skip.p);
+        TB_CUDA(ctx, cudaGetLastError());
+        TB_TRY(dots(vs(0), m, Tb, nb, coef.p, gs_skip.p));
+        TB_TRY(lincomb(vs(0), m, Tb, nb, 1.0, coef.p, -1.0, gs_skip.p));
         for (int j = 0; j < nb; ++j) {
             void *t = vs(m + j);
             for (int pass = 0; pass < 2 && j > 0; ++pass) {
@@ -953,12 +1025,12 @@ tbsci_status engine_results(DavEngine *e, double *energies, double *vecs, tbsci_
 size_t engine_device_bytes(int64_t N, int nroots, const tbsci_davidson_opts *o) {
     const int m_max = (o && o->max_subspace > 0) ? o->max_subspace : std::max(8 * nroots, nroots + 2);
     const int keep = (o && o->restart_keep > 0) ? o->restart_keep : std::max(nroots, m_max / 2);
-    size_t vec = (size_t)(2 * m_max + keep + 3 * nroots + 1) * N * sizeof(double);
+    size_t vec = (size_t)(2 * m_max + keep + 4 * nroots + 1) * N * sizeof(double);
     if (o && o->mixed && o->basis_f32) {
         const int m_ref = o->max_subspace_refine > 0 ? o->max_subspace_refine : std::max(nroots + 1, m_max / 2);
         const int keep_ref = std::max(nroots, m_ref / 2);
-        const size_t phase32 = (size_t)(2 * m_max + keep) * N * sizeof(float);
-        const size_t phase64 = (size_t)(2 * m_ref + keep_ref) * N * sizeof(double);
+        const size_t phase32 = (size_t)(2 * m_max + keep + nroots) * N * sizeof(float);
+        const size_t phase64 = (size_t)(2 * m_ref + keep_ref + nroots) * N * sizeof(double);
         vec = std::max(phase32, phase64) + (size_t)(3 * nroots + 1) * N * sizeof(double);
     } else if (o && o->mixed) {
         vec += (size_t)2 * nroots * N * sizeof(float);

@@ -208,6 +208,11 @@ struct Plan {
     // and the transposed c / sigma scratch of the beta-double class
     std::vector<std::unique_ptr<PartLayout>> parts;
     DevBuf<unsigned char> d_trans;
+    // same-spin beta links (singles, then doubles, per source string) with FP32
+    // values: the beta classes of the tensor-core types' product pass
+    DevBuf<int64_t> d_bss_off;
+    DevBuf<int32_t> d_bss_col;
+    DevBuf<float> d_bss_valf;
     tbsci_sigma_counts counts{};
     size_t charged = 0;  // device bytes counted against the context's budget
 };
@@ -296,6 +301,11 @@ int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, in
 template <typename T>
 tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int variant,
                           int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode);
+// The classes the tensor-core kernel leaves out (same-spin beta singles and
+// doubles, alpha doubles) as column-tiled products: beta on the transposed
+// vector, alpha on c; overwrites s (rest mode 4).
+tbsci_status rest_products_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const float *c, float *s, int nvec,
+                                  cudaStream_t st);
 // sigma_tc.cu: the diagonal, alpha singles and all alpha-beta classes on the
 // tensor cores (3xTF32 or BF16 products, FP32 accumulation), added into s.
 tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s, int nvec,

@@ -764,7 +764,19 @@ tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, con
     const int threads[3] = {128, 256, 512};
     float best = 1e30f;
     int bm = 0, bt = 0;
-    bool seen[6] = {false, false, false, false, false, false};
+    bool seen[7] = {false, false, false, false, false, false, false};
+    // mode 4 (column-tiled products) runs on the whole space; its time counts in
+    // proportion to the sample when the others are timed on one
+    if (ret == TBSCI_OK) {
+        float ms = 0.f;
+        ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, 4, 256); }, 1, &ms);
+        if (ret == TBSCI_OK) {
+            best = rows ? ms * (float)nrows / (float)la : ms;
+            bm = 4;
+            bt = 256;
+            seen[6] = true;
+        }
+    }
     for (int mode = 0; mode < 4 && ret == TBSCI_OK; ++mode) {
         const int var = rest_variant(ctx, npair, lb, mode, pairs);
         if (seen[var]) continue;
@@ -912,7 +924,7 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
         // the sample; the double-class products, transposes and combine do not
         // depend on its shape, so their full-space time is measured once and
         // added in proportion to the sample
-        if (ret == TBSCI_OK && variant(1, 0) != 0 && split_min_parts(ctx, npair, lb, ti == 0 ? 8 : 4, 4) >= 1) {
+        if (ret == TBSCI_OK && variant(1, 0) != 0 && split_min_parts(ctx, npair, lb, ti == 0 ? 8 : 4, 0) >= 1) {
             float fixed = 0.f;
             ret = dt == TBSCI_F64
                       ? timed_split<double>(ctx, ham, plan, static_cast<const double *>(c), static_cast<double *>(s),
@@ -1002,6 +1014,7 @@ tbsci_status launch_rest_v(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t
 // only), 2 (c only), 3 (neither), 4 (row pairs, c staged) or 5 (row pairs).
 int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode, bool pairs) {
     const size_t lim = ctx->smem_optin;
+    if (mode == 4) return 6;  // column-tiled products (rest_products_launch)
     if (mode == 3 && pairs) return smem_bytes<float>(npair, lb, 2, true, false) <= lim ? 4 : 5;
     if (mode == 3) mode = 1;
     if (mode == 0) {
@@ -1030,6 +1043,7 @@ tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan 
     }
     if (threads == 0) threads = A.lb >= 1024 ? 512 : 128;
     const int var = rest_variant(ctx, A.npair, A.lb, mode, plan->d_pairs.p != nullptr);
+    if (var == 6) return rest_products_launch(ctx, ham, const_cast<Plan *>(plan), c, s, nvec, st);
     if (var >= 4) {
         // row pairs: one vector per launch with vstride = l_beta, pair starts as rows
         SigArgs<float> P = A;

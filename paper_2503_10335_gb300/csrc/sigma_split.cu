@@ -55,14 +55,18 @@ __host__ __device__ size_t split_head_bytes(int npair) {
     return ((2 * npair + 2) * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15);
 }
 
-template <typename T, int kThreads>
+// GACC: one CTA per alpha row (NC = 1) that accumulates in the output row in
+// global memory (column order, coalesced), which frees shared memory for longer
+// column parts; otherwise the accumulators of the CTA's slices stay in shared memory.
+template <typename T, int kThreads, bool GACC>
 __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int npair = A.npair;
     T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2 npair + 2]: coefficient by (pair, sign); last two zero
     int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair + 2);
     T *sC = reinterpret_cast<T *>(smem_raw + split_head_bytes<T>(npair));  // [W]: one part of a c row
-    T *sAcc = sC + A.W;  // accumulators of this CTA's column slices
+    T *sAcc = GACC ? A.S + A.rowsa[blockIdx.x / A.NC] * A.lb  // the row itself, column order
+                   : sC + A.W;  // accumulators of this CTA's column slices
     const int NC = A.NC, P = A.P;
     const int64_t Ia = A.rowsa[blockIdx.x / NC];
     const int kk = (int)(blockIdx.x % NC);
@@ -79,7 +83,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
         sV2[2 * npair] = T(0);
         sV2[2 * npair + 1] = T(0);
     }
-    for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) sAcc[jl] = T(0);
+    // zero the accumulators (in global memory only the row's lb entries exist)
+    for (int64_t jl = threadIdx.x; jl < (GACC ? lb : nloc); jl += kThreads) sAcc[jl] = T(0);
     __syncthreads();
     const int na = A.na;
     const T eIa = A.ecore + A.Ea[Ia];
@@ -159,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
             }
         }
     }
+    if (GACC) return;  // the row was accumulated in place
     __syncthreads();
     T *__restrict__ S = A.S + Ia * lb;  // the row in the layout's column order
     for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) {
@@ -364,9 +370,9 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
     return TBSCI_OK;
 }
 
-template <typename T, int TH>
+template <typename T, int TH, bool GACC>
 tbsci_status launch_parts_th(tbsci_ctx *ctx, const SplitArgs<T> &A, size_t smem, cudaStream_t st) {
-    auto k = k_sigma_parts<T, TH>;
+    auto k = k_sigma_parts<T, TH, GACC>;
     TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<(unsigned)(A.la * A.NC), TH, smem, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
@@ -457,7 +463,7 @@ const float *dval_of<float>(const SpinPlan &sp) { return sp.d_dvalf.p; }
 int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc) {
     const size_t head = elem == 8 ? split_head_bytes<double>(npair) : split_head_bytes<float>(npair);
     const int64_t nsl = (lb + 31) / 32;
-    const size_t acc = (size_t)((nsl + nc - 1) / nc) * 32 * elem;
+    const size_t acc = nc == 0 ? 0 : (size_t)((nsl + nc - 1) / nc) * 32 * elem;  // nc 0: accumulators in global memory
     if (ctx->smem_optin <= head + acc) return 0;
     const int64_t wmax = (int64_t)((ctx->smem_optin - head - acc) / elem);
     if (wmax <= 0) return 0;
@@ -472,11 +478,14 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
                           int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode) {
     const int64_t la = P->A.l, lb = P->B.l;
     if (la == 0 || lb == 0) return TBSCI_OK;
-    // CTAs per alpha row: 1, 2 or 4 (the first that leaves room for a c part)
-    int nc = 1 << std::min(2, std::max(0, variant)), nparts = 0;
+    // variant 0: one CTA per alpha row accumulating in global memory; 1, 2: two or
+    // four CTAs per row with their accumulators in shared memory (four when two
+    // leave no room for a c part)
+    const bool gacc = variant <= 0;
+    int nc = gacc ? 1 : (variant == 1 ? 2 : 4), nparts = 0;
     for (; nc <= 4; nc *= 2) {
-        nparts = split_min_parts(ctx, P->npair, lb, sizeof(T), nc);
-        if (nparts >= 1) break;
+        nparts = split_min_parts(ctx, P->npair, lb, sizeof(T), gacc ? 0 : nc);
+        if (nparts >= 1 || gacc) break;
     }
     TB_CHECK(ctx, nparts >= 1 && nc <= 4, TBSCI_EINVAL, "split sigma: no room for a column part in shared memory");
     TB_CHECK(ctx, (la + 31) / 32 <= 65535, TBSCI_EINVAL, "split sigma: too many alpha strings");
@@ -505,7 +514,7 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
     }
     const int64_t nsl = (lb + 31) / 32;
     const size_t smem = split_head_bytes<T>(P->npair) + (size_t)pl->W * sizeof(T) +
-                        (size_t)((nsl + nc - 1) / nc) * 32 * sizeof(T);
+                        (gacc ? 0 : (size_t)((nsl + nc - 1) / nc) * 32 * sizeof(T));
     T *ct = reinterpret_cast<T *>(P->d_trans.p), *sz = ct + (size_t)la * lb;
     const dim3 tb(32, 8), tgrid((unsigned)((lb + 31) / 32), (unsigned)((la + 31) / 32));
     for (int v = 0; v < nvec; ++v) {
@@ -521,14 +530,100 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
             // K1 rows in the layout's column order into ct (free once c^T has been used)
             A.C = cv;
             A.S = ct;
-            if (threads >= 1024) TB_TRY((launch_parts_th<T, 1024>(ctx, A, smem, st)));
-            else TB_TRY((launch_parts_th<T, 512>(ctx, A, smem, st)));
+            if (gacc) {
+                if (threads >= 1024) TB_TRY((launch_parts_th<T, 1024, true>(ctx, A, smem, st)));
+                else TB_TRY((launch_parts_th<T, 512, true>(ctx, A, smem, st)));
+            } else {
+                if (threads >= 1024) TB_TRY((launch_parts_th<T, 1024, false>(ctx, A, smem, st)));
+                else TB_TRY((launch_parts_th<T, 512, false>(ctx, A, smem, st)));
+            }
         }
         if (mode == 1) continue;
         k_combine<T><<<tgrid, tb, 0, st>>>(sv, ct, pl->iperm.p, sz, la, lb);
         TB_CUDA(ctx, cudaGetLastError());
         // [2,0]: sigma += H_alpha,doubles c
         TB_TRY(launch_dbl<T>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, dval_of<T>(P->A), true, st));
+    }
+    return TBSCI_OK;
+}
+
+tbsci_status rest_products_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const float *c, float *s, int nvec,
+                                  cudaStream_t st) {
+    const int64_t la = P->A.l, lb = P->B.l;
+    if (la == 0 || lb == 0) return TBSCI_OK;
+    TB_CHECK(ctx, (la + 31) / 32 <= 65535 && (lb + 31) / 32 <= 65535, TBSCI_EINVAL,
+             "product pass: too many strings");
+    if (!P->d_bss_off.p) {  // merged same-spin beta links, built once
+        const int64_t ns = P->B.h_soff[lb], nd = P->B.h_doff[lb];
+        std::vector<int2> sci(ns);
+        std::vector<float> sv(ns), dv(nd);
+        std::vector<int32_t> dc(nd);
+        if (ns) {
+            TB_CUDA(ctx, cudaMemcpy(sci.data(), P->B.d_sci.p, ns * sizeof(int2), cudaMemcpyDeviceToHost));
+            TB_CUDA(ctx, cudaMemcpy(sv.data(), P->B.d_svalf.p, ns * sizeof(float), cudaMemcpyDeviceToHost));
+        }
+        if (nd) {
+            TB_CUDA(ctx, cudaMemcpy(dc.data(), P->B.d_dcol.p, nd * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            TB_CUDA(ctx, cudaMemcpy(dv.data(), P->B.d_dvalf.p, nd * sizeof(float), cudaMemcpyDeviceToHost));
+        }
+        std::vector<int64_t> off(lb + 1, 0);
+        std::vector<int32_t> col(ns + nd);
+        std::vector<float> val(ns + nd);
+        int64_t k = 0;
+        for (int64_t ib = 0; ib < lb; ++ib) {
+            off[ib] = k;
+            for (int64_t t = P->B.h_soff[ib]; t < P->B.h_soff[ib + 1]; ++t, ++k) {
+                col[k] = sci[t].x;
+                val[k] = sv[t];
+            }
+            for (int64_t t = P->B.h_doff[ib]; t < P->B.h_doff[ib + 1]; ++t, ++k) {
+                col[k] = dc[t];
+                val[k] = dv[t];
+            }
+        }
+        off[lb] = k;
+        const size_t bytes = (lb + 1) * 8 + (size_t)k * 8;
+        TB_TRY(charge(ctx, bytes, "same-spin beta link table"));
+        cudaError_t e = P->d_bss_off.alloc(lb + 1);
+        if (e == cudaSuccess) e = P->d_bss_col.alloc(std::max<int64_t>(k, 1));
+        if (e == cudaSuccess) e = P->d_bss_valf.alloc(std::max<int64_t>(k, 1));
+        if (e == cudaSuccess) e = cudaMemcpy(P->d_bss_off.p, off.data(), (lb + 1) * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && k) e = cudaMemcpy(P->d_bss_col.p, col.data(), k * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && k) e = cudaMemcpy(P->d_bss_valf.p, val.data(), k * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            P->d_bss_off.release();
+            uncharge(ctx, bytes);
+            return fail(ctx, e == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA,
+                        std::string("same-spin beta link table: ") + cudaGetErrorString(e));
+        }
+        P->charged += bytes;
+    }
+    const size_t need = 2 * (size_t)la * lb * sizeof(float);
+    if (P->d_trans.n < need) {
+        uncharge(ctx, P->d_trans.bytes());
+        P->charged -= std::min(P->charged, P->d_trans.bytes());
+        P->d_trans.release();
+        TB_TRY(charge(ctx, need, "product pass scratch"));
+        const cudaError_t e = P->d_trans.alloc(need);
+        if (e != cudaSuccess) {
+            uncharge(ctx, need);
+            return fail(ctx, e == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA,
+                        std::string("product pass scratch: ") + cudaGetErrorString(e));
+        }
+        P->charged += need;
+    }
+    float *ct = reinterpret_cast<float *>(P->d_trans.p), *sz = ct + (size_t)la * lb;
+    const dim3 tb(32, 8), tg_ab((unsigned)((lb + 31) / 32), (unsigned)((la + 31) / 32)),
+        tg_ba((unsigned)((la + 31) / 32), (unsigned)((lb + 31) / 32));
+    for (int v = 0; v < nvec; ++v) {
+        const float *cv = c + (size_t)v * la * lb;
+        float *sv = s + (size_t)v * la * lb;
+        k_transpose<float><<<tg_ab, tb, 0, st>>>(cv, ct, la, lb);
+        TB_CUDA(ctx, cudaGetLastError());
+        TB_TRY(launch_dbl<float>(ctx, ct, sz, lb, la, P->d_bss_off.p, P->d_bss_col.p, P->d_bss_valf.p, false, st));
+        k_transpose<float><<<tg_ba, tb, 0, st>>>(sz, sv, lb, la);  // sigma = (beta classes)^T
+        TB_CUDA(ctx, cudaGetLastError());
+        TB_TRY(launch_dbl<float>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, P->A.d_dvalf.p, true, st));
     }
     return TBSCI_OK;
 }
