@@ -84,6 +84,7 @@ tbsci_status tbsci_create_ex(const tbsci_options *opts, tbsci_ctx **out) {
     if (bad(cudaGetDeviceProperties(&prop, device))) return TBSCI_ECUDA;
     ctx->num_sms = prop.multiProcessorCount;
     ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    ctx->smem_per_sm = prop.sharedMemPerMultiprocessor;
     if (bad(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking))) return TBSCI_ECUDA;
     // binomials by Pascal's rule (no intermediate overflow up to C(64, 32))
     std::vector<int64_t> B(65 * 65, 0);
@@ -376,7 +377,7 @@ tbsci_status tbsci_tune_cache_load(tbsci_ctx *ctx, const char *path) {
         bool ok = n == 11 && k0 >= 1 && k0 <= 64 && k1 >= 0 && k2 >= 0 && threads_ok(e.rest_threads) &&
                   e.rest_mode >= 0 && e.rest_mode <= 4;
         for (int i = 0; i < 2 && ok; ++i)
-            ok = threads_ok(e.threads[i]) && e.nv[i] >= 0 && e.nv[i] <= 4 && e.stage[i] >= 0 && e.stage[i] <= 5 &&
+            ok = threads_ok(e.threads[i]) && e.nv[i] >= 0 && e.nv[i] <= 4 && e.stage[i] >= 0 && e.stage[i] <= 6 &&
                  (e.stage[i] < 3 ? e.threads[i] != 1024 : (e.threads[i] == 0 || e.threads[i] >= 512));
         if (!ok) {
             bad = "malformed line " + std::to_string(lineno);

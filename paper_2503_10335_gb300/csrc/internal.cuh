@@ -86,6 +86,7 @@ struct tbsci_ctx {
     int device = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
+    size_t smem_per_sm = 0;  // shared memory of one SM (all resident CTAs)
     // tbsci_options: device-memory budget of the context's objects (0 = none),
     // bytes they hold now, Davidson mode when no options are given, tune-cache file
     size_t hbm_budget = 0;
@@ -296,8 +297,9 @@ tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan 
 // same-spin double classes as column-tiled products); see the file head
 // smallest number of column parts of a c row that fits in shared memory beside
 // the accumulators of 1/nc of a sigma row (0: none fits)
-int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc);
-// variant: 0, 1, 2 -> 1, 2, 4 CTAs per alpha row, each with the minimal parts
+int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc, size_t budget = 0);
+// variant: 0 one CTA per alpha row (global accumulators), 1, 2 two or four CTAs
+// per row (shared-memory accumulators), 3 as 0 with parts for two CTAs per SM
 template <typename T>
 tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T *c, T *s, int nvec, int variant,
                           int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode);

@@ -933,7 +933,7 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
                                            st, e0, e1, &fixed);
             const float share = fixed * (float)nrows / (float)la;
             const int split_threads[2] = {512, 1024};
-            for (int stage = 3; stage <= 5 && ret == TBSCI_OK; ++stage)
+            for (int stage = 3; stage <= 6 && ret == TBSCI_OK; ++stage)
                 for (int t = 0; t < 2 && ret == TBSCI_OK; ++t) {
                     float ms = 0.f;
                     ret = trial(1, split_threads[t], stage, dsample.p, nrows, 1, &ms);

@@ -58,8 +58,8 @@ __host__ __device__ size_t split_head_bytes(int npair) {
 // GACC: one CTA per alpha row (NC = 1) that accumulates in the output row in
 // global memory (column order, coalesced), which frees shared memory for longer
 // column parts; otherwise the accumulators of the CTA's slices stay in shared memory.
-template <typename T, int kThreads, bool GACC>
-__global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
+template <typename T, int kThreads, bool GACC, int MINB = 1>
+__global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int npair = A.npair;
     T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2 npair + 2]: coefficient by (pair, sign); last two zero
@@ -119,7 +119,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_parts(SplitArgs<T> A) {
                     sV2[2 * x] = v;
                     sV2[2 * x + 1] = -v;
                 }
-            for (int64_t j = threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(Crow + base + j);
+            // stage the part: 16-byte loads when the part starts on a 16-byte boundary
+            // (four loads in flight per thread), else element by element
+            const T *src = Crow + base;
+            if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+                constexpr int E = 16 / sizeof(T);
+                const int64_t nv = len / E;
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+                uint4 *d4 = reinterpret_cast<uint4 *>(sC);
+                int64_t q = threadIdx.x;
+                for (; q + 3 * kThreads < nv; q += 4 * kThreads) {
+                    const uint4 a = __ldg(s4 + q), b = __ldg(s4 + q + kThreads), c2 = __ldg(s4 + q + 2 * kThreads),
+                                d = __ldg(s4 + q + 3 * kThreads);
+                    d4[q] = a;
+                    d4[q + kThreads] = b;
+                    d4[q + 2 * kThreads] = c2;
+                    d4[q + 3 * kThreads] = d;
+                }
+                for (; q < nv; q += kThreads) d4[q] = __ldg(s4 + q);
+                for (int64_t j = nv * E + threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(src + j);
+            } else {
+                for (int64_t j = threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(src + j);
+            }
             __syncthreads();
             for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) {
                 const int64_t sl = (jl >> 5) * NC + kk;
@@ -370,9 +391,9 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
     return TBSCI_OK;
 }
 
-template <typename T, int TH, bool GACC>
+template <typename T, int TH, bool GACC, int MINB = 1>
 tbsci_status launch_parts_th(tbsci_ctx *ctx, const SplitArgs<T> &A, size_t smem, cudaStream_t st) {
-    auto k = k_sigma_parts<T, TH, GACC>;
+    auto k = k_sigma_parts<T, TH, GACC, MINB>;
     TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k<<<(unsigned)(A.la * A.NC), TH, smem, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
@@ -460,12 +481,13 @@ const float *dval_of<float>(const SpinPlan &sp) { return sp.d_dvalf.p; }
 
 }  // namespace
 
-int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc) {
+int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc, size_t budget) {
     const size_t head = elem == 8 ? split_head_bytes<double>(npair) : split_head_bytes<float>(npair);
     const int64_t nsl = (lb + 31) / 32;
     const size_t acc = nc == 0 ? 0 : (size_t)((nsl + nc - 1) / nc) * 32 * elem;  // nc 0: accumulators in global memory
-    if (ctx->smem_optin <= head + acc) return 0;
-    const int64_t wmax = (int64_t)((ctx->smem_optin - head - acc) / elem);
+    const size_t lim = budget ? std::min(budget, ctx->smem_optin) : ctx->smem_optin;
+    if (lim <= head + acc) return 0;
+    const int64_t wmax = (int64_t)((lim - head - acc) / elem);
     if (wmax <= 0) return 0;
     return (int)std::max<int64_t>(1, (lb + wmax - 1) / wmax);
 }
@@ -478,13 +500,16 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
                           int threads, const int32_t *rows, int64_t nrows, cudaStream_t st, int mode) {
     const int64_t la = P->A.l, lb = P->B.l;
     if (la == 0 || lb == 0) return TBSCI_OK;
-    // variant 0: one CTA per alpha row accumulating in global memory; 1, 2: two or
-    // four CTAs per row with their accumulators in shared memory (four when two
-    // leave no room for a c part)
-    const bool gacc = variant <= 0;
+    // variant 0: one CTA per alpha row accumulating in global memory, parts as
+    // long as shared memory allows; 3: the same with parts short enough for two
+    // CTAs per SM (one stages while the other computes); 1, 2: two or four CTAs
+    // per row with their accumulators in shared memory (four when two leave no
+    // room for a c part)
+    const bool gacc = variant <= 0 || variant == 3;
+    const size_t budget = variant == 3 ? ctx->smem_per_sm / 2 - 1024 : 0;
     int nc = gacc ? 1 : (variant == 1 ? 2 : 4), nparts = 0;
     for (; nc <= 4; nc *= 2) {
-        nparts = split_min_parts(ctx, P->npair, lb, sizeof(T), gacc ? 0 : nc);
+        nparts = split_min_parts(ctx, P->npair, lb, sizeof(T), gacc ? 0 : nc, budget);
         if (nparts >= 1 || gacc) break;
     }
     TB_CHECK(ctx, nparts >= 1 && nc <= 4, TBSCI_EINVAL, "split sigma: no room for a column part in shared memory");
@@ -530,7 +555,9 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
             // K1 rows in the layout's column order into ct (free once c^T has been used)
             A.C = cv;
             A.S = ct;
-            if (gacc) {
+            if (variant == 3) {  // two CTAs per SM: 512 threads at most 64 registers each
+                TB_TRY((launch_parts_th<T, 512, true, 2>(ctx, A, smem, st)));
+            } else if (gacc) {
                 if (threads >= 1024) TB_TRY((launch_parts_th<T, 1024, true>(ctx, A, smem, st)));
                 else TB_TRY((launch_parts_th<T, 512, true>(ctx, A, smem, st)));
             } else {
