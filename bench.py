@@ -14,8 +14,13 @@ value  = nvec * ndet / (device time per step) / 1e9, timed with CUDA events on
 e2e    = the same metric through tbsci_sigma_host with pinned host buffers:
          host->device copy of c and device->host copy of sigma inside the timed
          region.
-roofline = the fused sigma kernel against the FP64 ALU (2 flops per non-zero
-         H_IJ per vector) or the FP32 ALU.
+roofline = the kernel with the largest share of the step (the fused sigma
+         kernel, or the split path's row kernel) against the FP64 ALU (2 flops
+         per non-zero H_IJ of the classes it computes, per vector), the FP32
+         ALU, the tensor cores or HBM; its launch time comes from the library's
+         kernel trace (CUDA events around each launch on its stream).
+         roofline.step gives the whole step the same way, and `kernels` every
+         kernel of the step.
 cpu_baseline = the CPU oracle timed on a bounded row sample of the same
          workload on this host's cores (rank 0, N = 1 only).
 sel16_sigma = the same measurement on norb=16, 3,000 x 3,000 selected strings
@@ -57,36 +62,128 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (recipe nominal)
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FMA = 2 flops
 
 
-# DRAM bytes (read + write) per launch of the sigma kernel, by workload and launch
-# shape (threads, vectors per CTA, shared-memory mode), from one ncu capture of the
-# kernel source with this sha1 (the shape-by-shape tables are in the profiles of
-# k_sigma FP64); a workload, shape or source not captured reports null
+# DRAM bytes (read + write) per launch, by workload, dtype and kernel, at a launch
+# shape, from one ncu capture of the kernel source file with this sha1 (the
+# captures are summarised in the kernels' profiles); a workload, shape or source
+# not captured reports null. Shapes: k_sigma (threads, vectors per CTA,
+# shared-memory mode); k_sigma_parts (threads, stage).
 NCU_TRAFFIC = {
-    ("sel16", "f64"): {"sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2",
-                       "shapes": {(512, 1, 0): 1.998e9, (512, 2, 0): 7.439e9, (512, 3, 0): 12.643e9,
-                                  (256, 1, 0): 1.356e9, (128, 1, 0): 0.803e9,
-                                  (512, 1, 1): 1.233e9, (256, 1, 1): 0.811e9, (128, 1, 1): 1.558e9,
-                                  (512, 1, 2): 2.049e9, (256, 1, 2): 1.496e9, (128, 1, 2): 3.683e9}},
+    ("sel16", "f64", "k_sigma"): {
+        "source": "sigma.cu", "sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2",
+        "shapes": {(512, 1, 0): 1.998e9, (512, 2, 0): 7.439e9, (512, 3, 0): 12.643e9,
+                   (256, 1, 0): 1.356e9, (128, 1, 0): 0.803e9,
+                   (512, 1, 1): 1.233e9, (256, 1, 1): 0.811e9, (128, 1, 1): 1.558e9,
+                   (512, 1, 2): 2.049e9, (256, 1, 2): 1.496e9, (128, 1, 2): 3.683e9}},
 }
 
 
-def _kernel_hash():
+def _source_hash(name):
     import hashlib
-    with open(os.path.join(ROOT, "paper_2503_10335_gb300", "csrc", "sigma.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2503_10335_gb300", "csrc", name), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
-def _traffic(workload, dtype, threads, nv, stage, nvec):
-    """Average DRAM bytes per launch of one step: nvec vectors in launch groups of
-    nv (the last one smaller) at the tuned threads and shared-memory mode."""
-    rec = NCU_TRAFFIC.get((workload, dtype))
-    if not rec or rec["sha1"] != _kernel_hash() or nv < 1:
+def _traffic(workload, dtype, kernel, counts, nvec=1):
+    """Average DRAM bytes per launch of `kernel` in one step at the tuned shape,
+    or None. k_sigma runs nvec vectors in launch groups of the tuned vectors per
+    CTA (the last group smaller); the other kernels take one vector a launch."""
+    rec = NCU_TRAFFIC.get((workload, dtype, kernel))
+    if not rec or rec["sha1"] != _source_hash(rec["source"]):
+        return None
+    t = 0 if dtype == "f64" else 1
+    threads, nv, stage = counts["tuned_threads"][t], counts["tuned_nv"][t], counts["tuned_stage"][t]
+    if kernel != "k_sigma":
+        return rec["shapes"].get((threads, stage))
+    if nv < 1:
         return None
     groups = [min(nv, nvec - v) for v in range(0, nvec, nv)]
     try:
         return sum(rec["shapes"][(threads, g, stage)] for g in groups) / len(groups)
     except KeyError:
         return None
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _kernel_work(name, c, nvec, dtype):
+    """Algorithmic work of one step for the launches of kernel `name`:
+    (amount, kind, rule); kind is "fp" (flops on the ALU), "tensor" (flops on
+    the tensor cores) or "bytes" (HBM)."""
+    la, lb, nd = c["la"], c["lb"], c["ndet"]
+    elem = 8 if dtype == "f64" else 4
+    tc = dtype in ("tf32tc", "bf16tc")
+    if name in ("k_sigma", "k_sigma_batch"):
+        return 2.0 * c["nnz"] * nvec, "fp", "2 flops per non-zero H_IJ per vector"
+    if name == "k_sigma_parts":
+        return (2.0 * (nd + c["n1a"] * lb + c["n1b"] * la + c["n1a"] * c["n1b"]) * nvec, "fp",
+                "2 flops per non-zero of the diagonal, single and alpha-beta classes per vector")
+    if name == "k_dbl_spmm_alpha":
+        return 2.0 * c["n2a"] * lb * nvec, "fp", "2 flops per non-zero of the alpha doubles per vector"
+    if name == "k_dbl_spmm_beta":
+        n = c["n2b"] + (c["n1b"] if tc else 0)
+        return 2.0 * n * la * nvec, "fp", "2 flops per non-zero of the beta %s per vector" % (
+            "singles and doubles" if tc else "doubles")
+    if name in ("k_sigma_rest", "k_sigma_rest_pair"):
+        return (2.0 * ((c["n1b"] + c["n2b"]) * la + c["n2a"] * lb) * nvec, "fp",
+                "2 flops per non-zero of the beta singles and doubles and the alpha doubles per vector")
+    if name == "k_sigma_ab_tc":
+        noff = c["norb"] * (c["norb"] - 1) // 2
+        return (2.0 * noff * c["n1a"] * lb * nvec, "tensor",
+                "2 flops per (alpha single, off-diagonal pair kl, beta column) of the dense contraction per vector")
+    if name == "k_transpose":
+        return None, "bytes", "read + write of one vector"
+    if name == "k_combine":
+        return None, "bytes", "two vectors read, one written"
+    return None, "fp", "not modelled"
+
+
+def _kernel_table(trace, steps, c, nvec, dtype):
+    """Per-kernel launches, device time and roofline fraction of the timed steps
+    (from the library's kernel trace)."""
+    peaks = _measured_peaks()
+    elem = 8 if dtype == "f64" else 4
+    by = {}
+    for name, ms in trace:
+        by.setdefault(name, []).append(ms)
+    total = sum(sum(v) for v in by.values()) or 1.0
+    out = []
+    for name, v in by.items():
+        launches = len(v) / steps
+        mean = statistics.mean(v)
+        work_step, kind, rule = _kernel_work(name, c, nvec, dtype)
+        if kind == "bytes":
+            per = (2 if name == "k_transpose" else 3) * c["ndet"] * elem
+            peak, unit = peaks.get("hbm_gbs", 6800.0), "GB/s"
+            src = "HBM copy of measured" if "hbm_gbs" in peaks else "HBM of fallback (6.8 TB/s)"
+            achieved = per / (mean * 1e-3) / 1e9
+            bound = "hbm"
+        elif kind == "tensor":
+            per = work_step / launches
+            bf = peaks.get("bf16_tflops", 1900.0)
+            peak = bf * (0.5 if dtype == "tf32tc" else 1.0)
+            unit, bound = "TFLOP/s", "tensor"
+            src = ("BF16 burst of measured" if "bf16_tflops" in peaks else "BF16 of fallback") + (
+                " x 0.5 (nominal TF32 : BF16)" if dtype == "tf32tc" else "")
+            achieved = per / (mean * 1e-3) / 1e12
+        else:
+            per = work_step / launches if work_step is not None else None
+            peak = FP64_NOMINAL_TFLOPS if dtype == "f64" else FP32_NOMINAL_TFLOPS
+            unit, bound = "TFLOP/s", "alu"
+            src = "%s ALU derived from unit counts and clocks (152 SMs x %s per clock x 2070 MHz)" % (
+                ("FP64", "2 DFMA") if dtype == "f64" else ("FP32", "128 FFMA"))
+            achieved = per / (mean * 1e-3) / 1e12 if per is not None else None
+        out.append({"kernel": name, "launches_per_step": launches, "ms_per_launch": mean,
+                    "ms_per_step": sum(v) / steps, "share": sum(v) / total, "bound": bound,
+                    "work_per_launch": per, "rule": rule, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak if achieved is not None else None, "peak_source": src})
+    out.sort(key=lambda r: -r["ms_per_step"])
+    return out
 
 
 def _dist():
@@ -498,34 +595,42 @@ def _sigma_leg(tb, ctx, wl, dtype, nvec, steps, warmup, dev, stream, autotune=Tr
         time.sleep(0.3)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     torch.cuda.synchronize()
+    # the library's kernel trace brackets each of its launches with events on
+    # the launching stream: per-kernel device times of the timed steps
+    tb.tbsci_trace_read(ctx.handle)
+    tb.tbsci_trace_enable(ctx.handle, True)
     ev[0].record(stream)
     for k in range(steps):
         sp.sigma(C, S, stream=stream, dtype=sdt)
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
+    tb.tbsci_trace_enable(ctx.handle, False)
+    trace, dropped = tb.tbsci_trace_read(ctx.handle)
     clk = sampler.stop() if sampler else None
     per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     counts = sp.counts()  # after tuning: carries the chosen launch shape
-    if sdt in (tb.TBSCI_F64, tb.TBSCI_F32):
-        nv_used = counts["tuned_nv"][0 if sdt == tb.TBSCI_F64 else 1] or min(nvec, 4)
-        launches_per_step = (nvec + nv_used - 1) // nv_used
-    else:  # SIMT pass + tensor-core kernel per vector
-        launches_per_step = 2 * nvec
-    flops_step = 2.0 * counts["nnz"] * nvec
-    kern_ms = statistics.mean(per_step) / launches_per_step
-    achieved = flops_step / launches_per_step / (kern_ms * 1e-3) / 1e12
-    peak = FP64_NOMINAL_TFLOPS if dtype == "f64" else FP32_NOMINAL_TFLOPS
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": (_traffic(wl.name, dtype, counts["tuned_threads"][0], counts["tuned_nv"][0],
-                                     counts["tuned_stage"][0], nvec) if dtype == "f64" else None),
-                "kernel": "k_sigma (fused, all classes)",
-                "peak_source": "%s ALU derived from unit counts and clocks (152 SMs x %s per clock x 2070 MHz)" %
-                               (("FP64", "2 DFMA") if dtype == "f64" else ("FP32", "128 FFMA")),
-                "algorithmic_flops_per_launch": flops_step / launches_per_step,
-                "algorithmic_flops_rule": "2 flops per non-zero H_IJ per vector"}
+    n1a, n2a = tb.tbsci_tables_counts(sp.ta)
+    n1b, n2b = tb.tbsci_tables_counts(sp.tb)
+    kernels = _kernel_table(trace, steps, dict(counts, n1a=n1a, n2a=n2a, n1b=n1b, n2b=n2b, la=sp.la, lb=sp.lb,
+                                               norb=wl.norb), nvec, dtype)
+    dom = max(kernels, key=lambda r: r["ms_per_step"])
+    step_flops = 2.0 * counts["nnz"] * nvec
+    traffic = _traffic(wl.name, dtype, dom["kernel"], counts, nvec)
+    roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"], "unit": dom["unit"],
+                "frac": dom["frac"], "traffic": traffic, "kernel": dom["kernel"],
+                "launches_per_step": dom["launches_per_step"], "ms_per_launch": dom["ms_per_launch"],
+                "share_of_step": dom["share"], "peak_source": dom["peak_source"],
+                "algorithmic_per_launch": dom["work_per_launch"], "algorithmic_rule": dom["rule"],
+                "timing": "library kernel trace: CUDA events around each launch on its stream, timed steps",
+                "step": {"achieved": step_flops / (total_ms / steps * 1e-3) / 1e12, "unit": "TFLOP/s",
+                         "peak": FP64_NOMINAL_TFLOPS if dtype == "f64" else FP32_NOMINAL_TFLOPS,
+                         "rule": "2 flops per non-zero H_IJ per vector over the whole step"}}
+    roofline["step"]["frac"] = roofline["step"]["achieved"] / roofline["step"]["peak"]
+    launches_per_step = len(trace) / steps if steps else 0
     rec = {"value": nvec * sp.ndet / (total_ms / steps * 1e-3) / 1e9, "ms_per_step": total_ms / steps,
            "step_ms_min": min(per_step), "step_ms_max": max(per_step), "roofline": roofline,
+           "kernels": kernels, "trace_dropped": dropped, "gpu_launches": len(trace),
            "launches_per_step": launches_per_step, "counts": counts, "setup_seconds": t_setup,
            "autotune_ms": tuned_ms, "config": _config(wl, nvec, dtype, la=sp.la, lb=sp.lb), "clocks": clk}
     return rec, sp, C, S, sdt
@@ -577,7 +682,7 @@ def _davidson_leg(tb, ctx, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=12)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--workload", default="sel24", choices=sorted(WORKLOADS))
@@ -664,7 +769,7 @@ def main():
         # the norb=16, 3,000 x 3,000 selected space (9.0M determinants, 3 vectors), FP64
         r16, sp16, C16, S16, _ = _sigma_leg(tb, ctx, WORKLOADS["sel16"], "f64", 3, max(5, args.steps // 2),
                                            args.warmup, dev, stream, autotune=not args.no_autotune)
-        extra = {k: r16[k] for k in ("value", "ms_per_step", "roofline", "config", "launches_per_step")}
+        extra = {k: r16[k] for k in ("value", "ms_per_step", "roofline", "kernels", "config", "launches_per_step")}
         extra["unit"] = UNIT
         sp16.close()
         del C16, S16
@@ -686,7 +791,7 @@ def main():
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": dict(rec["config"], parallelism="replicas" if ws > 1 else "single"),
             "roofline": rec["roofline"], "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": rec["launches_per_step"] * args.steps,
+            "gpu_launches": rec["gpu_launches"], "kernels": rec["kernels"],
             "clocks": rec["clocks"], "sel16_sigma": extra, "davidson": dav, "serving": serving,
             "counts": rec["counts"], "setup_seconds": rec["setup_seconds"], "autotune_ms": rec["autotune_ms"],
             "step_ms_min": rec["step_ms_min"], "step_ms_max": rec["step_ms_max"],

@@ -120,6 +120,26 @@ void tbsci_destroy(tbsci_ctx *ctx);
 const char *tbsci_last_error(const tbsci_ctx *ctx);
 const char *tbsci_status_string(tbsci_status st);
 
+/* Kernel trace: the device time of each launch of the sigma path (the fused
+ * row kernel, the split path's row kernel, double-class products, transposes
+ * and combine, the tensor-core kernel and its SIMT pass, the pruned kernel).
+ * While tracing is on, every such launch made through this context is
+ * bracketed by two CUDA events recorded on its own stream (launches made while
+ * that stream is being captured into a graph are not traced). The trace keeps
+ * the last 65,536 launches. tbsci_trace_enable: on != 0 starts, 0 stops
+ * (entries already recorded stay until read). */
+tbsci_status tbsci_trace_enable(tbsci_ctx *ctx, int on);
+typedef struct tbsci_trace_entry {
+    const char *kernel; /* static name of the kernel, valid for the library's lifetime */
+    double ms;          /* device time between the events around the launch */
+} tbsci_trace_entry;
+/* Moves up to `cap` of the oldest entries into the HOST array out[cap] (waiting
+ * for their end events) and sets *n to their number; *dropped (may be NULL)
+ * receives the entries lost to the cap since the last read. Errors: EINVAL
+ * (null n, negative cap, null out with cap > 0), ECUDA (an event failed; the
+ * entries are still removed). */
+tbsci_status tbsci_trace_read(tbsci_ctx *ctx, tbsci_trace_entry *out, int64_t cap, int64_t *n, int64_t *dropped);
+
 /* --------------------------------------------------------------- strings */
 
 /* Builds a string set (Sec. II.A, Eq. 3: the sets {S^alpha}, {S^beta}).

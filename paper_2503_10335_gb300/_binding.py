@@ -32,7 +32,7 @@ EXPORTS = [
     "tbsci_tune_cache_size", "tbsci_create_ex", "tbsci_hbm_used",
     "tbsci_pruned_create", "tbsci_pruned_count", "tbsci_pruned_destroy", "tbsci_sigma_pruned",
     "tbsci_diagonal_pruned", "tbsci_davidson_pruned", "tbsci_string_weights", "tbsci_select_by_weight",
-    "tbsci_coefficient_histogram", "tbsci_pruned_create_symmetry",
+    "tbsci_coefficient_histogram", "tbsci_pruned_create_symmetry", "tbsci_trace_enable", "tbsci_trace_read",
 ]
 
 
@@ -51,6 +51,10 @@ SINGLE_DTYPE = np.dtype([("target", "<i4"), ("sign", "i1"), ("p", "u1"), ("q", "
 DOUBLE_DTYPE = np.dtype([("target", "<i4"), ("sign", "i1"), ("p", "u1"), ("r", "u1"), ("q", "u1"),
                          ("s", "u1"), ("pad", "u1", (3,))])
 assert SINGLE_DTYPE.itemsize == 8 and DOUBLE_DTYPE.itemsize == 12
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_char_p), ("ms", ctypes.c_double)]
 
 
 class SigmaCounts(ctypes.Structure):
@@ -143,6 +147,8 @@ def load(path: str | None = None):
         "tbsci_create": ([I, PP], I),
         "tbsci_create_ex": ([ctypes.POINTER(Options), PP], I),
         "tbsci_hbm_used": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
+        "tbsci_trace_enable": ([P, I], I),
+        "tbsci_trace_read": ([P, ctypes.POINTER(TraceEntry), I64, ctypes.POINTER(I64), ctypes.POINTER(I64)], I),
         "tbsci_string_weights": ([P, P, P, P, P, P, P], I),
         "tbsci_select_by_weight": ([P, P, P, P, D, P, ctypes.POINTER(I64), P, ctypes.POINTER(I64), P], I),
         "tbsci_coefficient_histogram": ([P, P, I64, P, I, P, P], I),
@@ -244,6 +250,23 @@ def tbsci_hbm_used(ctx) -> int:
 
 def tbsci_destroy(ctx):
     load().tbsci_destroy(ctx)
+
+
+def tbsci_trace_enable(ctx, on: bool) -> None:
+    _check(ctx, load().tbsci_trace_enable(ctx, 1 if on else 0))
+
+
+def tbsci_trace_read(ctx, chunk: int = 4096):
+    """Drains the kernel trace: ([(kernel, ms), ...] oldest first, entries dropped)."""
+    out, dropped = [], 0
+    buf = (TraceEntry * chunk)()
+    while True:
+        n, d = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(ctx, load().tbsci_trace_read(ctx, buf, chunk, ctypes.byref(n), ctypes.byref(d)))
+        dropped += d.value
+        out.extend((buf[i].kernel.decode(), buf[i].ms) for i in range(n.value))
+        if n.value < chunk:
+            return out, dropped
 
 
 def tbsci_last_error(ctx) -> str:

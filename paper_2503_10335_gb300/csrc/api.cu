@@ -31,6 +31,40 @@ void uncharge(tbsci_ctx *ctx, size_t bytes) {
     if (ctx && bytes) ctx->hbm_used.fetch_sub(std::min(bytes, ctx->hbm_used.load()));
 }
 
+constexpr size_t kTraceCap = 1 << 16;  // launches held before the oldest unread ones are dropped
+
+TraceScope::TraceScope(tbsci_ctx *ctx, const char *kernel, cudaStream_t st) : ctx_(ctx), kernel_(kernel), st_(st) {
+    if (!ctx || !ctx->trace_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+    if (cudaEventCreate(&start_) != cudaSuccess) {
+        start_ = nullptr;
+        return;
+    }
+    if (cudaEventRecord(start_, st) != cudaSuccess) {
+        cudaEventDestroy(start_);
+        start_ = nullptr;
+    }
+}
+
+TraceScope::~TraceScope() {
+    if (!start_) return;
+    cudaEvent_t end = nullptr;
+    if (cudaEventCreate(&end) != cudaSuccess || cudaEventRecord(end, st_) != cudaSuccess) {
+        if (end) cudaEventDestroy(end);
+        cudaEventDestroy(start_);
+        return;
+    }
+    std::lock_guard<std::mutex> g(ctx_->trace_mu);
+    if (ctx_->trace.size() >= kTraceCap) {
+        cudaEventDestroy(ctx_->trace.front().start);
+        cudaEventDestroy(ctx_->trace.front().end);
+        ctx_->trace.erase(ctx_->trace.begin());
+        ++ctx_->trace_dropped;
+    }
+    ctx_->trace.push_back({kernel_, start_, end});
+}
+
 }  // namespace tbsci
 
 using namespace tbsci;
@@ -127,6 +161,11 @@ void tbsci_destroy(tbsci_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->copy_out) cudaStreamSynchronize(ctx->copy_out);
     if (!ctx->tune_path.empty()) tbsci_tune_cache_save(ctx, ctx->tune_path.c_str());
+    for (auto &r : ctx->trace) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.end);
+    }
+    ctx->trace.clear();
     ctx->host_c.release();
     ctx->host_s.release();
     ctx->d_binom.release();
@@ -137,6 +176,41 @@ void tbsci_destroy(tbsci_ctx *ctx) {
 }
 
 const char *tbsci_last_error(const tbsci_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+tbsci_status tbsci_trace_enable(tbsci_ctx *ctx, int on) {
+    if (!ctx) return TBSCI_EINVAL;
+    ctx->trace_on.store(on != 0);
+    return TBSCI_OK;
+}
+
+tbsci_status tbsci_trace_read(tbsci_ctx *ctx, tbsci_trace_entry *out, int64_t cap, int64_t *n, int64_t *dropped) {
+    TB_GUARD_CTX(ctx);
+    TB_CHECK(ctx, n && cap >= 0 && (out || cap == 0), TBSCI_EINVAL, "tbsci_trace_read: null argument");
+    *n = 0;
+    std::vector<tbsci_ctx::TraceRec> take;
+    {
+        std::lock_guard<std::mutex> g(ctx->trace_mu);
+        const size_t k = std::min(ctx->trace.size(), (size_t)cap);
+        take.assign(ctx->trace.begin(), ctx->trace.begin() + k);
+        ctx->trace.erase(ctx->trace.begin(), ctx->trace.begin() + k);
+        if (dropped) *dropped = ctx->trace_dropped;
+        ctx->trace_dropped = 0;
+    }
+    tbsci_status st = TBSCI_OK;
+    for (size_t i = 0; i < take.size(); ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(take[i].end);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, take[i].start, take[i].end);
+        if (e != cudaSuccess && st == TBSCI_OK)
+            st = fail(ctx, TBSCI_ECUDA, std::string("tbsci_trace_read: ") + cudaGetErrorString(e));
+        out[i].kernel = take[i].kernel;
+        out[i].ms = ms;
+        cudaEventDestroy(take[i].start);
+        cudaEventDestroy(take[i].end);
+    }
+    *n = (int64_t)take.size();
+    return st;
+}
 
 tbsci_status tbsci_build_strings(tbsci_ctx *ctx, int norb, int nelec, const uint64_t *selected, int64_t nsel,
                                  tbsci_strings **out) {

@@ -109,6 +109,17 @@ struct tbsci_ctx {
     };
     std::mutex tune_mu;
     std::map<std::array<int64_t, 3>, TuneEntry> tune_cache;
+    // kernel trace (tbsci_trace_enable): while on, each sigma-path launch is
+    // bracketed by two events recorded on its own stream; tbsci_trace_read
+    // turns them into durations, oldest first
+    struct TraceRec {
+        const char *kernel;
+        cudaEvent_t start, end;
+    };
+    std::atomic<bool> trace_on{false};
+    std::mutex trace_mu;
+    std::vector<TraceRec> trace;
+    int64_t trace_dropped = 0;
 };
 
 struct tbsci_strings {
@@ -136,6 +147,23 @@ struct tbsci_tables {
 };
 
 namespace tbsci {
+
+// Records the launches made in its scope in the context's kernel trace when
+// tracing is on (nothing otherwise, and nothing while `st` is being captured
+// into a graph). `kernel` must be a string literal.
+class TraceScope {
+  public:
+    TraceScope(tbsci_ctx *ctx, const char *kernel, cudaStream_t st);
+    ~TraceScope();
+    TraceScope(const TraceScope &) = delete;
+    TraceScope &operator=(const TraceScope &) = delete;
+
+  private:
+    tbsci_ctx *ctx_;
+    const char *kernel_;
+    cudaStream_t st_;
+    cudaEvent_t start_ = nullptr;
+};
 
 // Per-spin data of one prepared space (values depend on the Hamiltonian).
 struct SpinPlan {
@@ -170,8 +198,9 @@ struct PartLayout {
     DevBuf<int2> ci;              // {target, 2 * pair + (sign < 0)}
     DevBuf<double> val;           // same-spin string-Hamiltonian value
     DevBuf<float> valf;
-    DevBuf<double> U;             // [npair][l_b], columns in perm order
-    DevBuf<float> Uf;
+    DevBuf<uint64_t> str;         // beta string of each column, in perm order
+    DevBuf<double> Eb;            // its one-electron energy, same order
+    DevBuf<float> Ebf;
 };
 
 struct Plan {
@@ -297,7 +326,7 @@ tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan 
 // same-spin double classes as column-tiled products); see the file head
 // smallest number of column parts of a c row that fits in shared memory beside
 // the accumulators of 1/nc of a sigma row (0: none fits)
-int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc, size_t budget = 0);
+int split_min_parts(const tbsci_ctx *ctx, int npair, int norb, int64_t lb, size_t elem, int nc, size_t budget = 0);
 // variant: 0 one CTA per alpha row (global accumulators), 1, 2 two or four CTAs
 // per row (shared-memory accumulators), 3 as 0 with parts for two CTAs per SM
 template <typename T>

@@ -253,6 +253,7 @@ tbsci_status launch_pruned(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, 
     for (int v = 0; v < nvec; ++v) {
         A.C = c + (size_t)v * pr->nd;
         A.S = s + (size_t)v * pr->nd;
+        TraceScope tr(ctx, "k_sigma_pruned", st);
         if (expand) {
             TB_CUDA(ctx, cudaFuncSetAttribute(k_sigma_pruned<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)full));

@@ -459,6 +459,7 @@ template <typename T, int NV, bool STAGE, bool ACCS, int TH>
 tbsci_status launch_th(tbsci_ctx *ctx, SigArgs<T> A, size_t smem, cudaStream_t st) {
     auto kern = k_sigma<T, NV, STAGE, ACCS, TH>;
     TB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TraceScope tr(ctx, "k_sigma", st);
     kern<<<(unsigned)A.la, TH, smem, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
@@ -548,6 +549,7 @@ tbsci_status launch_batch_th(tbsci_ctx *ctx, const SigArgs<T> *dargs, const int6
     TB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TH, smem));
     const int64_t grid = std::min<int64_t>(rows, (int64_t)std::max(1, per_sm) * ctx->num_sms);
     TB_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
+    TraceScope tr(ctx, "k_sigma_batch", st);
     kern<<<(unsigned)grid, TH, smem, st>>>(dargs, doff, njobs, rows, counter);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
@@ -924,7 +926,7 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
         // the sample; the double-class products, transposes and combine do not
         // depend on its shape, so their full-space time is measured once and
         // added in proportion to the sample
-        if (ret == TBSCI_OK && variant(1, 0) != 0 && split_min_parts(ctx, npair, lb, ti == 0 ? 8 : 4, 0) >= 1) {
+        if (ret == TBSCI_OK && variant(1, 0) != 0 && split_min_parts(ctx, npair, plan->norb, lb, ti == 0 ? 8 : 4, 0) >= 1) {
             float fixed = 0.f;
             ret = dt == TBSCI_F64
                       ? timed_split<double>(ctx, ham, plan, static_cast<const double *>(c), static_cast<double *>(s),
@@ -976,6 +978,7 @@ tbsci_status launch_rest_th(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_
     const size_t sm = smem_bytes<float>(A.npair, A.lb, 1, STAGE, ACCS);
     auto k = k_sigma<float, 1, STAGE, ACCS, TH, true>;
     TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TraceScope tr(ctx, "k_sigma_rest", st);
     k<<<(unsigned)A.la, TH, sm, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
@@ -986,6 +989,7 @@ tbsci_status launch_rest_pair_th(tbsci_ctx *ctx, const SigArgs<float> &A, cudaSt
     const size_t sm = smem_bytes<float>(A.npair, A.lb, 2, STAGE, false);
     auto k = k_sigma_rest_pair<STAGE, TH>;
     TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TraceScope tr(ctx, "k_sigma_rest_pair", st);
     k<<<(unsigned)A.la, TH, sm, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;

@@ -20,6 +20,7 @@
 // Every column is summed in a fixed order: results do not depend on the launch.
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -33,15 +34,17 @@ struct SplitArgs {
     int64_t la, lb;
     const T *C;
     T *S;  // K1 output: rows in the layout's column order
-    int npair, na, P, NC;
+    int npair, na, norb, P, NC;
     int64_t W;
     const uint64_t *stra;
     const int64_t *a_soff;
     const int2 *a_sci;
     const T *a_sval;
-    const T *Ea, *Eb;
+    const T *Ea;
     const T *V;  // [npair][npair]
-    const T *U;  // [npair][lb], columns in the layout's order
+    const uint64_t *pstr;  // beta string of each column, in the layout's order
+    const T *pEb;          // its one-electron energy, same order
+    int nbt;               // bytes of a beta string: ceil(norb / 8) lookup tables
     const int32_t *perm, *rowsa;
     T ecore;
     const int64_t *poff;
@@ -50,9 +53,16 @@ struct SplitArgs {
     const T *pval;
 };
 
+// shared memory ahead of the c part: the coefficient table by (pair, sign), the
+// occupied pairs of the alpha string, then 256-entry lookup tables, one per byte
+// of a beta string (their offset is split_tab_offset)
 template <typename T>
-__host__ __device__ size_t split_head_bytes(int npair) {
+__host__ __device__ size_t split_tab_offset(int npair) {
     return ((2 * npair + 2) * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15);
+}
+template <typename T>
+__host__ __device__ size_t split_head_bytes(int npair, int norb) {
+    return split_tab_offset<T>(npair) + (size_t)((norb + 7) / 8) * 256 * sizeof(T);
 }
 
 // GACC: one CTA per alpha row (NC = 1) that accumulates in the output row in
@@ -64,7 +74,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
     const int npair = A.npair;
     T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2 npair + 2]: coefficient by (pair, sign); last two zero
     int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair + 2);
-    T *sC = reinterpret_cast<T *>(smem_raw + split_head_bytes<T>(npair));  // [W]: one part of a c row
+    // sTab[256 b + v]: the column coefficient's share of the orbitals of byte b of
+    // a beta string whose byte b is v (see the table build below)
+    T *sTab = reinterpret_cast<T *>(smem_raw + split_tab_offset<T>(npair));
+    const int nbt = A.nbt;
+    T *sC = sTab + 256 * nbt;  // [W]: one part of a c row
     T *sAcc = GACC ? A.S + A.rowsa[blockIdx.x / A.NC] * A.lb  // the row itself, column order
                    : sC + A.W;  // accumulators of this CTA's column slices
     const int NC = A.NC, P = A.P;
@@ -103,7 +117,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
             ha = __ldg(A.a_sval + t);
         }
         const T *__restrict__ Crow = C + Ja * lb;
-        const T *__restrict__ Urow = A.U + (size_t)pr * lb;
         for (int p = 0; p < P; ++p) {
             const int64_t base = (int64_t)p * W, len = min(W, lb - base);
             __syncthreads();  // the previous pass is done with sC and sV2
@@ -142,47 +155,77 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
                 for (int64_t j = threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(src + j);
             }
             __syncthreads();
-            for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) {
-                const int64_t sl = (jl >> 5) * NC + kk;
-                const int lane = (int)(jl & 31);
-                const int64_t j = sl * 32 + lane;
-                if (j >= lb) continue;
-                const int64_t ib = __ldg(A.perm + j);
-                T acc = sAcc[jl];
-                if ((uint64_t)(ib - base) < (uint64_t)len) {  // the column's own c value is in this part
-                    T coef;
-                    if (self) {
-                        coef = eIa + __ldg(A.Eb + ib);
-                        for (int k = 0; k < na; ++k) coef += __ldg(A.U + (size_t)sOcc[k] * lb + j);
-                    } else {
-                        coef = ha + sa * __ldg(Urow + j);
+            if (p == 0) {
+                // The coefficient of a column's own c value is base + sum over the
+                // orbitals l of its beta string of sV2[2 ll]: sa (pr|ll) for an
+                // alpha single (base h(Ia, Ja)), sum_{q in Ia} (qq|ll) for Ja = Ia
+                // (base E_core + E_a(Ia), plus E_b of the column). The sum is read
+                // from one 256-entry table per byte of the string.
+                const T base0 = self ? eIa : ha;
+                for (int e = threadIdx.x; e < 256 * nbt; e += kThreads) {
+                    const int b = e >> 8, v = e & 255;
+                    T x = b == 0 ? base0 : T(0);
+                    for (int i = 0; i < 8; ++i) {
+                        const int l = 8 * b + i;
+                        if (((v >> i) & 1) && l < A.norb) x += sV2[2 * (l * (l + 1) / 2 + l)];
                     }
-                    acc += coef * sC[ib - base];
+                    sTab[e] = x;
                 }
-                const int64_t o = __ldg(A.poff + sl * P + p) + lane;
-                const int w = __ldg(A.pw + sl * P + p);
-                const int2 *ci = A.pci + o;
-                const T *cv = A.pval + o;
-                T acc2 = T(0);
-                int k = 0;
-                for (; k + 1 < w; k += 2) {
-                    const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
-                    T x0 = sV2[e0.y], x1 = sV2[e1.y];
-                    if (self) {
-                        x0 += __ldg(cv + 32 * k);
-                        x1 += __ldg(cv + 32 * (k + 1));
-                    }
-                    acc += x0 * sC[e0.x - base];
-                    acc2 += x1 * sC[e1.x - base];
-                }
-                if (k < w) {
-                    const int2 e = __ldg(ci + 32 * k);
-                    T x = sV2[e.y];
-                    if (self) x += __ldg(cv + 32 * k);
-                    acc += x * sC[e.x - base];
-                }
-                sAcc[jl] = acc + acc2;
+                __syncthreads();
             }
+            // the column sweep, compiled separately for the Ja = Ia term so that the
+            // singles' inner loop carries no per-link test of the term kind
+            auto sweep = [&](auto self_tag) {
+                constexpr bool SELF = decltype(self_tag)::value;
+                for (int64_t jl = threadIdx.x; jl < nloc; jl += kThreads) {
+                    const int64_t sl = (jl >> 5) * NC + kk;
+                    const int lane = (int)(jl & 31);
+                    const int64_t j = sl * 32 + lane;
+                    if (j >= lb) continue;
+                    const int64_t ib = __ldg(A.perm + j);
+                    T acc = sAcc[jl];
+                    if ((uint64_t)(ib - base) < (uint64_t)len) {  // the column's own c value is in this part
+                        const uint64_t sb = __ldg(A.pstr + j);
+                        T coef = sTab[sb & 255];
+                        for (int b = 1; b < nbt; ++b) coef += sTab[256 * b + ((sb >> (8 * b)) & 255)];
+                        if (SELF) coef += __ldg(A.pEb + j);
+                        acc += coef * sC[ib - base];
+                    }
+                    const int64_t o = __ldg(A.poff + sl * P + p) + lane;
+                    const int w = __ldg(A.pw + sl * P + p);
+                    const int2 *ci = A.pci + o;
+                    const T *cv = A.pval + o;
+                    T acc2 = T(0);
+                    int k = 0;
+                    // four links in flight per iteration: their loads overlap
+                    for (; k + 3 < w; k += 4) {
+                        const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                        const int2 e2 = __ldg(ci + 32 * (k + 2)), e3 = __ldg(ci + 32 * (k + 3));
+                        T x0 = sV2[e0.y], x1 = sV2[e1.y], x2 = sV2[e2.y], x3 = sV2[e3.y];
+                        if (SELF) {
+                            x0 += __ldg(cv + 32 * k);
+                            x1 += __ldg(cv + 32 * (k + 1));
+                            x2 += __ldg(cv + 32 * (k + 2));
+                            x3 += __ldg(cv + 32 * (k + 3));
+                        }
+                        acc += x0 * sC[e0.x - base];
+                        acc2 += x1 * sC[e1.x - base];
+                        acc += x2 * sC[e2.x - base];
+                        acc2 += x3 * sC[e3.x - base];
+                    }
+                    for (; k < w; ++k) {
+                        const int2 e = __ldg(ci + 32 * k);
+                        T x = sV2[e.y];
+                        if (SELF) x += __ldg(cv + 32 * k);
+                        acc += x * sC[e.x - base];
+                    }
+                    sAcc[jl] = acc + acc2;
+                }
+            };
+            if (self)
+                sweep(std::true_type{});
+            else
+                sweep(std::false_type{});
         }
     }
     if (GACC) return;  // the row was accumulated in place
@@ -272,18 +315,6 @@ __global__ void k_combine(T *y, const T *__restrict__ pz, const int32_t *__restr
     }
 }
 
-// k_permute_cols equivalent for the part layout's Coulomb tables:
-// out[r][j] = in[r][perm[j]]
-__global__ void k_gather_cols(const double *__restrict__ in, int64_t rows, int64_t lb, const int32_t *__restrict__ perm,
-                              double *out, float *outf) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t r = blockIdx.y;
-    if (j >= lb || r >= rows) return;
-    const double v = in[r * lb + perm[j]];
-    out[r * lb + j] = v;
-    outf[r * lb + j] = (float)v;
-}
-
 // Part layout of the beta single links for `nparts` column parts (built on the host).
 tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int nparts, PartLayout **out) {
     for (auto &pl : P->parts)
@@ -350,11 +381,21 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
                 for (int k = fill[p]; k < lw[sl * nparts + p]; ++k)
                     ci[loff[sl * nparts + p] + 32 * (int64_t)k + lane] = make_int2((int)(p * W), zero_idx);
         }
+    // beta strings and their energies in the layout's column order
+    std::vector<uint64_t> hstr(lb), pstr(lb);
+    std::vector<double> hE(lb), pE(lb);
+    std::vector<float> pEf(lb);
+    TB_CUDA(ctx, cudaMemcpy(hstr.data(), P->B.d_str, lb * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    TB_CUDA(ctx, cudaMemcpy(hE.data(), P->B.d_E.p, lb * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < lb; ++j) {
+        pstr[j] = hstr[perm[j]];
+        pE[j] = hE[perm[j]];
+        pEf[j] = (float)pE[j];
+    }
     auto pl = std::make_unique<PartLayout>();
     pl->P = nparts;
     pl->W = W;
-    const int64_t np = ham->npair;
-    const size_t bytes = loff.size() * 12 + ci.size() * (sizeof(int2) + 12) + (size_t)lb * 8 + (size_t)np * lb * 12;
+    const size_t bytes = loff.size() * 12 + ci.size() * (sizeof(int2) + 12) + (size_t)lb * 28;
     TB_TRY(charge(ctx, bytes, "column-part link layout"));
     cudaError_t e = pl->off.alloc(loff.size());
     if (e == cudaSuccess) e = pl->w.alloc(lw.size());
@@ -363,8 +404,9 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
     if (e == cudaSuccess) e = pl->valf.alloc(vf.size());
     if (e == cudaSuccess) e = pl->perm.alloc(lb);
     if (e == cudaSuccess) e = pl->iperm.alloc(lb);
-    if (e == cudaSuccess) e = pl->U.alloc((size_t)np * lb);
-    if (e == cudaSuccess) e = pl->Uf.alloc((size_t)np * lb);
+    if (e == cudaSuccess) e = pl->str.alloc(lb);
+    if (e == cudaSuccess) e = pl->Eb.alloc(lb);
+    if (e == cudaSuccess) e = pl->Ebf.alloc(lb);
     if (e == cudaSuccess && !loff.empty())
         e = cudaMemcpy(pl->off.p, loff.data(), loff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !lw.empty())
@@ -374,12 +416,9 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
     if (e == cudaSuccess) e = cudaMemcpy(pl->valf.p, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->perm.p, perm.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->iperm.p, iperm.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        k_gather_cols<<<dim3((unsigned)((lb + 127) / 128), (unsigned)np), 128, 0, ctx->stream>>>(
-            P->d_U.p, np, lb, pl->perm.p, pl->U.p, pl->Uf.p);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    }
+    if (e == cudaSuccess) e = cudaMemcpy(pl->str.p, pstr.data(), lb * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->Eb.p, pE.data(), lb * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->Ebf.p, pEf.data(), lb * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         uncharge(ctx, bytes);
         return fail(ctx, e == cudaErrorMemoryAllocation ? TBSCI_ENOMEM : TBSCI_ECUDA,
@@ -395,6 +434,7 @@ template <typename T, int TH, bool GACC, int MINB = 1>
 tbsci_status launch_parts_th(tbsci_ctx *ctx, const SplitArgs<T> &A, size_t smem, cudaStream_t st) {
     auto k = k_sigma_parts<T, TH, GACC, MINB>;
     TB_CUDA(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TraceScope tr(ctx, "k_sigma_parts", st);
     k<<<(unsigned)(A.la * A.NC), TH, smem, st>>>(A);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
@@ -405,11 +445,13 @@ constexpr int dbl_tile() { return sizeof(T) == 8 ? 128 : 256; }
 
 template <typename T>
 tbsci_status launch_dbl(tbsci_ctx *ctx, const T *X, T *Y, int64_t rows, int64_t ld, const int64_t *off,
-                        const int32_t *col, const T *val, bool accumulate, cudaStream_t st) {
+                        const int32_t *col, const T *val, bool accumulate, cudaStream_t st,
+                        const char *name) {
     if (rows == 0 || ld == 0) return TBSCI_OK;
     constexpr int TW = dbl_tile<T>();
     const int64_t nrb = (rows + kDblRows - 1) / kDblRows, ntiles = (ld + TW - 1) / TW;
     TB_CHECK(ctx, nrb * ntiles <= INT32_MAX, TBSCI_EINVAL, "double-class product: grid too large");
+    TraceScope tr(ctx, name, st);
     k_dbl_spmm<T, TW><<<(unsigned)(nrb * ntiles), TW, 0, st>>>(X, Y, rows, ld, off, col, val, nrb, accumulate ? 1 : 0);
     TB_CUDA(ctx, cudaGetLastError());
     return TBSCI_OK;
@@ -432,9 +474,11 @@ SplitArgs<double> split_args<double>(const tbsci_ham *ham, const Plan *P, const 
     A.a_sci = P->A.d_sci.p;
     A.a_sval = P->A.d_sval.p;
     A.Ea = P->A.d_E.p;
-    A.Eb = P->B.d_E.p;
+    A.norb = P->norb;
+    A.nbt = (P->norb + 7) / 8;
     A.V = ham->d_V.p;
-    A.U = pl->U.p;
+    A.pstr = pl->str.p;
+    A.pEb = pl->Eb.p;
     A.perm = pl->perm.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = ham->ecore;
@@ -459,9 +503,11 @@ SplitArgs<float> split_args<float>(const tbsci_ham *ham, const Plan *P, const Pa
     A.a_sci = P->A.d_sci.p;
     A.a_sval = P->A.d_svalf.p;
     A.Ea = P->A.d_Ef.p;
-    A.Eb = P->B.d_Ef.p;
+    A.norb = P->norb;
+    A.nbt = (P->norb + 7) / 8;
     A.V = ham->d_Vf.p;
-    A.U = pl->Uf.p;
+    A.pstr = pl->str.p;
+    A.pEb = pl->Ebf.p;
     A.perm = pl->perm.p;
     A.rowsa = P->d_rowsa.p;
     A.ecore = (float)ham->ecore;
@@ -481,8 +527,8 @@ const float *dval_of<float>(const SpinPlan &sp) { return sp.d_dvalf.p; }
 
 }  // namespace
 
-int split_min_parts(const tbsci_ctx *ctx, int npair, int64_t lb, size_t elem, int nc, size_t budget) {
-    const size_t head = elem == 8 ? split_head_bytes<double>(npair) : split_head_bytes<float>(npair);
+int split_min_parts(const tbsci_ctx *ctx, int npair, int norb, int64_t lb, size_t elem, int nc, size_t budget) {
+    const size_t head = elem == 8 ? split_head_bytes<double>(npair, norb) : split_head_bytes<float>(npair, norb);
     const int64_t nsl = (lb + 31) / 32;
     const size_t acc = nc == 0 ? 0 : (size_t)((nsl + nc - 1) / nc) * 32 * elem;  // nc 0: accumulators in global memory
     const size_t lim = budget ? std::min(budget, ctx->smem_optin) : ctx->smem_optin;
@@ -509,7 +555,7 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
     const size_t budget = variant == 3 ? ctx->smem_per_sm / 2 - 1024 : 0;
     int nc = gacc ? 1 : (variant == 1 ? 2 : 4), nparts = 0;
     for (; nc <= 4; nc *= 2) {
-        nparts = split_min_parts(ctx, P->npair, lb, sizeof(T), gacc ? 0 : nc, budget);
+        nparts = split_min_parts(ctx, P->npair, P->norb, lb, sizeof(T), gacc ? 0 : nc, budget);
         if (nparts >= 1 || gacc) break;
     }
     TB_CHECK(ctx, nparts >= 1 && nc <= 4, TBSCI_EINVAL, "split sigma: no room for a column part in shared memory");
@@ -538,7 +584,7 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
         A.la = nrows;
     }
     const int64_t nsl = (lb + 31) / 32;
-    const size_t smem = split_head_bytes<T>(P->npair) + (size_t)pl->W * sizeof(T) +
+    const size_t smem = split_head_bytes<T>(P->npair, P->norb) + (size_t)pl->W * sizeof(T) +
                         (gacc ? 0 : (size_t)((nsl + nc - 1) / nc) * 32 * sizeof(T));
     T *ct = reinterpret_cast<T *>(P->d_trans.p), *sz = ct + (size_t)la * lb;
     const dim3 tb(32, 8), tgrid((unsigned)((lb + 31) / 32), (unsigned)((la + 31) / 32));
@@ -547,9 +593,13 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
         T *sv = s + (size_t)v * la * lb;
         if (mode != 1) {
             // [0,2]: sz = H_beta,doubles c^T (c^T in ct)
-            k_transpose<T><<<tgrid, tb, 0, st>>>(cv, ct, la, lb);
-            TB_CUDA(ctx, cudaGetLastError());
-            TB_TRY(launch_dbl<T>(ctx, ct, sz, lb, la, P->B.d_doff, P->B.d_dcol.p, dval_of<T>(P->B), false, st));
+            {
+                TraceScope tr(ctx, "k_transpose", st);
+                k_transpose<T><<<tgrid, tb, 0, st>>>(cv, ct, la, lb);
+                TB_CUDA(ctx, cudaGetLastError());
+            }
+            TB_TRY(launch_dbl<T>(ctx, ct, sz, lb, la, P->B.d_doff, P->B.d_dcol.p, dval_of<T>(P->B), false, st,
+                                 "k_dbl_spmm_beta"));
         }
         if (mode != 2) {
             // K1 rows in the layout's column order into ct (free once c^T has been used)
@@ -566,10 +616,14 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
             }
         }
         if (mode == 1) continue;
-        k_combine<T><<<tgrid, tb, 0, st>>>(sv, ct, pl->iperm.p, sz, la, lb);
-        TB_CUDA(ctx, cudaGetLastError());
+        {
+            TraceScope tr(ctx, "k_combine", st);
+            k_combine<T><<<tgrid, tb, 0, st>>>(sv, ct, pl->iperm.p, sz, la, lb);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
         // [2,0]: sigma += H_alpha,doubles c
-        TB_TRY(launch_dbl<T>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, dval_of<T>(P->A), true, st));
+        TB_TRY(launch_dbl<T>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, dval_of<T>(P->A), true, st,
+                             "k_dbl_spmm_alpha"));
     }
     return TBSCI_OK;
 }
@@ -645,12 +699,20 @@ tbsci_status rest_products_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P,
     for (int v = 0; v < nvec; ++v) {
         const float *cv = c + (size_t)v * la * lb;
         float *sv = s + (size_t)v * la * lb;
-        k_transpose<float><<<tg_ab, tb, 0, st>>>(cv, ct, la, lb);
-        TB_CUDA(ctx, cudaGetLastError());
-        TB_TRY(launch_dbl<float>(ctx, ct, sz, lb, la, P->d_bss_off.p, P->d_bss_col.p, P->d_bss_valf.p, false, st));
-        k_transpose<float><<<tg_ba, tb, 0, st>>>(sz, sv, lb, la);  // sigma = (beta classes)^T
-        TB_CUDA(ctx, cudaGetLastError());
-        TB_TRY(launch_dbl<float>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, P->A.d_dvalf.p, true, st));
+        {
+            TraceScope tr(ctx, "k_transpose", st);
+            k_transpose<float><<<tg_ab, tb, 0, st>>>(cv, ct, la, lb);
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+        TB_TRY(launch_dbl<float>(ctx, ct, sz, lb, la, P->d_bss_off.p, P->d_bss_col.p, P->d_bss_valf.p, false, st,
+                                 "k_dbl_spmm_beta"));
+        {
+            TraceScope tr(ctx, "k_transpose", st);
+            k_transpose<float><<<tg_ba, tb, 0, st>>>(sz, sv, lb, la);  // sigma = (beta classes)^T
+            TB_CUDA(ctx, cudaGetLastError());
+        }
+        TB_TRY(launch_dbl<float>(ctx, cv, sv, la, lb, P->A.d_doff, P->A.d_dcol.p, P->A.d_dvalf.p, true, st,
+                                 "k_dbl_spmm_alpha"));
     }
     return TBSCI_OK;
 }

@@ -376,6 +376,7 @@ tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *P, c
     for (int v = 0; v < nvec; ++v) {
         A.C = c + (size_t)v * la * lb;
         A.S = s + (size_t)v * la * lb;
+        TraceScope tr(ctx, "k_sigma_ab_tc", st);
         kern<<<(unsigned)la, bf16 ? tc_threads<true>() : tc_threads<false>(), smem, st>>>(A);
         TB_CUDA(ctx, cudaGetLastError());
     }

@@ -34,20 +34,47 @@ def test_clock_summary(bench):
 
 
 def test_traffic_only_for_the_profiled_kernel_source_and_shape(bench, monkeypatch):
-    rec = bench.NCU_TRAFFIC[("sel16", "f64")]
-    monkeypatch.setattr(bench, "_kernel_hash", lambda: rec["sha1"])
+    rec = bench.NCU_TRAFFIC[("sel16", "f64", "k_sigma")]
+    monkeypatch.setattr(bench, "_source_hash", lambda name: rec["sha1"])
     shapes = rec["shapes"]
-    # 3 vectors at 2 per CTA: one 2-vector launch and one 1-vector launch
-    assert bench._traffic("sel16", "f64", 512, 2, 0, 3) == pytest.approx((shapes[(512, 2, 0)] + shapes[(512, 1, 0)]) / 2)
-    assert bench._traffic("sel16", "f64", 512, 3, 0, 3) == pytest.approx(shapes[(512, 3, 0)])
-    assert bench._traffic("sel16", "f64", 512, 1, 0, 3) == pytest.approx(shapes[(512, 1, 0)])
-    assert bench._traffic("sel16", "f64", 256, 2, 0, 3) is None  # shape not captured
-    assert bench._traffic("sel16", "f64", 512, 0, 0, 3) is None  # not tuned
-    assert bench._traffic("fci16", "f64", 512, 1, 0, 1) is None  # workload not captured
-    monkeypatch.setattr(bench, "_kernel_hash", lambda: "0" * 40)
-    assert bench._traffic("sel16", "f64", 512, 2, 0, 3) is None  # kernel source changed since the capture
-    assert bench._traffic("sel16", "bf16tc", 512, 2, 0, 3) is None
 
+    def counts(threads, nv, stage):
+        return {"tuned_threads": [threads, 0], "tuned_nv": [nv, 0], "tuned_stage": [stage, 0]}
+
+    # three vectors in groups of two: one launch of two and one of one
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 2, 0), 3) == pytest.approx(
+        (shapes[(512, 2, 0)] + shapes[(512, 1, 0)]) / 2)
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 3, 0), 3) == pytest.approx(shapes[(512, 3, 0)])
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 1, 0), 3) == pytest.approx(shapes[(512, 1, 0)])
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(256, 2, 0), 3) is None  # shape not captured
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 0, 0), 3) is None  # not tuned
+    assert bench._traffic("fci16", "f64", "k_sigma", counts(512, 1, 0), 1) is None  # workload not captured
+    assert bench._traffic("sel16", "f64", "k_sigma_parts", counts(512, 1, 3), 1) is None  # kernel not captured
+    monkeypatch.setattr(bench, "_source_hash", lambda name: "0" * 40)
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 2, 0), 3) is None  # source changed since
+    assert bench._traffic("sel16", "bf16tc", "k_sigma", counts(512, 2, 0), 3) is None
+
+
+def test_kernel_table_shares_and_fractions(bench):
+    """Per-kernel rows from a synthetic trace of two split-path steps: shares sum
+    to one, the row kernel's work counts the diagonal, single and alpha-beta
+    classes, and the transposes are measured against HBM."""
+    c = {"la": 100, "lb": 200, "ndet": 20000, "nnz": 0, "n1a": 300, "n2a": 900, "n1b": 500, "n2b": 1100,
+         "norb": 10}
+    step = [("k_transpose", 1.0), ("k_dbl_spmm_beta", 4.0), ("k_sigma_parts", 10.0), ("k_combine", 1.0),
+            ("k_dbl_spmm_alpha", 4.0)]
+    rows = bench._kernel_table(step * 2, 2, c, 1, "f64")
+    assert [r["kernel"] for r in rows][0] == "k_sigma_parts"
+    assert sum(r["share"] for r in rows) == pytest.approx(1.0)
+    k1 = rows[0]
+    assert k1["launches_per_step"] == 1 and k1["ms_per_launch"] == 10.0
+    assert k1["work_per_launch"] == 2.0 * (20000 + 300 * 200 + 500 * 100 + 300 * 500)
+    assert k1["achieved"] == pytest.approx(k1["work_per_launch"] / 1e-2 / 1e12)
+    assert k1["frac"] == pytest.approx(k1["achieved"] / bench.FP64_NOMINAL_TFLOPS)
+    tr = [r for r in rows if r["kernel"] == "k_transpose"][0]
+    assert tr["bound"] == "hbm" and tr["work_per_launch"] == 2 * 20000 * 8
+    beta = [r for r in rows if r["kernel"] == "k_dbl_spmm_beta"][0]
+    assert beta["work_per_launch"] == 2.0 * 1100 * 100
 
 def test_replica_throughput_and_single_rank_max(bench):
     assert bench.replica_throughput(2, 9e6, 0.5) == pytest.approx(3.6e7)

@@ -1,7 +1,8 @@
 """The split sigma path for rows longer than shared memory (row a4-a6 at the
-norb-24 workload): the row kernel with c rows staged in column parts (stage 3,
-4, 5: one, two or four CTAs per alpha row, each keeping the sigma accumulators
-of its share of the columns in shared memory), plus the
+norb-24 workload): the row kernel with c rows staged in column parts (stage 3:
+one CTA per alpha row accumulating in the output row; 4, 5: two or four CTAs
+per alpha row, each keeping the sigma accumulators of its share of the columns
+in shared memory; 6: as 3 with parts short enough for two CTAs per SM), plus the
 alpha-double and beta-double classes as column-tiled sparse x dense products
 (the latter on the transposed vector). Each launch shape is pinned through a
 tune-cache file and compared with the oracle element by element, on spaces that
@@ -47,7 +48,7 @@ def _ctx_with_shape(tb, tmp_path, n, la, lb, dtype, threads, stage):
 CASES = [
     # n, na, nb, alpha count, beta count, nvec
     (8, 4, 4, None, None, 2),
-    (10, 5, 5, 120, 257, 3),    # 257 beta columns: ragged slices, transpose tiles and column tiles
+    (10, 5, 5, 120, 257, 3),    # all 252 beta strings: ragged slices, transpose tiles and column tiles
     (12, 6, 6, 300, 280, 1),
     (12, 4, 6, None, 200, 2),   # distinct alpha and beta sets of different sizes
     (9, 1, 0, None, None, 1),   # no beta electron
@@ -55,7 +56,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("threads,stage", [(512, 3), (1024, 4), (512, 5)])
+@pytest.mark.parametrize("threads,stage", [(512, 3), (1024, 3), (1024, 4), (512, 5), (512, 6)])
 @pytest.mark.parametrize("n,na,nb,acnt,bcnt,nvec", CASES)
 def test_split_sigma_parity(tb, tmp_path, n, na, nb, acnt, bcnt, nvec, threads, stage, dtype):
     import torch

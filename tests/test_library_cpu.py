@@ -74,7 +74,8 @@ def test_binding_struct_layout_matches_header(tmp_path):
     pairs = [("tbsci_single_link", B.SingleLink), ("tbsci_double_link", B.DoubleLink),
              ("tbsci_sigma_counts", B.SigmaCounts), ("tbsci_davidson_opts", B.DavidsonOpts),
              ("tbsci_davidson_info", B.DavidsonInfo), ("tbsci_server_opts", B.ServerOpts),
-             ("tbsci_request", B.Request), ("tbsci_result", B.Result)]
+             ("tbsci_request", B.Request), ("tbsci_result", B.Result), ("tbsci_trace_entry", B.TraceEntry),
+             ("tbsci_options", B.Options)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tbsci.h"', "int main(void) {"]
     for cname, cls in pairs:
         lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
