@@ -142,14 +142,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
                 uint4 *d4 = reinterpret_cast<uint4 *>(sC);
                 int64_t q = threadIdx.x;
                 for (; q + 3 * kThreads < nv; q += 4 * kThreads) {
-                    const uint4 a = __ldg(s4 + q), b = __ldg(s4 + q + kThreads), c2 = __ldg(s4 + q + 2 * kThreads),
-                                d = __ldg(s4 + q + 3 * kThreads);
+                    const uint4 a = __ldcs(s4 + q), b = __ldcs(s4 + q + kThreads), c2 = __ldcs(s4 + q + 2 * kThreads),
+                                d = __ldcs(s4 + q + 3 * kThreads);
                     d4[q] = a;
                     d4[q + kThreads] = b;
                     d4[q + 2 * kThreads] = c2;
                     d4[q + 3 * kThreads] = d;
                 }
-                for (; q < nv; q += kThreads) d4[q] = __ldg(s4 + q);
+                for (; q < nv; q += kThreads) d4[q] = __ldcs(s4 + q);
                 for (int64_t j = nv * E + threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(src + j);
             } else {
                 for (int64_t j = threadIdx.x; j < len; j += kThreads) sC[j] = __ldg(src + j);
@@ -195,9 +195,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
                     const int w = __ldg(A.pw + sl * P + p);
                     const int2 *ci = A.pci + o;
                     const T *cv = A.pval + o;
-                    T acc2 = T(0);
                     int k = 0;
-                    // four links in flight per iteration: their loads overlap
+                    // four links in flight per iteration: their loads overlap. One
+                    // accumulator: the FP64 pipe, not the add latency, is the limit,
+                    // and a second chain would cost an add per column and part
                     for (; k + 3 < w; k += 4) {
                         const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
                         const int2 e2 = __ldg(ci + 32 * (k + 2)), e3 = __ldg(ci + 32 * (k + 3));
@@ -209,9 +210,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
                             x3 += __ldg(cv + 32 * (k + 3));
                         }
                         acc += x0 * sC[e0.x - base];
-                        acc2 += x1 * sC[e1.x - base];
+                        acc += x1 * sC[e1.x - base];
                         acc += x2 * sC[e2.x - base];
-                        acc2 += x3 * sC[e3.x - base];
+                        acc += x3 * sC[e3.x - base];
                     }
                     for (; k < w; ++k) {
                         const int2 e = __ldg(ci + 32 * k);
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
                         if (SELF) x += __ldg(cv + 32 * k);
                         acc += x * sC[e.x - base];
                     }
-                    sAcc[jl] = acc + acc2;
+                    sAcc[jl] = acc;
                 }
             };
             if (self)
