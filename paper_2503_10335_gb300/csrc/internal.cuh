@@ -195,7 +195,8 @@ struct PartLayout {
     DevBuf<int32_t> perm, iperm;  // column order and its inverse
     DevBuf<int64_t> off;          // [nslices * P]
     DevBuf<int32_t> w;            // [nslices * P]
-    DevBuf<int2> ci;              // {target, 2 * pair + (sign < 0)}
+    // one 32-bit link: (target - part start) << kPartLinkBits | (2 * pair + (sign < 0))
+    DevBuf<uint32_t> ci;
     DevBuf<double> val;           // same-spin string-Hamiltonian value
     DevBuf<float> valf;
     DevBuf<uint64_t> str;         // beta string of each column, in perm order
@@ -216,7 +217,10 @@ struct Plan {
     // slice's longest list with zero-coefficient entries (coalesced warp loads).
     DevBuf<int64_t> d_s1_off, d_s2_off, d_d2_off;
     DevBuf<int32_t> d_s1_w, d_s2_w, d_d2_w;
-    DevBuf<int2> d_s1_ci, d_s2_ci;       // singles {target, 2*pair + neg}; s1: permb order, s2: permb2 order
+    // singles, one 32-bit word each: target << link_shift | (2*pair + neg); s1: permb
+    // order, s2: permb2 order. link_shift bits hold the coefficient index.
+    DevBuf<uint32_t> d_s1_ci, d_s2_ci;
+    int link_shift = 0;
     DevBuf<double> d_s2_val, d_d2_val;   // string-Hamiltonian values (permb2 order)
     DevBuf<float> d_s2_valf, d_d2_valf;
     DevBuf<int32_t> d_d2_col;            // doubles target (permb2 order)

@@ -57,7 +57,8 @@ struct SigArgs {
     // values and doubles in permb2 order; tables with columns in those orders
     const int64_t *s1_off, *s2_off, *d2_off;
     const int32_t *s1_w, *s2_w, *d2_w;
-    const int2 *s1_ci, *s2_ci;
+    const uint32_t *s1_ci, *s2_ci;  // packed: target << lsh | coefficient index
+    int lsh;
     const T *s2_val, *d2_val;
     const int32_t *d2_col;
     const T *U1, *U2, *Eb2;
@@ -73,6 +74,8 @@ template <typename T, int NV, bool STAGE, bool ACCS, int kThreads, bool REST = f
 __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia, unsigned char *smem_raw) {
     const int npair = A.npair;
     const int64_t lb = A.lb, vs = A.vstride;
+    const int lsh = A.lsh;
+    const uint32_t lmask = (1u << lsh) - 1u;
     T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2*npair + 2], last two entries zero (padding)
     int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair + 2);
     T *sC = reinterpret_cast<T *>(smem_raw + (((2 * npair + 2) * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15)));
@@ -133,25 +136,25 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
             acc2[v] = T(0);
         }
         {
-            const int2 *ci = A.s2_ci + A.s2_off[sl] + lane;
+            const uint32_t *ci = A.s2_ci + A.s2_off[sl] + lane;
             const T *cv = A.s2_val + A.s2_off[sl] + lane;
             const int w = A.s2_w[sl];
             int k = 0;
             for (; k + 1 < w; k += 2) {
-                const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
-                const T x0 = __ldg(cv + 32 * k) + sV2[e0.y];
-                const T x1 = __ldg(cv + 32 * (k + 1)) + sV2[e1.y];
+                const uint32_t e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                const T x0 = __ldg(cv + 32 * k) + sV2[e0 & lmask];
+                const T x1 = __ldg(cv + 32 * (k + 1)) + sV2[e1 & lmask];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    acc[v] += x0 * cval(v, Ia, e0.x);
-                    acc2[v] += x1 * cval(v, Ia, e1.x);
+                    acc[v] += x0 * cval(v, Ia, e0 >> lsh);
+                    acc2[v] += x1 * cval(v, Ia, e1 >> lsh);
                 }
             }
             if (k < w) {
-                const int2 e = __ldg(ci + 32 * k);
-                const T x = __ldg(cv + 32 * k) + sV2[e.y];
+                const uint32_t e = __ldg(ci + 32 * k);
+                const T x = __ldg(cv + 32 * k) + sV2[e & lmask];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, e.x);
+                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, e >> lsh);
             }
         }
         {
@@ -207,23 +210,23 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
                 acc[v] = acc_ref(v, ib) + coef * cval(v, Ja, ib);
                 acc2[v] = T(0);
             }
-            const int2 *ci = A.s1_ci + A.s1_off[sl] + lane;
+            const uint32_t *ci = A.s1_ci + A.s1_off[sl] + lane;
             const int w = A.s1_w[sl];
             int k = 0;
             for (; k + 1 < w; k += 2) {
-                const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
-                const T x0 = sV2[e0.y], x1 = sV2[e1.y];
+                const uint32_t e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                const T x0 = sV2[e0 & lmask], x1 = sV2[e1 & lmask];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    acc[v] += x0 * cval(v, Ja, e0.x);
-                    acc2[v] += x1 * cval(v, Ja, e1.x);
+                    acc[v] += x0 * cval(v, Ja, e0 >> lsh);
+                    acc2[v] += x1 * cval(v, Ja, e1 >> lsh);
                 }
             }
             if (k < w) {
-                const int2 e = __ldg(ci + 32 * k);
-                const T x = sV2[e.y];
+                const uint32_t e = __ldg(ci + 32 * k);
+                const T x = sV2[e & lmask];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ja, e.x);
+                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ja, e >> lsh);
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v] + acc2[v];
@@ -367,6 +370,7 @@ void set_sell(SigArgs<T> &A, const Plan *P) {
     A.d2_w = P->d_d2_w.p;
     A.s1_ci = P->d_s1_ci.p;
     A.s2_ci = P->d_s2_ci.p;
+    A.lsh = P->link_shift;
     A.d2_col = P->d_d2_col.p;
 }
 

@@ -29,6 +29,11 @@ namespace tbsci {
 
 namespace {
 
+// A part layout link packs the target's offset in its column part (below 2^19:
+// a part fits in shared memory) above the coefficient index 2 pair + sign (below
+// 2^13: at most 2,080 pairs for 64 orbitals, plus the zero padding entries).
+constexpr int kPartLinkBits = 13;
+
 template <typename T>
 struct SplitArgs {
     int64_t la, lb;
@@ -49,7 +54,7 @@ struct SplitArgs {
     T ecore;
     const int64_t *poff;
     const int32_t *pw;
-    const int2 *pci;
+    const uint32_t *pci;  // packed links: part-local target << kPartLinkBits | coefficient index
     const T *pval;
 };
 
@@ -193,32 +198,33 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sigma_parts(SplitArgs<T> A) 
                     }
                     const int64_t o = __ldg(A.poff + sl * P + p) + lane;
                     const int w = __ldg(A.pw + sl * P + p);
-                    const int2 *ci = A.pci + o;
+                    const uint32_t *ci = A.pci + o;
                     const T *cv = A.pval + o;
+                    constexpr uint32_t kIdx = (1u << kPartLinkBits) - 1;
                     int k = 0;
                     // four links in flight per iteration: their loads overlap. One
                     // accumulator: the FP64 pipe, not the add latency, is the limit,
                     // and a second chain would cost an add per column and part
                     for (; k + 3 < w; k += 4) {
-                        const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
-                        const int2 e2 = __ldg(ci + 32 * (k + 2)), e3 = __ldg(ci + 32 * (k + 3));
-                        T x0 = sV2[e0.y], x1 = sV2[e1.y], x2 = sV2[e2.y], x3 = sV2[e3.y];
+                        const uint32_t e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                        const uint32_t e2 = __ldg(ci + 32 * (k + 2)), e3 = __ldg(ci + 32 * (k + 3));
+                        T x0 = sV2[e0 & kIdx], x1 = sV2[e1 & kIdx], x2 = sV2[e2 & kIdx], x3 = sV2[e3 & kIdx];
                         if (SELF) {
                             x0 += __ldg(cv + 32 * k);
                             x1 += __ldg(cv + 32 * (k + 1));
                             x2 += __ldg(cv + 32 * (k + 2));
                             x3 += __ldg(cv + 32 * (k + 3));
                         }
-                        acc += x0 * sC[e0.x - base];
-                        acc += x1 * sC[e1.x - base];
-                        acc += x2 * sC[e2.x - base];
-                        acc += x3 * sC[e3.x - base];
+                        acc += x0 * sC[e0 >> kPartLinkBits];
+                        acc += x1 * sC[e1 >> kPartLinkBits];
+                        acc += x2 * sC[e2 >> kPartLinkBits];
+                        acc += x3 * sC[e3 >> kPartLinkBits];
                     }
                     for (; k < w; ++k) {
-                        const int2 e = __ldg(ci + 32 * k);
-                        T x = sV2[e.y];
+                        const uint32_t e = __ldg(ci + 32 * k);
+                        T x = sV2[e & kIdx];
                         if (SELF) x += __ldg(cv + 32 * k);
-                        acc += x * sC[e.x - base];
+                        acc += x * sC[e >> kPartLinkBits];
                     }
                     sAcc[jl] = acc;
                 }
@@ -325,6 +331,8 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
         }
     const int64_t lb = P->B.l, nsl = (lb + 31) / 32;
     const int64_t W = (lb + nparts - 1) / nparts;
+    TB_CHECK(ctx, W < (int64_t(1) << (32 - kPartLinkBits)) && 2 * ham->npair + 2 <= (1 << kPartLinkBits),
+             TBSCI_EINVAL, "split sigma: column part or pair count too large for the packed link layout");
     const int64_t ns = P->B.h_soff.empty() ? 0 : P->B.h_soff[lb];
     std::vector<int2> sci(ns);
     std::vector<double> sval(ns);
@@ -360,7 +368,7 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
             total += 32 * (int64_t)w;
         }
     const int zero_idx = 2 * ham->npair;
-    std::vector<int2> ci(std::max<int64_t>(total, 1));
+    std::vector<uint32_t> ci(std::max<int64_t>(total, 1));
     std::vector<double> v(std::max<int64_t>(total, 1), 0.0);
     std::vector<float> vf(std::max<int64_t>(total, 1), 0.f);
     std::vector<int32_t> fill(nparts);
@@ -373,14 +381,14 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
                 for (int64_t t = off[ib]; t < off[ib + 1]; ++t) {
                     const int p = (int)(sci[t].x / W);
                     const int64_t pos = loff[sl * nparts + p] + 32 * (int64_t)fill[p]++ + lane;
-                    ci[pos] = sci[t];
+                    ci[pos] = ((uint32_t)(sci[t].x - p * W) << kPartLinkBits) | (uint32_t)sci[t].y;
                     v[pos] = sval[t];
                     vf[pos] = (float)sval[t];
                 }
             }
             for (int p = 0; p < nparts; ++p)  // padding: the part's first column, zero coefficient
                 for (int k = fill[p]; k < lw[sl * nparts + p]; ++k)
-                    ci[loff[sl * nparts + p] + 32 * (int64_t)k + lane] = make_int2((int)(p * W), zero_idx);
+                    ci[loff[sl * nparts + p] + 32 * (int64_t)k + lane] = (uint32_t)zero_idx;
         }
     // beta strings and their energies in the layout's column order
     std::vector<uint64_t> hstr(lb), pstr(lb);
@@ -396,7 +404,7 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
     auto pl = std::make_unique<PartLayout>();
     pl->P = nparts;
     pl->W = W;
-    const size_t bytes = loff.size() * 12 + ci.size() * (sizeof(int2) + 12) + (size_t)lb * 28;
+    const size_t bytes = loff.size() * 12 + ci.size() * (sizeof(uint32_t) + 12) + (size_t)lb * 28;
     TB_TRY(charge(ctx, bytes, "column-part link layout"));
     cudaError_t e = pl->off.alloc(loff.size());
     if (e == cudaSuccess) e = pl->w.alloc(lw.size());
@@ -412,7 +420,7 @@ tbsci_status build_parts(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, int npar
         e = cudaMemcpy(pl->off.p, loff.data(), loff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !lw.empty())
         e = cudaMemcpy(pl->w.p, lw.data(), lw.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(pl->ci.p, ci.data(), ci.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->ci.p, ci.data(), ci.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->val.p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->valf.p, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pl->perm.p, perm.data(), lb * sizeof(int32_t), cudaMemcpyHostToDevice);
