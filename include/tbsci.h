@@ -196,7 +196,9 @@ void tbsci_hamiltonian_destroy(tbsci_ham *ham);
  * Hamiltonian values of every link, per-string energies, the beta Coulomb
  * table and the work schedules. Called implicitly by tbsci_sigma; exposed to
  * keep set-up out of timed regions. `a` and `b` must have double links and
- * the same norb as `ham`. Errors: EINVAL, ENOMEM, ECUDA. */
+ * the same norb as `ham`. Errors: EINVAL (also when the beta set is too large
+ * for the 32-bit packed links: l_beta above 2^(32 - s) with 2^s >= norb(norb+1)
+ * + 2, i.e. 2^22 strings at norb 24 and 2^19 at norb 64), ENOMEM, ECUDA. */
 tbsci_status tbsci_prepare(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b);
 
 /* sigma = H.c over the space a x b (Sec. II.B, Eq. 7, on one device; the six
