@@ -196,9 +196,7 @@ void tbsci_hamiltonian_destroy(tbsci_ham *ham);
  * Hamiltonian values of every link, per-string energies, the beta Coulomb
  * table and the work schedules. Called implicitly by tbsci_sigma; exposed to
  * keep set-up out of timed regions. `a` and `b` must have double links and
- * the same norb as `ham`. Errors: EINVAL (also when the beta set is too large
- * for the 32-bit packed links: l_beta above 2^(32 - s) with 2^s >= norb(norb+1)
- * + 2, i.e. 2^22 strings at norb 24 and 2^19 at norb 64), ENOMEM, ECUDA. */
+ * the same norb as `ham`. Errors: EINVAL, ENOMEM, ECUDA. */
 tbsci_status tbsci_prepare(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, const tbsci_tables *b);
 
 /* sigma = H.c over the space a x b (Sec. II.B, Eq. 7, on one device; the six
@@ -286,7 +284,13 @@ typedef struct tbsci_sigma_counts {
                                  the beta links (even l_alpha; else as 1), 4 the
                                  column-tiled products of the split path (beta
                                  classes on the transposed vector, alpha doubles on
-                                 c) */
+                                 c), 5 dense products on the tensor cores through
+                                 cuBLAS (off-diagonal same-spin Hamiltonians stored
+                                 dense, sides padded to multiples of 32: about
+                                 8 (l_a^2 + l_b^2) bytes for the TF32 type and
+                                 2 (l_a^2 + l_b^2) for BF16, plus 12 or 6 bytes
+                                 per determinant of scratch; split-TF32 or BF16
+                                 products with the type) */
 } tbsci_sigma_counts;
 tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a,
                                     const tbsci_tables *b, tbsci_sigma_counts *out);

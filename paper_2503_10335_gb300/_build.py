@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtbsci.so")
 SOURCES = ["api.cu", "strings_tables.cu", "plan.cu", "sigma.cu", "davidson.cu", "server.cu", "sigma_tc.cu",
-           "pruned.cu", "sigma_split.cu", "select.cu"]
+           "pruned.cu", "sigma_split.cu", "select.cu", "sigma_dense.cu"]
 HEADERS = [os.path.join(CSRC, "internal.cuh"), os.path.join(ROOT, "include", "tbsci.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcublas",
              "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
         os.replace(tmp, LIB)
     return LIB

@@ -166,6 +166,7 @@ void tbsci_destroy(tbsci_ctx *ctx) {
         cudaEventDestroy(r.end);
     }
     ctx->trace.clear();
+    dense_context_release(ctx);
     ctx->host_c.release();
     ctx->host_s.release();
     ctx->d_binom.release();
@@ -449,7 +450,7 @@ tbsci_status tbsci_tune_cache_load(tbsci_ctx *ctx, const char *path) {
                                   &e.nv[0], &e.stage[0], &e.threads[1], &e.nv[1], &e.stage[1], &e.rest_mode,
                                   &e.rest_threads);
         bool ok = n == 11 && k0 >= 1 && k0 <= 64 && k1 >= 0 && k2 >= 0 && threads_ok(e.rest_threads) &&
-                  e.rest_mode >= 0 && e.rest_mode <= 4;
+                  e.rest_mode >= 0 && e.rest_mode <= 5;
         for (int i = 0; i < 2 && ok; ++i)
             ok = threads_ok(e.threads[i]) && e.nv[i] >= 0 && e.nv[i] <= 4 && e.stage[i] >= 0 && e.stage[i] <= 6 &&
                  (e.stage[i] < 3 ? e.threads[i] != 1024 : (e.threads[i] == 0 || e.threads[i] >= 512));

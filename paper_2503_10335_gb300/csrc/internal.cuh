@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libtbsci.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -109,6 +110,9 @@ struct tbsci_ctx {
     };
     std::mutex tune_mu;
     std::map<std::array<int64_t, 3>, TuneEntry> tune_cache;
+    // cuBLAS handle of the dense same-spin products (rest mode 5), made on first use
+    void *cublas = nullptr;
+    std::mutex cublas_mu;
     // kernel trace (tbsci_trace_enable): while on, each sigma-path launch is
     // bracketed by two events recorded on its own stream; tbsci_trace_read
     // turns them into durations, oldest first
@@ -204,6 +208,15 @@ struct PartLayout {
     DevBuf<float> Ebf;
 };
 
+// Dense off-diagonal same-spin string Hamiltonians (rest mode 5): beta singles
+// + doubles and alpha doubles, each zero-padded to a multiple of 32 strings per
+// side; split-TF32 planes or BF16.
+struct DenseSameSpin {
+    DevBuf<float> a_hi, a_lo, b_hi, b_lo;
+    DevBuf<__nv_bfloat16> a_bf, b_bf;
+    DevBuf<unsigned char> scratch;  // padded split vector and product
+};
+
 struct Plan {
     uint64_t ida = 0, idb = 0;
     int norb = 0, npair = 0;
@@ -217,10 +230,7 @@ struct Plan {
     // slice's longest list with zero-coefficient entries (coalesced warp loads).
     DevBuf<int64_t> d_s1_off, d_s2_off, d_d2_off;
     DevBuf<int32_t> d_s1_w, d_s2_w, d_d2_w;
-    // singles, one 32-bit word each: target << link_shift | (2*pair + neg); s1: permb
-    // order, s2: permb2 order. link_shift bits hold the coefficient index.
-    DevBuf<uint32_t> d_s1_ci, d_s2_ci;
-    int link_shift = 0;
+    DevBuf<int2> d_s1_ci, d_s2_ci;       // singles {target, 2*pair + neg}; s1: permb order, s2: permb2 order
     DevBuf<double> d_s2_val, d_d2_val;   // string-Hamiltonian values (permb2 order)
     DevBuf<float> d_s2_valf, d_d2_valf;
     DevBuf<int32_t> d_d2_col;            // doubles target (permb2 order)
@@ -247,6 +257,7 @@ struct Plan {
     DevBuf<int64_t> d_bss_off;
     DevBuf<int32_t> d_bss_col;
     DevBuf<float> d_bss_valf;
+    DenseSameSpin dense;
     tbsci_sigma_counts counts{};
     size_t charged = 0;  // device bytes counted against the context's budget
 };
@@ -325,7 +336,7 @@ tbsci_status sigma_autotune(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, co
                             tbsci_dtype dt, cudaStream_t st, double *best_ms);
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
                                int nvec, cudaStream_t st, int mode = -1, int threads = 0,
-                               const int32_t *rows = nullptr, int64_t nrows = 0);
+                               const int32_t *rows = nullptr, int64_t nrows = 0, bool bf16 = false);
 // sigma_split.cu: sigma for rows longer than shared memory (column parts + the
 // same-spin double classes as column-tiled products); see the file head
 // smallest number of column parts of a c row that fits in shared memory beside
@@ -341,6 +352,12 @@ tbsci_status split_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const T
 // vector, alpha on c; overwrites s (rest mode 4).
 tbsci_status rest_products_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const float *c, float *s, int nvec,
                                   cudaStream_t st);
+// sigma_dense.cu: the same classes as dense products on the tensor cores (cuBLAS;
+// split TF32, or BF16 when bf16); overwrites s (rest mode 5). The context's
+// cuBLAS handle is released by dense_context_release.
+tbsci_status rest_dense_launch(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *P, const float *c, float *s, int nvec,
+                               bool bf16, cudaStream_t st);
+void dense_context_release(tbsci_ctx *ctx);
 // sigma_tc.cu: the diagonal, alpha singles and all alpha-beta classes on the
 // tensor cores (3xTF32 or BF16 products, FP32 accumulation), added into s.
 tbsci_status sigma_tc_add(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s, int nvec,

@@ -94,7 +94,7 @@ __global__ void k_coulomb_table(const uint64_t *__restrict__ strb, int64_t lb, i
 __global__ void k_sell_singles(const int32_t *__restrict__ perm, int64_t lb, const int64_t *__restrict__ off,
                                const int2 *__restrict__ sci, const double *__restrict__ sval,
                                const int64_t *__restrict__ soff, const int32_t *__restrict__ sw, int64_t nsl,
-                               int zero_idx, int shift, uint32_t *out_ci, double *out_val, float *out_valf) {
+                               int zero_idx, int2 *out_ci, double *out_val, float *out_valf) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nsl * 32) return;
     const int64_t sl = t >> 5, j = t;
@@ -106,14 +106,13 @@ __global__ void k_sell_singles(const int32_t *__restrict__ perm, int64_t lb, con
     for (int k = 0; k < w; ++k) {
         const int64_t pos = base + 32 * (int64_t)k;
         if (k < cnt) {
-            const int2 e = sci[a + k];
-            out_ci[pos] = ((uint32_t)e.x << shift) | (uint32_t)e.y;
+            out_ci[pos] = sci[a + k];
             if (out_val) {
                 out_val[pos] = sval[a + k];
                 out_valf[pos] = (float)sval[a + k];
             }
         } else {
-            out_ci[pos] = ((uint32_t)ib << shift) | (uint32_t)zero_idx;
+            out_ci[pos] = make_int2((int)ib, zero_idx);
             if (out_val) {
                 out_val[pos] = 0.0;
                 out_valf[pos] = 0.f;
@@ -320,13 +319,6 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
         int64_t tot = 0;
         const unsigned g = (unsigned)std::max<int64_t>(1, (nsl * 32 + 255) / 256);
         const int zero_idx = 2 * ham->npair;
-        // packed links: the coefficient index (2 pair + sign, or the zero entry)
-        // in the low link_shift bits, the target column above it
-        int shift = 1;
-        while ((1 << shift) < zero_idx + 2) ++shift;
-        TB_CHECK(ctx, shift < 32 && lb <= (int64_t(1) << (32 - shift)), TBSCI_EINVAL,
-                 "prepare: too many beta strings for 32-bit packed links at this orbital count");
-        plan->link_shift = shift;
         // singles in permb order
         sell_shape(permb, b->h_off1, so, sw, tot);
         TB_CUDA(ctx, plan->d_s1_off.alloc(nsl));
@@ -336,7 +328,7 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
             TB_CUDA(ctx, cudaMemcpy(plan->d_s1_off.p, so.data(), nsl * sizeof(int64_t), cudaMemcpyHostToDevice));
             TB_CUDA(ctx, cudaMemcpy(plan->d_s1_w.p, sw.data(), nsl * sizeof(int32_t), cudaMemcpyHostToDevice));
             k_sell_singles<<<g, 256, 0, st>>>(plan->d_permb.p, lb, b->d_off1.p, plan->B.d_sci.p, nullptr,
-                                              plan->d_s1_off.p, plan->d_s1_w.p, nsl, zero_idx, shift, plan->d_s1_ci.p,
+                                              plan->d_s1_off.p, plan->d_s1_w.p, nsl, zero_idx, plan->d_s1_ci.p,
                                               nullptr, nullptr);
             TB_CUDA(ctx, cudaGetLastError());
         }
@@ -351,7 +343,7 @@ tbsci_status plan_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_tables *a, con
             TB_CUDA(ctx, cudaMemcpy(plan->d_s2_off.p, so.data(), nsl * sizeof(int64_t), cudaMemcpyHostToDevice));
             TB_CUDA(ctx, cudaMemcpy(plan->d_s2_w.p, sw.data(), nsl * sizeof(int32_t), cudaMemcpyHostToDevice));
             k_sell_singles<<<g, 256, 0, st>>>(plan->d_permb2.p, lb, b->d_off1.p, plan->B.d_sci.p, plan->B.d_sval.p,
-                                              plan->d_s2_off.p, plan->d_s2_w.p, nsl, zero_idx, shift, plan->d_s2_ci.p,
+                                              plan->d_s2_off.p, plan->d_s2_w.p, nsl, zero_idx, plan->d_s2_ci.p,
                                               plan->d_s2_val.p, plan->d_s2_valf.p);
             TB_CUDA(ctx, cudaGetLastError());
         }

@@ -57,8 +57,7 @@ struct SigArgs {
     // values and doubles in permb2 order; tables with columns in those orders
     const int64_t *s1_off, *s2_off, *d2_off;
     const int32_t *s1_w, *s2_w, *d2_w;
-    const uint32_t *s1_ci, *s2_ci;  // packed: target << lsh | coefficient index
-    int lsh;
+    const int2 *s1_ci, *s2_ci;
     const T *s2_val, *d2_val;
     const int32_t *d2_col;
     const T *U1, *U2, *Eb2;
@@ -74,8 +73,6 @@ template <typename T, int NV, bool STAGE, bool ACCS, int kThreads, bool REST = f
 __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia, unsigned char *smem_raw) {
     const int npair = A.npair;
     const int64_t lb = A.lb, vs = A.vstride;
-    const int lsh = A.lsh;
-    const uint32_t lmask = (1u << lsh) - 1u;
     T *sV2 = reinterpret_cast<T *>(smem_raw);  // [2*npair + 2], last two entries zero (padding)
     int *sOcc = reinterpret_cast<int *>(sV2 + 2 * npair + 2);
     T *sC = reinterpret_cast<T *>(smem_raw + (((2 * npair + 2) * sizeof(T) + 64 * sizeof(int) + 15) & ~size_t(15)));
@@ -136,25 +133,25 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
             acc2[v] = T(0);
         }
         {
-            const uint32_t *ci = A.s2_ci + A.s2_off[sl] + lane;
+            const int2 *ci = A.s2_ci + A.s2_off[sl] + lane;
             const T *cv = A.s2_val + A.s2_off[sl] + lane;
             const int w = A.s2_w[sl];
             int k = 0;
             for (; k + 1 < w; k += 2) {
-                const uint32_t e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
-                const T x0 = __ldg(cv + 32 * k) + sV2[e0 & lmask];
-                const T x1 = __ldg(cv + 32 * (k + 1)) + sV2[e1 & lmask];
+                const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                const T x0 = __ldg(cv + 32 * k) + sV2[e0.y];
+                const T x1 = __ldg(cv + 32 * (k + 1)) + sV2[e1.y];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    acc[v] += x0 * cval(v, Ia, e0 >> lsh);
-                    acc2[v] += x1 * cval(v, Ia, e1 >> lsh);
+                    acc[v] += x0 * cval(v, Ia, e0.x);
+                    acc2[v] += x1 * cval(v, Ia, e1.x);
                 }
             }
             if (k < w) {
-                const uint32_t e = __ldg(ci + 32 * k);
-                const T x = __ldg(cv + 32 * k) + sV2[e & lmask];
+                const int2 e = __ldg(ci + 32 * k);
+                const T x = __ldg(cv + 32 * k) + sV2[e.y];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, e >> lsh);
+                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ia, e.x);
             }
         }
         {
@@ -210,23 +207,23 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
                 acc[v] = acc_ref(v, ib) + coef * cval(v, Ja, ib);
                 acc2[v] = T(0);
             }
-            const uint32_t *ci = A.s1_ci + A.s1_off[sl] + lane;
+            const int2 *ci = A.s1_ci + A.s1_off[sl] + lane;
             const int w = A.s1_w[sl];
             int k = 0;
             for (; k + 1 < w; k += 2) {
-                const uint32_t e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
-                const T x0 = sV2[e0 & lmask], x1 = sV2[e1 & lmask];
+                const int2 e0 = __ldg(ci + 32 * k), e1 = __ldg(ci + 32 * (k + 1));
+                const T x0 = sV2[e0.y], x1 = sV2[e1.y];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    acc[v] += x0 * cval(v, Ja, e0 >> lsh);
-                    acc2[v] += x1 * cval(v, Ja, e1 >> lsh);
+                    acc[v] += x0 * cval(v, Ja, e0.x);
+                    acc2[v] += x1 * cval(v, Ja, e1.x);
                 }
             }
             if (k < w) {
-                const uint32_t e = __ldg(ci + 32 * k);
-                const T x = sV2[e & lmask];
+                const int2 e = __ldg(ci + 32 * k);
+                const T x = sV2[e.y];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ja, e >> lsh);
+                for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ja, e.x);
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v] + acc2[v];
@@ -370,7 +367,6 @@ void set_sell(SigArgs<T> &A, const Plan *P) {
     A.d2_w = P->d_d2_w.p;
     A.s1_ci = P->d_s1_ci.p;
     A.s2_ci = P->d_s2_ci.p;
-    A.lsh = P->link_shift;
     A.d2_col = P->d_d2_col.p;
 }
 
@@ -742,7 +738,8 @@ tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, con
         return TBSCI_OK;
     };
     float probe = 0.f;
-    tbsci_status ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, 0, 0); }, 1, &probe);
+    tbsci_status ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, 0, 0, nullptr, 0,
+                                                            dt == TBSCI_F32_TC_BF16); }, 1, &probe);
     // a strided sample of the work-ordered rows (and of the row pairs, for the
     // pair variants: the same number of rows)
     DevBuf<int32_t> dsample, dpsample;
@@ -770,18 +767,25 @@ tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, con
     const int threads[3] = {128, 256, 512};
     float best = 1e30f;
     int bm = 0, bt = 0;
-    bool seen[7] = {false, false, false, false, false, false, false};
-    // mode 4 (column-tiled products) runs on the whole space; its time counts in
-    // proportion to the sample when the others are timed on one
-    if (ret == TBSCI_OK) {
+    bool seen[8] = {false, false, false, false, false, false, false, false};
+    const bool bf16 = dt == TBSCI_F32_TC_BF16;
+    // modes 4 (column-tiled products) and 5 (dense products) run on the whole
+    // space; their time counts in proportion to the sample when the others are
+    // timed on one. Mode 5 is skipped when its dense matrices do not fit the
+    // context's budget or the device (the failed set-up leaves the plan as it was).
+    for (int mode = 4; mode <= 5 && ret == TBSCI_OK; ++mode) {
         float ms = 0.f;
-        ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, 4, 256); }, 1, &ms);
-        if (ret == TBSCI_OK) {
-            best = rows ? ms * (float)nrows / (float)la : ms;
-            bm = 4;
+        tbsci_status r5 = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, mode, 256, nullptr, 0,
+                                                               bf16); }, 1, &ms);
+        if (mode == 5 && r5 == TBSCI_ENOMEM) continue;
+        ret = r5;
+        const float scaled = rows ? ms * (float)nrows / (float)la : ms;
+        if (ret == TBSCI_OK && scaled < best) {
+            best = scaled;
+            bm = mode;
             bt = 256;
-            seen[6] = true;
         }
+        seen[mode == 4 ? 6 : 7] = true;
     }
     for (int mode = 0; mode < 4 && ret == TBSCI_OK; ++mode) {
         const int var = rest_variant(ctx, npair, lb, mode, pairs);
@@ -791,7 +795,7 @@ tbsci_status autotune_rest(tbsci_ctx *ctx, const tbsci_ham *ham, Plan *plan, con
         const int64_t nr = var >= 4 ? nprows : nrows;
         for (int t = 0; t < 3 && ret == TBSCI_OK; ++t) {
             float ms = 0.f;
-            ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, mode, threads[t], r, nr); },
+            ret = timed([&] { return sigma_launch_rest(ctx, ham, plan, c, s, nvec, st, mode, threads[t], r, nr, bf16); },
                         rows ? 1 : 2, &ms);
             if (ret == TBSCI_OK && ms < best) {
                 best = ms;
@@ -1023,6 +1027,7 @@ tbsci_status launch_rest_v(tbsci_ctx *ctx, const SigArgs<float> &A, cudaStream_t
 int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode, bool pairs) {
     const size_t lim = ctx->smem_optin;
     if (mode == 4) return 6;  // column-tiled products (rest_products_launch)
+    if (mode == 5) return 7;  // dense products on the tensor cores (rest_dense_launch)
     if (mode == 3 && pairs) return smem_bytes<float>(npair, lb, 2, true, false) <= lim ? 4 : 5;
     if (mode == 3) mode = 1;
     if (mode == 0) {
@@ -1042,7 +1047,8 @@ int rest_variant(const tbsci_ctx *ctx, int npair, int64_t lb, int mode, bool pai
 // columns, else 128); rows / nrows: launch only these alpha rows (tuning sample;
 // for the row-pair variants: these even pair starts).
 tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan, const float *c, float *s,
-                               int nvec, cudaStream_t st, int mode, int threads, const int32_t *rows, int64_t nrows) {
+                               int nvec, cudaStream_t st, int mode, int threads, const int32_t *rows, int64_t nrows,
+                               bool bf16) {
     SigArgs<float> A = make_args<float>(ham, plan);
     if (A.la == 0 || A.lb == 0) return TBSCI_OK;
     if (mode < 0) {
@@ -1052,6 +1058,7 @@ tbsci_status sigma_launch_rest(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan 
     if (threads == 0) threads = A.lb >= 1024 ? 512 : 128;
     const int var = rest_variant(ctx, A.npair, A.lb, mode, plan->d_pairs.p != nullptr);
     if (var == 6) return rest_products_launch(ctx, ham, const_cast<Plan *>(plan), c, s, nvec, st);
+    if (var == 7) return rest_dense_launch(ctx, ham, const_cast<Plan *>(plan), c, s, nvec, bf16, st);
     if (var >= 4) {
         // row pairs: one vector per launch with vstride = l_beta, pair starts as rows
         SigArgs<float> P = A;
@@ -1094,7 +1101,7 @@ tbsci_status sigma_launch(tbsci_ctx *ctx, const tbsci_ham *ham, const Plan *plan
         float *sf = static_cast<float *>(s);
         if (plan->npoff > 128 || !plan->d_lbp.p)  // no tensor-core tile for this norb: FP32 on the SIMT path
             return launch_typed<float>(ctx, ham, plan, cf, sf, nvec, st);
-        TB_TRY(sigma_launch_rest(ctx, ham, plan, cf, sf, nvec, st));
+        TB_TRY(sigma_launch_rest(ctx, ham, plan, cf, sf, nvec, st, -1, 0, nullptr, 0, dt == TBSCI_F32_TC_BF16));
         return sigma_tc_add(ctx, ham, plan, cf, sf, nvec, dt == TBSCI_F32_TC_BF16, st);
     }
     return fail(ctx, TBSCI_EINVAL, "unknown dtype");

@@ -1,6 +1,7 @@
 """Tensor-core sigma modes (tcgen05, row a6): the alpha-beta classes, alpha
 singles and diagonal from split-TF32 (3 products per term) or BF16 products
-with FP32 accumulation, the other classes on the FP32 SIMT path. Compared with
+with FP32 accumulation, the other classes on the FP32 SIMT path or as dense
+products on the tensor cores (rest mode 5). Compared with
 the oracle applied to the FP32-rounded vector: split TF32 within FP32-level
 accumulation error, BF16 within its 8-bit-mantissa error."""
 import os
@@ -104,7 +105,7 @@ def test_tc_sigma_parity_after_autotune(tb, ctx, mode, n, na, nb, acnt, bcnt):
     ms = tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, Ct, out, 1, dt)
     assert ms > 0
     cnt = sp.counts()
-    assert cnt["tuned_rest"][0] in (0, 1, 2, 3, 4) and cnt["tuned_rest"][1] in (128, 256, 512)
+    assert cnt["tuned_rest"][0] in (0, 1, 2, 3, 4, 5) and cnt["tuned_rest"][1] in (128, 256, 512)
     ref, bound = oracle.sigma(osp, h, eri, 0.2, C.astype(np.float64), with_bound=True)
     rel, norm_rel = TOL[mode]
     for s in (out, sp.sigma(Ct, dtype=dt)):
@@ -136,6 +137,39 @@ def test_tc_sigma_rest_modes_from_tune_cache(tb, n, na, nb, acnt, bcnt, rest_mod
     ref, bound = oracle.sigma(osp, h, eri, 0.2, C.astype(np.float64), with_bound=True)
     rel, norm_rel = TOL["tf32"]
     assert_sigma_close(s, ref, bound, rel=rel, norm_rel=norm_rel)
+    sp.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("n,na,nb,acnt,bcnt", [(10, 5, 5, 120, 257), (12, 4, 6, None, 200), (16, 8, 8, 700, 650)])
+def test_tc_sigma_dense_same_spin(tb, n, na, nb, acnt, bcnt, mode, tmp_path):
+    """Rest mode 5: the same-spin classes as dense products on the tensor cores
+    (split TF32 for the TF32 type, one BF16 product for the BF16 type), pinned
+    through a tune cache; two vectors against the oracle at the type's
+    tolerance, twice."""
+    import torch
+    h, eri, _ = synth_hamiltonian(n, seed=300 + n)
+    asel = None if acnt is None else selected_strings(n, na, acnt, 31 + n)
+    bsel = None if bcnt is None else selected_strings(n, nb, bcnt, 37 + n)
+    osp = oracle.make_space(n, na, nb, asel, bsel)
+    path = tmp_path / "tune.txt"
+    path.write_text("tbsci-tune 1\n%d %d %d 0 0 0 0 0 0 5 256\n" % (n, osp.la, osp.lb))
+    ctx = tb.Context(0)
+    tb.tbsci_tune_cache_load(ctx.handle, str(path))
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.2, alpha=asel, beta=bsel)
+    assert sp.counts()["tuned_rest"] == [5, 256]
+    dt = tb.TBSCI_F32_TC_TF32 if mode == "tf32" else tb.TBSCI_F32_TC_BF16
+    C = random_vectors(2, sp.la, sp.lb, seed=n + 3).astype(np.float32)
+    Ct = torch.from_numpy(C).cuda()
+    s = sp.sigma(Ct, dtype=dt).double().cpu().numpy().reshape(2, -1)
+    ref, bound = oracle.sigma(osp, h, eri, 0.2, C.astype(np.float64), with_bound=True)
+    rel, norm_rel = TOL[mode]
+    assert_sigma_close(s, ref, bound, rel=rel, norm_rel=norm_rel)
+    # the tensor-core kernel's scatter sums with shared-memory atomics, so a second
+    # evaluation agrees to rounding, not bit for bit
+    assert_sigma_close(sp.sigma(Ct, dtype=dt).double().cpu().numpy().reshape(2, -1), ref, bound, rel=rel,
+                       norm_rel=norm_rel)
     sp.close()
     ctx.close()
 
