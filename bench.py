@@ -74,6 +74,9 @@ NCU_TRAFFIC = {
                    (256, 1, 0): 1.356e9, (128, 1, 0): 0.803e9,
                    (512, 1, 1): 1.233e9, (256, 1, 1): 0.811e9, (128, 1, 1): 1.558e9,
                    (512, 1, 2): 2.049e9, (256, 1, 2): 1.496e9, (128, 1, 2): 3.683e9}},
+    ("sel24", "f64", "k_sigma_parts"): {
+        "source": "sigma_split.cu", "sha1": "bbca57e694e9aafe0b9476961be6286e724c7b3a",
+        "shapes": {(1024, 3): 380.95e9}},
 }
 
 
