@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace tbsci {
@@ -96,16 +98,19 @@ __global__ void k_reduce_partials(const double *partial, int nblocks, int ldp, i
 constexpr int kMaxBasis = 128;
 constexpr int kMaxOut = 8;
 
-// out[k][K] = beta * out[k][K] + yscale * sum_i Y[i][k] * A[i][K], k < kout <= KOUT,
+// out[k][K] = beta * out[k][K] + yscale * sum_i Y[i][k] * A[i][K], k < KOUT,
 // accumulated in FP64 and stored as TO. Each thread handles U elements spaced
 // blockDim apart per step and reads two rows per unrolled pass (2U loads in
 // flight); the accumulator tile KOUT x U stays small enough for 4 CTAs per SM.
+// KOUT is the exact output count: a guarded output slot would still occupy the
+// FP64 pipe with predicated-off multiply-adds.
 template <typename TA, typename TO, int KOUT>
-__global__ void __launch_bounds__(256) k_lincomb(const TA *__restrict__ A, int m, TO *out, int kout, int64_t N,
-                                                 double beta, const double *__restrict__ Y, double yscale,
+__global__ void __launch_bounds__(256) k_lincomb(const TA *__restrict__ A, int m, TO *out, int64_t N, double beta,
+                                                 const double *__restrict__ Y, double yscale,
                                                  const int *__restrict__ skip) {
     if (skip && *skip) return;
-    constexpr int U = KOUT >= 4 ? 2 : 4;
+    constexpr int U = KOUT >= 3 ? 2 : 4;
+    constexpr int kout = KOUT;
     __shared__ double sY[kMaxBasis * KOUT];
     for (int x = threadIdx.x; x < m * kout; x += blockDim.x) sY[x] = yscale * Y[x];
     __syncthreads();
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(256) k_lincomb(const TA *__restrict__ A, int m
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int64_t K = K0 + (int64_t)u * blockDim.x;
-                acc[k][u] = (k < kout && beta != 0.0 && K < N) ? beta * (double)out[(size_t)k * N + K] : 0.0;
+                acc[k][u] = (beta != 0.0 && K < N) ? beta * (double)out[(size_t)k * N + K] : 0.0;
             }
 #pragma unroll 2
         for (int i = 0; i < m; ++i) {
@@ -128,31 +133,35 @@ __global__ void __launch_bounds__(256) k_lincomb(const TA *__restrict__ A, int m
                 a[u] = K < N ? (double)__ldg(A + (size_t)i * N + K) : 0.0;
             }
 #pragma unroll
-            for (int k = 0; k < KOUT; ++k)
-                if (k < kout) {
-                    const double y = sY[i * kout + k];
+            for (int k = 0; k < KOUT; ++k) {
+                const double y = sY[i * kout + k];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) acc[k][u] = fma(y, a[u], acc[k][u]);
-                }
+                for (int u = 0; u < U; ++u) acc[k][u] = fma(y, a[u], acc[k][u]);
+            }
         }
 #pragma unroll
         for (int k = 0; k < KOUT; ++k)
-            if (k < kout)
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t K = K0 + (int64_t)u * blockDim.x;
-                    if (K < N) out[(size_t)k * N + K] = (TO)acc[k][u];
-                }
+            for (int u = 0; u < U; ++u) {
+                const int64_t K = K0 + (int64_t)u * blockDim.x;
+                if (K < N) out[(size_t)k * N + K] = (TO)acc[k][u];
+            }
     }
 }
 
 template <typename TA, typename TO>
 void launch_lincomb(int grid, cudaStream_t st, const TA *A, int m, TO *out, int kout, int64_t N, double beta,
                     const double *Y, double yscale, const int *skip = nullptr) {
-    if (kout <= 1) k_lincomb<TA, TO, 1><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
-    else if (kout <= 2) k_lincomb<TA, TO, 2><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
-    else if (kout <= 4) k_lincomb<TA, TO, 4><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
-    else k_lincomb<TA, TO, 8><<<grid, 256, 0, st>>>(A, m, out, kout, N, beta, Y, yscale, skip);
+    switch (kout) {  // kout is 1..kMaxOut (callers split larger sets)
+        case 1: k_lincomb<TA, TO, 1><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+        case 2: k_lincomb<TA, TO, 2><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+        case 3: k_lincomb<TA, TO, 3><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+        case 4: k_lincomb<TA, TO, 4><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+        case 5: k_lincomb<TA, TO, 5><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+        case 6: k_lincomb<TA, TO, 6><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+        case 7: k_lincomb<TA, TO, 7><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+        default: k_lincomb<TA, TO, 8><<<grid, 256, 0, st>>>(A, m, out, N, beta, Y, yscale, skip); break;
+    }
 }
 
 // Second Gram-Schmidt pass needed? "Twice is enough" (Daniel-Gragg-Kaufman-
@@ -444,22 +453,24 @@ struct DavEngine {
     // device flag that, when set, turns the product into no work
     tbsci_status dots(const void *A, int ma, const void *B, int mb, double *out, const int *skip = nullptr) {
         const int ldp = ma * mb;
-        if (mb == 1) {  // one column (Rayleigh columns, projections of one vector, norms)
-            dim3 grid(nblocks, (ma + kMA - 1) / kMA, 1);
+        // columns of B per block: mb itself up to kMB (no guarded column costs
+        // FP64 work), else kMB with a partial last block
+        const int mbb = std::min(mb, kMB);
+        const dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + mbb - 1) / mbb);
+        auto go = [&](auto mb_tag) {
+            constexpr int MB = decltype(mb_tag)::value;
             if (b32)
-                k_dots<float, 1><<<grid, kDotThreads, 0, st>>>((const float *)A, ma, (const float *)B, mb, N,
-                                                               partial.p, ldp, skip);
-            else
-                k_dots<double, 1><<<grid, kDotThreads, 0, st>>>((const double *)A, ma, (const double *)B, mb, N,
+                k_dots<float, MB><<<grid, kDotThreads, 0, st>>>((const float *)A, ma, (const float *)B, mb, N,
                                                                 partial.p, ldp, skip);
-        } else {
-            dim3 grid(nblocks, (ma + kMA - 1) / kMA, (mb + kMB - 1) / kMB);
-            if (b32)
-                k_dots<float><<<grid, kDotThreads, 0, st>>>((const float *)A, ma, (const float *)B, mb, N, partial.p,
-                                                            ldp, skip);
             else
-                k_dots<double><<<grid, kDotThreads, 0, st>>>((const double *)A, ma, (const double *)B, mb, N,
-                                                             partial.p, ldp, skip);
+                k_dots<double, MB><<<grid, kDotThreads, 0, st>>>((const double *)A, ma, (const double *)B, mb, N,
+                                                                 partial.p, ldp, skip);
+        };
+        switch (mbb) {
+            case 1: go(std::integral_constant<int, 1>{}); break;
+            case 2: go(std::integral_constant<int, 2>{}); break;
+            case 3: go(std::integral_constant<int, 3>{}); break;
+            default: go(std::integral_constant<int, 4>{}); break;
         }
         TB_CUDA(ctx, cudaGetLastError());
         k_reduce_partials<<<(ldp + 127) / 128, 128, 0, st>>>(partial.p, nblocks, ldp, ldp, out);
