@@ -174,6 +174,46 @@ def test_tc_sigma_dense_same_spin(tb, n, na, nb, acnt, bcnt, mode, tmp_path):
     ctx.close()
 
 
+def test_tc_dense_mode_respects_the_budget(tb, tmp_path):
+    """Under a device-memory budget that holds the space and the column-tiled
+    products but not the dense same-spin matrices, tuning a tensor-core type
+    skips rest mode 5 (its set-up is refused with ENOMEM and leaves nothing
+    counted) and sigma still matches the oracle."""
+    import torch
+    n, na, nb, acnt, bcnt = 16, 8, 8, 700, 650
+    h, eri, _ = synth_hamiltonian(n, seed=300 + n)
+    asel, bsel = selected_strings(n, na, acnt, 31 + n), selected_strings(n, nb, bcnt, 37 + n)
+    osp = oracle.make_space(n, na, nb, asel, bsel)
+    C = random_vectors(1, osp.la, osp.lb, seed=5).astype(np.float32)
+    path = tmp_path / "tune.txt"
+    path.write_text("tbsci-tune 1\n%d %d %d 0 0 0 0 0 0 4 256\n" % (n, osp.la, osp.lb))
+    # bytes the space needs with the column-tiled products (measured without a budget)
+    free = tb.Context(0)
+    tb.tbsci_tune_cache_load(free.handle, str(path))
+    sp = tb.Space(free, n, na, nb, h, eri, 0.2, alpha=asel, beta=bsel)
+    sp.sigma(torch.from_numpy(C).cuda(), dtype=tb.TBSCI_F32_TC_TF32)
+    need = tb.tbsci_hbm_used(free.handle)
+    sp.close()
+    free.close()
+    dense = 8 * ((osp.la + 31) // 32 * 32) ** 2  # the alpha matrix alone, split-TF32 planes
+    ctx = tb.Context(0, hbm_budget=need + dense // 2)
+    tb.tbsci_tune_cache_load(ctx.handle, str(path))
+    sp = tb.Space(ctx, n, na, nb, h, eri, 0.2, alpha=asel, beta=bsel)
+    Ct = torch.from_numpy(C).cuda()
+    out = torch.empty_like(Ct)
+    sp.sigma(Ct, out, dtype=tb.TBSCI_F32_TC_TF32)
+    before = tb.tbsci_hbm_used(ctx.handle)
+    assert tb.tbsci_sigma_autotune(ctx.handle, sp.ham, sp.ta, sp.tb, Ct, out, 1, tb.TBSCI_F32_TC_TF32) > 0
+    assert sp.counts()["tuned_rest"][0] != 5
+    assert tb.tbsci_hbm_used(ctx.handle) == before
+    ref, bound = oracle.sigma(osp, h, eri, 0.2, C.astype(np.float64), with_bound=True)
+    rel, norm_rel = TOL["tf32"]
+    s = sp.sigma(Ct, dtype=tb.TBSCI_F32_TC_TF32).double().cpu().numpy().reshape(1, -1)
+    assert_sigma_close(s, ref, bound, rel=rel, norm_rel=norm_rel)
+    sp.close()
+    ctx.close()
+
+
 @pytest.mark.parametrize("mode", ["tf32", "bf16"])
 def test_tc_sigma_fci16_sampled_tuned(tb, ctx, mode):
     """norb=16 full string space (12,870^2 = 165.6M determinants), 1 vector, in the
