@@ -210,14 +210,12 @@ __global__ void __launch_bounds__(kDotThreads) k_residual(const double *__restri
             if (K >= N) break;
             const double d = diag[K];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                if (k < nroots) {
-                    const double r = WY[(size_t)k * N + K] - theta[k] * X[(size_t)k * N + K];
-                    acc[k] = fma(r, r, acc[k]);
-                    double den = theta[k] - d;
-                    if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
-                    T[(size_t)k * N + K] = r / den;
-                }
+            for (int k = 0; k < NR; ++k) {  // NR == nroots: no guarded FP64 slots
+                const double r = WY[(size_t)k * N + K] - theta[k] * X[(size_t)k * N + K];
+                acc[k] = fma(r, r, acc[k]);
+                double den = theta[k] - d;
+                if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
+                T[(size_t)k * N + K] = r / den;
             }
         }
     }
@@ -711,8 +709,17 @@ struct DavEngine {
         TB_CUDA(ctx, cudaMemcpyAsync(dtheta.p, hR, nroots * sizeof(double), cudaMemcpyHostToDevice, st));
         TB_TRY(ritz(vs(0), m, X.p, nroots, dY.p));
         TB_TRY(ritz(ws(0), m, WY.p, nroots, dY.p));
-        auto resid = nroots <= 1 ? k_residual<1> : nroots <= 2 ? k_residual<2> : nroots <= 4 ? k_residual<4>
-                                                                                              : k_residual<8>;
+        decltype(&k_residual<1>) resid = nullptr;
+        switch (nroots) {
+            case 1: resid = k_residual<1>; break;
+            case 2: resid = k_residual<2>; break;
+            case 3: resid = k_residual<3>; break;
+            case 4: resid = k_residual<4>; break;
+            case 5: resid = k_residual<5>; break;
+            case 6: resid = k_residual<6>; break;
+            case 7: resid = k_residual<7>; break;
+            default: resid = k_residual<8>; break;
+        }
         resid<<<rgrid, kDotThreads, 0, st>>>(X.p, WY.p, diag.p, dtheta.p, nroots, N, T.p, partial.p);
         TB_CUDA(ctx, cudaGetLastError());
         k_reduce_partials<<<1, 32, 0, st>>>(partial.p, rgrid, kMaxOut, nroots, red.p);
