@@ -192,6 +192,16 @@ __global__ void k_set_guess(T *V, int64_t N, const int64_t *idx, const double *M
     V[(size_t)r * N + idx[j]] = (T)M[t];
 }
 
+// 1/x for the diagonal preconditioner: an FP32 reciprocal as the seed, then one
+// Newton-Raphson step y' = y (2 - x y) in FP64, which doubles the seed's ~23
+// correct bits. |x| is clamped to [1e-8, ~1e3] by the caller, inside FP32's range.
+// The preconditioned residual only sets a search direction, so ~1e-13 relative
+// accuracy is ample, and it costs a fraction of a full FP64 division per element.
+__device__ __forceinline__ double precond_recip(double x) {
+    const double y = (double)(1.0f / (float)x);
+    return y * fma(-x, y, 2.0);
+}
+
 // r = wy - theta x; t = r / clamp(theta - diag); partial norms of r (nroots <= NR)
 template <int NR>
 __global__ void __launch_bounds__(kDotThreads) k_residual(const double *__restrict__ X, const double *__restrict__ WY,
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(kDotThreads) k_residual(const double *__restri
                 acc[k] = fma(r, r, acc[k]);
                 double den = theta[k] - d;
                 if (fabs(den) < 1e-8) den = den < 0.0 ? -1e-8 : 1e-8;
-                T[(size_t)k * N + K] = r / den;
+                T[(size_t)k * N + K] = r * precond_recip(den);
             }
         }
     }
