@@ -216,7 +216,10 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     acc[v] += x0 * cval(v, Ja, e0.x);
-                    acc2[v] += x1 * cval(v, Ja, e1.x);
+                    // FP64: one chain (the FP64 pipe, not the add latency, is the
+                    // limit; the merge below would cost an add per column and term)
+                    if constexpr (sizeof(T) == 8) acc[v] += x1 * cval(v, Ja, e1.x);
+                    else acc2[v] += x1 * cval(v, Ja, e1.x);
                 }
             }
             if (k < w) {
@@ -226,7 +229,10 @@ __device__ __forceinline__ void sigma_row(const SigArgs<T> &A, const int64_t Ia,
                 for (int v = 0; v < NV; ++v) acc[v] += x * cval(v, Ja, e.x);
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc_ref(v, ib) = acc[v] + acc2[v];
+            for (int v = 0; v < NV; ++v) {
+                if constexpr (sizeof(T) == 8) acc_ref(v, ib) = acc[v];
+                else acc_ref(v, ib) = acc[v] + acc2[v];
+            }
         }
     }
     __syncthreads();
