@@ -122,7 +122,9 @@ const char *tbsci_status_string(tbsci_status st);
 
 /* Kernel trace: the device time of each launch of the sigma path (the fused
  * row kernel, the split path's row kernel, double-class products, transposes
- * and combine, the tensor-core kernel and its SIMT pass, the pruned kernel).
+ * and combine, the tensor-core kernel and its SIMT pass, the dense same-spin
+ * products of rest mode 5 (one entry for the cuBLAS calls of a vector, plus
+ * the split and unpad passes), the pruned kernel).
  * While tracing is on, every such launch made through this context is
  * bracketed by two CUDA events recorded on its own stream (launches made while
  * that stream is being captured into a graph are not traced). The trace keeps
