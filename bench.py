@@ -69,11 +69,8 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 128 FP32 lanes/SM/clk, FM
 # shared-memory mode); k_sigma_parts (threads, stage).
 NCU_TRAFFIC = {
     ("sel16", "f64", "k_sigma"): {
-        "source": "sigma.cu", "sha1": "7ddd8577b4c3c6aae2b8c7dd26e911d79be638c2",
-        "shapes": {(512, 1, 0): 1.998e9, (512, 2, 0): 7.439e9, (512, 3, 0): 12.643e9,
-                   (256, 1, 0): 1.356e9, (128, 1, 0): 0.803e9,
-                   (512, 1, 1): 1.233e9, (256, 1, 1): 0.811e9, (128, 1, 1): 1.558e9,
-                   (512, 1, 2): 2.049e9, (256, 1, 2): 1.496e9, (128, 1, 2): 3.683e9}},
+        "source": "sigma.cu", "sha1": "2e38dd72db29d3137f5f54aee410b1a51db79613",
+        "shapes": {(512, 3, 2): 21.10e9}},
     ("sel24", "f64", "k_sigma_parts"): {
         "source": "sigma_split.cu", "sha1": "bbca57e694e9aafe0b9476961be6286e724c7b3a",
         "shapes": {(1024, 3): 380.95e9}},

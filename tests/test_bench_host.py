@@ -41,18 +41,21 @@ def test_traffic_only_for_the_profiled_kernel_source_and_shape(bench, monkeypatc
     def counts(threads, nv, stage):
         return {"tuned_threads": [threads, 0], "tuned_nv": [nv, 0], "tuned_stage": [stage, 0]}
 
-    # three vectors in groups of two: one launch of two and one of one
-    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 2, 0), 3) == pytest.approx(
-        (shapes[(512, 2, 0)] + shapes[(512, 1, 0)]) / 2)
-    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 3, 0), 3) == pytest.approx(shapes[(512, 3, 0)])
-    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 1, 0), 3) == pytest.approx(shapes[(512, 1, 0)])
-    assert bench._traffic("sel16", "f64", "k_sigma", counts(256, 2, 0), 3) is None  # shape not captured
-    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 0, 0), 3) is None  # not tuned
+    # the captured shape: three vectors in one launch
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 3, 2), 3) == pytest.approx(shapes[(512, 3, 2)])
+    # three vectors in groups of two need the shapes of a 2-vector and a 1-vector launch
+    two = dict(shapes)
+    two[(512, 2, 2)], two[(512, 1, 2)] = 4.0e9, 1.0e9
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("sel16", "f64", "k_sigma"), dict(rec, shapes=two))
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 2, 2), 3) == pytest.approx(2.5e9)
+    monkeypatch.setitem(bench.NCU_TRAFFIC, ("sel16", "f64", "k_sigma"), rec)
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(256, 3, 2), 3) is None  # shape not captured
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 0, 2), 3) is None  # not tuned
     assert bench._traffic("fci16", "f64", "k_sigma", counts(512, 1, 0), 1) is None  # workload not captured
     assert bench._traffic("sel16", "f64", "k_sigma_parts", counts(512, 1, 3), 1) is None  # kernel not captured
     monkeypatch.setattr(bench, "_source_hash", lambda name: "0" * 40)
-    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 2, 0), 3) is None  # source changed since
-    assert bench._traffic("sel16", "bf16tc", "k_sigma", counts(512, 2, 0), 3) is None
+    assert bench._traffic("sel16", "f64", "k_sigma", counts(512, 3, 2), 3) is None  # source changed since
+    assert bench._traffic("sel16", "bf16tc", "k_sigma", counts(512, 3, 2), 3) is None
 
 
 def test_kernel_table_shares_and_fractions(bench):
