@@ -301,7 +301,7 @@ tbsci_status tbsci_sigma_counts_get(tbsci_ctx *ctx, tbsci_ham *ham, const tbsci_
 
 typedef struct tbsci_davidson_opts {
     int max_subspace;    /* basis size before restart; 0 -> max(8*nroots, nroots+2) */
-    int restart_keep;    /* Ritz vectors kept at a restart; 0 -> max(nroots, max_subspace/4) */
+    int restart_keep;    /* Ritz vectors kept at a restart; 0 -> max(nroots, max_subspace/2) */
     int max_iter;        /* 0 -> 1000 */
     double tol_energy;   /* |theta - theta_prev| per root; 0 -> 1e-9 */
     double tol_residual; /* ||r||_2 per root; 0 -> 1e-5 */

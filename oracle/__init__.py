@@ -399,7 +399,7 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     each unconverged residual by (theta - H_KK)^-1 (denominators of magnitude
     below 1e-8 clamped to +-1e-8, zero -> +1e-8); when the subspace would exceed
     ``max_subspace`` restart from the lowest ``restart_keep`` Ritz vectors
-    (default ``max(nroots, max_subspace // 4)``; the paper's restart scheme,
+    (default ``max(nroots, max_subspace // 2)``; the paper's restart scheme,
     Sec. III.C, keeps a bounded number of vectors and says no more), and with
     ``restart_prev`` also the previous iteration's Ritz vectors, orthonormalised
     against the kept ones in the coefficient space of the basis (while room is
@@ -420,7 +420,7 @@ def davidson(apply_h, diag, nroots, tol_e=1e-9, tol_r=1e-5, max_subspace=None, m
     if max_subspace is None:
         max_subspace = max(8 * nroots, nroots + 2)
     if restart_keep is None:
-        restart_keep = max(nroots, max_subspace // 4)
+        restart_keep = max(nroots, max_subspace // 2)
     order = np.lexsort((np.arange(N), diag))
     extra = min(4, N - nroots)
     V = np.zeros((nroots, N))

@@ -519,7 +519,7 @@ struct DavEngine {
         nroots = nr;
         t_start = std::chrono::steady_clock::now();
         m_max = opt.max_subspace > 0 ? opt.max_subspace : std::max(8 * nroots, nroots + 2);
-        keep = opt.restart_keep > 0 ? opt.restart_keep : std::max(nroots, m_max / 4);
+        keep = opt.restart_keep > 0 ? opt.restart_keep : std::max(nroots, m_max / 2);
         max_iter = opt.max_iter > 0 ? opt.max_iter : 1000;
         tol_e = opt.tol_energy > 0 ? opt.tol_energy : 1e-9;
         tol_r = opt.tol_residual > 0 ? opt.tol_residual : 1e-5;
@@ -904,23 +904,6 @@ struct DavEngine {
                 TB_CUDA(ctx, cudaMemcpyAsync(src, b32 ? (void *)R32.p : (void *)R.p, (size_t)kq * N * es(),
                                              cudaMemcpyDeviceToDevice, st));
             }
-            if (!b32) {
-                // FP64 basis: the Rayleigh matrix of the new basis V Q is Q^T G Q,
-                // formed on the host instead of kq^2 dot products over the vectors
-                // (the FP32 basis measures G and its overlap again instead)
-                std::vector<double> GQ((size_t)m * kq, 0.0), Gn((size_t)kq * kq, 0.0);
-                for (int i = 0; i < m; ++i)
-                    for (int j = 0; j < m; ++j) {
-                        const double g = G[(size_t)i * m_max + j];
-                        for (int c = 0; c < kq; ++c) GQ[(size_t)i * kq + c] += g * Q[(size_t)j * ldq + c];
-                    }
-                for (int i = 0; i < m; ++i)
-                    for (int a = 0; a < kq; ++a)
-                        for (int c = 0; c < kq; ++c) Gn[(size_t)a * kq + c] += Q[(size_t)i * ldq + a] * GQ[(size_t)i * kq + c];
-                for (int a = 0; a < kq; ++a)
-                    for (int c = 0; c < kq; ++c)
-                        G[(size_t)a * m_max + c] = 0.5 * (Gn[(size_t)a * kq + c] + Gn[(size_t)c * kq + a]);
-            }
             m = kq;
             restarted = true;
         }
@@ -965,7 +948,7 @@ struct DavEngine {
             TB_TRY(normalize(t, scal.p + 2 * j + 1));
         }
         TB_CUDA(ctx, cudaMemcpyAsync(hN, scal.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-        g_lo = (restarted && b32) ? 0 : m;
+        g_lo = restarted ? 0 : m;
         return finish_phase(St::WaitGS);
     }
 
@@ -1069,7 +1052,7 @@ tbsci_status engine_results(DavEngine *e, double *energies, double *vecs, tbsci_
 
 size_t engine_device_bytes(int64_t N, int nroots, const tbsci_davidson_opts *o) {
     const int m_max = (o && o->max_subspace > 0) ? o->max_subspace : std::max(8 * nroots, nroots + 2);
-    const int keep = (o && o->restart_keep > 0) ? o->restart_keep : std::max(nroots, m_max / 4);
+    const int keep = (o && o->restart_keep > 0) ? o->restart_keep : std::max(nroots, m_max / 2);
     size_t vec = (size_t)(2 * m_max + keep + 4 * nroots + 1) * N * sizeof(double);
     if (o && o->mixed && o->basis_f32) {
         const int m_ref = o->max_subspace_refine > 0 ? o->max_subspace_refine : std::max(nroots + 1, m_max / 2);
