@@ -990,7 +990,7 @@ struct DavEngine {
             if (s == St::WaitG) TB_TRY(after_G());
             else if (s == St::WaitR) TB_TRY(after_R());
             else TB_TRY(after_GS());
-            if (!blocking) return TBSCI_OK;  // one phase per poll keeps the driver's round short
+            if (!blocking) return TBSCI_OK;  // one phase per poll keeps each scheduler pass short
         }
         return TBSCI_OK;
     }
