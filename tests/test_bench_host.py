@@ -104,3 +104,22 @@ def test_clock_sampler_start_stop_with_a_stand_in_tool(bench, tmp_path, monkeypa
     out = s.stop()
     assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     assert s.proc.poll() is not None  # the tool was terminated
+
+
+def test_kernel_table_tensor_and_unmodelled_kernels(bench):
+    """The tensor-core alpha-beta kernel is measured against the tensor peak (the
+    TF32 type at half the BF16 peak), the column-tiled beta product of the
+    tensor-core types counts the beta singles too, and a kernel without an
+    algorithmic model (the cuBLAS products of rest mode 5) reports no fraction."""
+    c = {"la": 64, "lb": 64, "ndet": 4096, "nnz": 0, "n1a": 640, "n2a": 1000, "n1b": 640, "n2b": 1000,
+         "norb": 8}
+    trace = [("k_sigma_ab_tc", 2.0), ("k_dbl_spmm_beta", 1.0), ("gemm_same_spin", 0.5)]
+    rows = {r["kernel"]: r for r in bench._kernel_table(trace, 1, c, 1, "tf32tc")}
+    tc = rows["k_sigma_ab_tc"]
+    assert tc["bound"] == "tensor" and tc["work_per_launch"] == 2.0 * 28 * 640 * 64
+    bf = bench._measured_peaks().get("bf16_tflops", 1900.0)
+    assert tc["peak"] == pytest.approx(0.5 * bf)
+    assert rows["k_dbl_spmm_beta"]["work_per_launch"] == 2.0 * (1000 + 640) * 64
+    g = rows["gemm_same_spin"]
+    assert g["work_per_launch"] is None and g["achieved"] is None and g["frac"] is None
+
